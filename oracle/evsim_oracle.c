@@ -1,0 +1,464 @@
+/*
+ * Oracle for the Neurosim event-generation path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, single-threaded CPU
+ * restatement of the event model, written to check the CUDA library against.
+ * Only the test suite, the smoke check and the CPU-baseline leg of the
+ * benchmark may load it.  It shares no code, header, table or constant
+ * generator with the CUDA path, and the CUDA path never calls it.
+ *
+ * Paper: "Neurosim: A Fast Simulator for Neuromorphic Robot Perception",
+ * arXiv 2602.15018.
+ *   - Sec. 1: an event is a tuple (t, u, p) with an integer timestamp in
+ *     microseconds, an integer pixel u and a polarity p in {-1, +1}.
+ *   - Sec. 2, paragraph "Neurosim simulates event cameras at multi-kilohertz
+ *     rates": each pixel keeps the intensity level of its last triggered
+ *     event; an event fires when the change from that level passes a
+ *     contrast threshold (the contrast-threshold model of the cited ESIM);
+ *     noise is among the non-idealities the user may switch off; each
+ *     rendering step yields a variable number of events.
+ * The paper gives the model in prose only.  Every reading of a silent point
+ * taken here is listed in the "Readings" block below and is the same reading
+ * the CUDA path implements.
+ *
+ * Readings (the paper is silent on all of these):
+ *   R1  L = log(clamp(I, 0, 1e6) + eps) in FP32 with the project's own log
+ *       (oracle_mylog below); with input_is_log the frame already holds L and
+ *       is clamped to [-32, 32].  NaN intensities clamp to 0 (or to -32 in the
+ *       log domain).
+ *   R2  Log intensity is linear in time between consecutive frames (ESIM).
+ *   R3  Crossings are taken one threshold at a time with sequential FP32
+ *       adds: ON while fl(ref + C+) <= b, OFF while fl(ref - C-) >= b, and on
+ *       each crossing ref moves to the crossed level (not to b).
+ *   R4  Crossing time t = ta + floor(frac * D) with frac = (lvl - a)/(b - a)
+ *       in FP32 and D = tb - ta in integer microseconds, so t lies in
+ *       [ta, tb].  A negative t - ta (only reachable from an imported state
+ *       that breaks the reference-band invariant) is clamped to 0.
+ *   R5  Refractory period R: a crossing with t - t_last < R is suppressed;
+ *       ref still moves, t_last keeps the last emitted time.
+ *   R6  Per-pixel thresholds C+-_u = max(c_min, C+- + sigma * z+-_u), drawn
+ *       once.  z is an Irwin-Hall(12) normal (sum of twelve 20-bit uniforms
+ *       minus 6) from SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) used as
+ *       a counter-based generator: draw k of pixel u and polarity q is output
+ *       number ((2u + q) * 12 + k) of the SplitMix64 stream seeded with seed.
+ *   R7  The first frame a sensor ever sees sets ref = L_prev = L and emits
+ *       nothing.
+ *   R8  Output order: interval-major; inside one interval ascending by the
+ *       packed record (t, y, x, p), OFF (p = 0) before ON (p = 1).
+ *
+ * Packed record (64 bits): [63:32] t (us) | [31:17] y | [16:1] x | [0] p.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -fPIC -shared.
+ * Contraction must stay off: the FP32 variant mirrors the operation order of
+ * the model exactly so that its events are reproducible bit for bit.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_OK 0
+#define ORACLE_E_INVALID 1
+#define ORACLE_E_NOMEM 2
+#define ORACLE_E_TIME 3
+
+#define LOG_DOMAIN_MAX 32.0f
+#define INTENSITY_MAX 1.0e6f
+#define TLAST_NONE (-1)
+
+static uint32_t f2u(float x) { uint32_t u; memcpy(&u, &x, 4); return u; }
+static float u2f(uint32_t u) { float x; memcpy(&x, &u, 4); return x; }
+
+/* ------------------------------------------------------------------------ */
+/* The project's own single-precision natural log (reading R1).             */
+/*                                                                          */
+/* Textbook method: x = m * 2^e with m in [sqrt(1/2), sqrt(2)); with        */
+/* s = (m - 1)/(m + 1), log m = 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + s^7/7    */
+/* + s^9/9 + ...), truncated after s^9 (|s| < 0.1716 so the next term is    */
+/* below 1e-9 relative); log x = log m + e ln2 with ln2 split into a 16-bit */
+/* head (so that e * head is exact) and a tail.  Every operation is one     */
+/* IEEE-rounded FP32 operation in the order written.                        */
+/* ------------------------------------------------------------------------ */
+static const float C_INV3 = 0x1.555556p-2f;   /* 1/3 rounded to FP32 */
+static const float C_INV5 = 0x1.99999ap-3f;   /* 1/5 */
+static const float C_INV7 = 0x1.24924ap-3f;   /* 1/7 */
+static const float C_INV9 = 0x1.c71c72p-4f;   /* 1/9 */
+static const float C_LN2_HI = 0x1.62e4p-1f;   /* round(ln2 * 2^16) / 2^16 */
+static const float C_LN2_LO = 0x1.7f7d1cp-20f; /* ln2 - C_LN2_HI, rounded */
+static const float C_SQRT2 = 0x1.6a09e6p+0f;  /* sqrt(2) rounded */
+
+float oracle_mylog(float x)
+{
+    if (x != x) return x;                 /* NaN */
+    if (x < 0.0f) return NAN;
+    if (x == 0.0f) return -INFINITY;
+    if (x == INFINITY) return INFINITY;
+    int e = 0;
+    uint32_t bits = f2u(x);
+    if (bits < 0x00800000u) {             /* subnormal: scale by 2^24 (exact) */
+        x = x * 0x1p24f;
+        bits = f2u(x);
+        e = -24;
+    }
+    e += (int)(bits >> 23) - 127;
+    float m = u2f((bits & 0x007fffffu) | 0x3f800000u);   /* [1, 2) */
+    if (m > C_SQRT2) {
+        m = m * 0.5f;
+        e += 1;
+    }
+    float num = m - 1.0f;
+    float den = m + 1.0f;
+    float s = num / den;
+    float z = s * s;
+    float q = fmaf(z, C_INV9, C_INV7);
+    q = fmaf(z, q, C_INV5);
+    q = fmaf(z, q, C_INV3);
+    float s2 = s + s;
+    float zq = z * q;
+    float lm = fmaf(s2, zq, s2);
+    float fe = (float)e;
+    float tail = fmaf(fe, C_LN2_LO, lm);
+    return fmaf(fe, C_LN2_HI, tail);
+}
+
+void oracle_mylog_batch(const float *x, float *y, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = oracle_mylog(x[i]);
+}
+
+/* Distance in units in the last place between a float and a double
+ * reference, measured on the FP32 grid around the reference. */
+static double ulp_err(float got, double ref)
+{
+    if (isinf(ref) || isnan(ref)) return (got == (float)ref) ? 0.0 : INFINITY;
+    double a = fabs(ref);
+    int ex;
+    frexp(a, &ex);                 /* a = f * 2^ex, f in [0.5, 1) */
+    double ulp = ldexp(1.0, ex - 24);
+    if (ulp < 0x1p-149) ulp = 0x1p-149;
+    return fabs((double)got - ref) / ulp;
+}
+
+/* Scans every FP32 value with bit pattern in [lo_bits, hi_bits] (positive
+ * floats only) and reports the largest error of oracle_mylog against the
+ * double-precision libm log, in FP32 ulps. */
+double oracle_mylog_max_ulp(uint32_t lo_bits, uint32_t hi_bits, uint32_t stride,
+                            uint32_t *worst_bits)
+{
+    double worst = 0.0;
+    uint32_t wb = lo_bits;
+    if (stride == 0) stride = 1;
+    for (uint64_t b = lo_bits; b <= hi_bits; b += stride) {
+        float x = u2f((uint32_t)b);
+        double e = ulp_err(oracle_mylog(x), log((double)x));
+        if (e > worst) { worst = e; wb = (uint32_t)b; }
+    }
+    if (worst_bits) *worst_bits = wb;
+    return worst;
+}
+
+/* ------------------------------------------------------------------------ */
+/* SplitMix64 (Steele, Lea, Flood 2014): state += 0x9e3779b97f4a7c15, then  */
+/* the output is the state passed through the variant-13 mixer.  Output     */
+/* number i (0-based) of the stream seeded with s therefore only depends on */
+/* s + (i + 1) * gamma, which makes it usable as a counter-based generator. */
+/* ------------------------------------------------------------------------ */
+uint64_t oracle_splitmix64_at(uint64_t seed, uint64_t index)
+{
+    uint64_t z = seed + (index + 1u) * 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+/* Irwin-Hall(12) standard normal draw number `slot` (reading R6): the sum of
+ * twelve uniforms on {0..2^20-1}, minus 6 * 2^20, scaled by 2^-20.  The sum is
+ * below 2^24 so the FP32 result is exact. */
+float oracle_normal_ih12(uint64_t seed, uint64_t slot)
+{
+    int64_t acc = 0;
+    for (int k = 0; k < 12; ++k)
+        acc += (int64_t)(oracle_splitmix64_at(seed, slot * 12u + (uint64_t)k) >> 44);
+    int64_t centred = acc - 6 * (int64_t)(1 << 20);
+    return (float)centred * 0x1p-20f;
+}
+
+/* Per-pixel thresholds (reading R6): C+-_u = max(c_min, C+- + sigma * z+-_u)
+ * with one FP32 multiply and one FP32 add. */
+void oracle_threshold_maps(int32_t width, int32_t height, float c_pos, float c_neg,
+                           float sigma, float c_min, uint64_t seed,
+                           float *cpos_out, float *cneg_out)
+{
+    int64_t n = (int64_t)width * height;
+    for (int64_t u = 0; u < n; ++u) {
+        float vp = c_pos, vn = c_neg;
+        if (sigma != 0.0f) {
+            float zp = oracle_normal_ih12(seed, (uint64_t)u * 2u + 0u);
+            float zn = oracle_normal_ih12(seed, (uint64_t)u * 2u + 1u);
+            float dp = sigma * zp;
+            float dn = sigma * zn;
+            vp = c_pos + dp;
+            vn = c_neg + dn;
+        }
+        cpos_out[u] = fmaxf(c_min, vp);
+        cneg_out[u] = fmaxf(c_min, vn);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Event buffer                                                             */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    uint64_t *ev;
+    int64_t n, cap;
+    int64_t *seg;       /* interval offsets, n_seg + 1 entries */
+    int32_t n_seg, seg_cap;
+    int failed;
+} evbuf;
+
+static void eb_push(evbuf *b, uint64_t rec)
+{
+    if (b->failed) return;
+    if (b->n == b->cap) {
+        int64_t nc = b->cap ? b->cap * 2 : 4096;
+        uint64_t *p = (uint64_t *)realloc(b->ev, (size_t)nc * sizeof(uint64_t));
+        if (!p) { b->failed = 1; return; }
+        b->ev = p;
+        b->cap = nc;
+    }
+    b->ev[b->n++] = rec;
+}
+
+static void eb_close_segment(evbuf *b)
+{
+    if (b->failed) return;
+    if (b->n_seg + 2 > b->seg_cap) {
+        int32_t nc = b->seg_cap ? b->seg_cap * 2 : 256;
+        int64_t *p = (int64_t *)realloc(b->seg, (size_t)nc * sizeof(int64_t));
+        if (!p) { b->failed = 1; return; }
+        b->seg = p;
+        b->seg_cap = nc;
+    }
+    if (b->n_seg == 0) b->seg[0] = 0;
+    b->seg[++b->n_seg] = b->n;
+}
+
+static int cmp_u64(const void *pa, const void *pb)
+{
+    uint64_t a = *(const uint64_t *)pa, b = *(const uint64_t *)pb;
+    return (a > b) - (a < b);
+}
+
+static uint64_t pack(int64_t t, int32_t x, int32_t y, int on)
+{
+    return ((uint64_t)(uint32_t)t << 32) | ((uint64_t)(uint32_t)y << 17) |
+           ((uint64_t)(uint32_t)x << 1) | (uint64_t)(on ? 1u : 0u);
+}
+
+static int check_args(int32_t W, int32_t H, int32_t T, int64_t t0, int32_t dt,
+                      int has_prev, int64_t tau_prev)
+{
+    if (W <= 0 || H <= 0 || W > 65535 || H > 32767 || T < 0) return ORACLE_E_INVALID;
+    if (dt <= 0 || dt >= (1 << 24) || t0 < 0) return ORACLE_E_TIME;
+    if (T == 0) return ORACLE_OK;
+    int64_t last = t0 + (int64_t)(T - 1) * dt;
+    if (last > 0xFFFFFFFEll) return ORACLE_E_TIME;
+    if (has_prev && (t0 <= tau_prev || t0 - tau_prev >= (1 << 24))) return ORACLE_E_TIME;
+    return ORACLE_OK;
+}
+
+static void finish(evbuf *b, uint64_t **events_out, int64_t *n_events_out,
+                   int64_t **seg_out, int32_t *n_seg_out)
+{
+    if (b->n_seg == 0) {                 /* always hand back seg[0] = 0 */
+        b->seg = (int64_t *)malloc(sizeof(int64_t));
+        if (b->seg) b->seg[0] = 0;
+    }
+    *events_out = b->ev;
+    *n_events_out = b->n;
+    *seg_out = b->seg;
+    *n_seg_out = b->n_seg;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One step of the event model, FP32 mirrored (readings R1-R8).             */
+/*                                                                          */
+/* frames: T frames of H x W row-major FP32 intensities (or log intensities */
+/* when input_is_log).  Frame f is at time t0 + f * dt.  State arrays are   */
+/* read and updated in place.  tlast holds -1 for "no event yet".           */
+/* On return *events_out holds the step's records in output order and       */
+/* *seg_out the n_seg + 1 interval offsets; release both with oracle_free.  */
+/* ------------------------------------------------------------------------ */
+int oracle_evsim_step_f32(int32_t W, int32_t H, const float *frames, int32_t T,
+                          int64_t t0, int32_t dt, const float *cpos, const float *cneg,
+                          uint32_t refractory_us, float log_eps, int32_t input_is_log,
+                          float *ref, float *lprev, int64_t *tlast, int32_t *has_prev,
+                          int64_t *tau_prev, uint64_t **events_out, int64_t *n_events_out,
+                          int64_t **seg_out, int32_t *n_seg_out)
+{
+    int rc = check_args(W, H, T, t0, dt, *has_prev, *tau_prev);
+    if (rc != ORACLE_OK) return rc;
+    const int64_t npix = (int64_t)W * H;
+    evbuf b;
+    memset(&b, 0, sizeof b);
+
+    for (int32_t f = 0; f < T; ++f) {
+        const float *fr = frames + (int64_t)f * npix;
+        const int64_t tb = t0 + (int64_t)f * dt;
+        if (!*has_prev) {                                   /* R7 */
+            for (int64_t u = 0; u < npix; ++u) {
+                float L;
+                if (input_is_log) L = fminf(fmaxf(fr[u], -LOG_DOMAIN_MAX), LOG_DOMAIN_MAX);
+                else L = oracle_mylog(fminf(fmaxf(fr[u], 0.0f), INTENSITY_MAX) + log_eps);
+                ref[u] = L;
+                lprev[u] = L;
+                tlast[u] = TLAST_NONE;
+            }
+            *has_prev = 1;
+            *tau_prev = tb;
+            continue;
+        }
+        const int64_t ta = *tau_prev;
+        const int64_t D = tb - ta;
+        const float Df = (float)D;
+        const int64_t seg_start = b.n;
+        for (int64_t u = 0; u < npix; ++u) {
+            const int32_t y = (int32_t)(u / W), x = (int32_t)(u % W);
+            float L;
+            if (input_is_log) L = fminf(fmaxf(fr[u], -LOG_DOMAIN_MAX), LOG_DOMAIN_MAX);
+            else L = oracle_mylog(fminf(fmaxf(fr[u], 0.0f), INTENSITY_MAX) + log_eps);
+            const float a = lprev[u];
+            const float bb = L;
+            float r = ref[u];
+            int64_t tl = tlast[u];
+            if (bb > a) {
+                const float den = bb - a;
+                for (;;) {                                   /* R3 (ON) */
+                    const float lvl = r + cpos[u];
+                    if (!(lvl <= bb)) break;
+                    const float num = lvl - a;
+                    const float frac = num / den;
+                    float tf = floorf(frac * Df);            /* R4 */
+                    if (tf < 0.0f) tf = 0.0f;
+                    const int64_t t = ta + (int64_t)tf;
+                    r = lvl;
+                    if (refractory_us != 0 && tl != TLAST_NONE && t - tl < (int64_t)refractory_us)
+                        continue;                            /* R5 */
+                    eb_push(&b, pack(t, x, y, 1));
+                    tl = t;
+                }
+            } else if (bb < a) {
+                const float den = bb - a;
+                for (;;) {                                   /* R3 (OFF) */
+                    const float lvl = r - cneg[u];
+                    if (!(lvl >= bb)) break;
+                    const float num = lvl - a;
+                    const float frac = num / den;
+                    float tf = floorf(frac * Df);
+                    if (tf < 0.0f) tf = 0.0f;
+                    const int64_t t = ta + (int64_t)tf;
+                    r = lvl;
+                    if (refractory_us != 0 && tl != TLAST_NONE && t - tl < (int64_t)refractory_us)
+                        continue;
+                    eb_push(&b, pack(t, x, y, 0));
+                    tl = t;
+                }
+            }
+            ref[u] = r;
+            tlast[u] = tl;
+            lprev[u] = bb;
+        }
+        if (!b.failed && b.n > seg_start)                   /* R8 */
+            qsort(b.ev + seg_start, (size_t)(b.n - seg_start), sizeof(uint64_t), cmp_u64);
+        eb_close_segment(&b);
+        *tau_prev = tb;
+    }
+    if (b.failed) {
+        free(b.ev);
+        free(b.seg);
+        return ORACLE_E_NOMEM;
+    }
+    finish(&b, events_out, n_events_out, seg_out, n_seg_out);
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same model in FP64 with the libm log: the precision reference that    */
+/* the FP32 path is compared against (at most 1e-4 of events differ, times  */
+/* within 1 us).  Thresholds come in as the same FP32 maps.                 */
+/* ------------------------------------------------------------------------ */
+int oracle_evsim_step_f64(int32_t W, int32_t H, const float *frames, int32_t T,
+                          int64_t t0, int32_t dt, const float *cpos, const float *cneg,
+                          uint32_t refractory_us, double log_eps, int32_t input_is_log,
+                          double *ref, double *lprev, int64_t *tlast, int32_t *has_prev,
+                          int64_t *tau_prev, uint64_t **events_out, int64_t *n_events_out,
+                          int64_t **seg_out, int32_t *n_seg_out)
+{
+    int rc = check_args(W, H, T, t0, dt, *has_prev, *tau_prev);
+    if (rc != ORACLE_OK) return rc;
+    const int64_t npix = (int64_t)W * H;
+    evbuf b;
+    memset(&b, 0, sizeof b);
+
+    for (int32_t f = 0; f < T; ++f) {
+        const float *fr = frames + (int64_t)f * npix;
+        const int64_t tb = t0 + (int64_t)f * dt;
+        if (!*has_prev) {
+            for (int64_t u = 0; u < npix; ++u) {
+                double L;
+                if (input_is_log) L = fmin(fmax((double)fr[u], -32.0), 32.0);
+                else L = log(fmin(fmax((double)fr[u], 0.0), 1.0e6) + log_eps);
+                ref[u] = L;
+                lprev[u] = L;
+                tlast[u] = TLAST_NONE;
+            }
+            *has_prev = 1;
+            *tau_prev = tb;
+            continue;
+        }
+        const int64_t ta = *tau_prev;
+        const double D = (double)(tb - ta);
+        const int64_t seg_start = b.n;
+        for (int64_t u = 0; u < npix; ++u) {
+            const int32_t y = (int32_t)(u / W), x = (int32_t)(u % W);
+            double L;
+            if (input_is_log) L = fmin(fmax((double)fr[u], -32.0), 32.0);
+            else L = log(fmin(fmax((double)fr[u], 0.0), 1.0e6) + log_eps);
+            const double a = lprev[u], bb = L;
+            double r = ref[u];
+            int64_t tl = tlast[u];
+            const int on = bb > a;
+            if (bb != a) {
+                const double c = on ? (double)cpos[u] : -(double)cneg[u];
+                for (;;) {
+                    const double lvl = r + c;
+                    if (on ? !(lvl <= bb) : !(lvl >= bb)) break;
+                    double tf = floor((lvl - a) / (bb - a) * D);
+                    if (tf < 0.0) tf = 0.0;
+                    const int64_t t = ta + (int64_t)tf;
+                    r = lvl;
+                    if (refractory_us != 0 && tl != TLAST_NONE && t - tl < (int64_t)refractory_us)
+                        continue;
+                    eb_push(&b, pack(t, x, y, on));
+                    tl = t;
+                }
+            }
+            ref[u] = r;
+            tlast[u] = tl;
+            lprev[u] = bb;
+        }
+        if (!b.failed && b.n > seg_start)
+            qsort(b.ev + seg_start, (size_t)(b.n - seg_start), sizeof(uint64_t), cmp_u64);
+        eb_close_segment(&b);
+        *tau_prev = tb;
+    }
+    if (b.failed) {
+        free(b.ev);
+        free(b.seg);
+        return ORACLE_E_NOMEM;
+    }
+    finish(&b, events_out, n_events_out, seg_out, n_seg_out);
+    return ORACLE_OK;
+}
+
+void oracle_free(void *p) { free(p); }

@@ -1,0 +1,81 @@
+"""Planted mistakes in a copy of the oracle must each fail at least one pin.
+
+Each case rewrites one expression of oracle/evsim_oracle.c in a temporary
+copy, builds it with the oracle's own flags, and runs the pins against it.
+This checks that the pins are strong enough to catch a plausible slip (a tie
+rule, a dropped state update, a transposed coordinate, a wrong rounding)."""
+import os
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle
+import oracle_pins as P
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(os.path.dirname(HERE), "oracle")
+
+# (name, original text, replacement, count of occurrences to replace)
+MUTANTS = [
+    ("tie_rule_strict", "if (!(lvl <= bb)) break;", "if (!(lvl < bb)) break;"),
+    ("ref_to_frame_value", "                    r = lvl;\n                    if (refractory_us != 0 && tl != TLAST_NONE && t - tl < (int64_t)refractory_us)\n                        continue;                            /* R5 */",
+     "                    r = bb;\n                    if (refractory_us != 0 && tl != TLAST_NONE && t - tl < (int64_t)refractory_us)\n                        continue;                            /* R5 */"),
+    ("frac_flipped", "const float num = lvl - a;\n                    const float frac = num / den;\n                    float tf = floorf(frac * Df);            /* R4 */",
+     "const float num = bb - lvl;\n                    const float frac = num / den;\n                    float tf = floorf(frac * Df);            /* R4 */"),
+    ("round_not_floor", "float tf = floorf(frac * Df);            /* R4 */",
+     "float tf = roundf(frac * Df);            /* R4 */"),
+    ("refractory_le", "t - tl < (int64_t)refractory_us)\n                        continue;                            /* R5 */",
+     "t - tl <= (int64_t)refractory_us)\n                        continue;                            /* R5 */"),
+    ("tlast_not_updated", "eb_push(&b, pack(t, x, y, 1));\n                    tl = t;",
+     "eb_push(&b, pack(t, x, y, 1));"),
+    ("polarity_swapped", "eb_push(&b, pack(t, x, y, 0));", "eb_push(&b, pack(t, x, y, 1));"),
+    ("xy_transposed", "eb_push(&b, pack(t, x, y, 1));", "eb_push(&b, pack(t, y, x, 1));"),
+    ("interval_start_wrong", "const int64_t ta = *tau_prev;", "const int64_t ta = tb - dt;"),
+    ("log_coeff", "static const float C_INV5 = 0x1.99999ap-3f;",
+     "static const float C_INV5 = 0x1.555556p-3f;"),
+    ("log_no_range_fold", "if (m > C_SQRT2) {", "if (m > 2.0f) {"),
+    ("noise_same_draw", "float zn = oracle_normal_ih12(seed, (uint64_t)u * 2u + 1u);",
+     "float zn = oracle_normal_ih12(seed, (uint64_t)u * 2u + 0u);"),
+    ("noise_sign", "vp = c_pos + dp;", "vp = c_pos - dp;"),
+    ("first_frame_lprev", "                ref[u] = L;\n                lprev[u] = L;\n                tlast[u] = TLAST_NONE;\n            }\n            *has_prev = 1;\n            *tau_prev = tb;\n            continue;\n        }\n        const int64_t ta = *tau_prev;\n        const int64_t D = tb - ta;\n        const float Df",
+     "                ref[u] = L;\n                lprev[u] = 0.0f;\n                tlast[u] = TLAST_NONE;\n            }\n            *has_prev = 1;\n            *tau_prev = tb;\n            continue;\n        }\n        const int64_t ta = *tau_prev;\n        const int64_t D = tb - ta;\n        const float Df"),
+]
+
+
+def _build_mutant(tmp, name, old, new):
+    src = open(os.path.join(SRC, "evsim_oracle.c")).read()
+    assert old in src, f"mutation site for {name} not found"
+    mutated = src.replace(old, new, 1)
+    d = os.path.join(tmp, name)
+    os.makedirs(d)
+    open(os.path.join(d, "evsim_oracle.c"), "w").write(mutated)
+    shutil.copy(os.path.join(SRC, "consumers_oracle.c"), d)
+    so = os.path.join(d, "lib.so")
+    subprocess.check_call(["gcc", *oracle.CFLAGS, "-o", so, os.path.join(d, "evsim_oracle.c"),
+                           os.path.join(d, "consumers_oracle.c"), "-lm"])
+    return oracle.load_library(so)
+
+
+def _fails_some_pin(library):
+    pins = P.ALL_PINS + [lambda L: P.pin_log(L, stride=257)]
+    for pin in pins:
+        try:
+            pin(library)
+        except (AssertionError, oracle.OracleError):
+            return True
+    return False
+
+
+@pytest.fixture(scope="module")
+def tmpdir_mut():
+    d = tempfile.mkdtemp(prefix="oracle_mut_")
+    yield d
+    shutil.rmtree(d, ignore_errors=True)
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmpdir_mut, name, old, new):
+    lib = _build_mutant(tmpdir_mut, name, old, new)
+    assert _fails_some_pin(lib), f"planted mistake {name} passed every pin"
