@@ -1,0 +1,437 @@
+#!/usr/bin/env python
+"""Benchmark of the event-generation path on GB300 (one JSON line on stdout).
+
+Workload (default, "hd"): 1280x720 FP32 intensity frames, 2000 frames at
+1000 FPS per step; value-noise texture under an affine camera path with 16
+moving occluders; C+ 0.2, C- 0.25, per-pixel threshold sigma 0.03, refractory
+100 us.  One step = emission + interval sort + drain of the step's events to
+a device buffer, over frames already resident in HBM (7.4 GB per step, far
+larger than L2, so no L2 flush is needed between steps).
+
+Metric: Mpixel-frames/s (whole job, all ranks) with events/s alongside.
+Roofline: the emission kernel (the dominant one), algorithmic bytes per
+launch = 4 B per pixel-frame read + 32 B per pixel of state and thresholds
++ 4 B per event key written, over its CUDA-event duration on the library's
+stream, against the measured HBM copy bandwidth.
+
+--impl reference runs the oracle (the plain CPU restatement of the model) on
+a bounded sample of the same workload on the host cores.
+
+Multi-GPU (torchrun): independent replicas, one sensor stream per rank with
+its own seed; no collective on the data path (the barrier and the max over
+ranks of the timed region use torch.distributed only for timing).
+"""
+from __future__ import annotations
+
+import argparse
+import datetime as _dt
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+import scenes  # noqa: E402
+
+DT = 1000
+HD = dict(W=1280, H=720, T=2000)
+CONFIG2_SIM = dict(c_pos=0.2, c_neg=0.25, sigma_c=0.03, c_min=0.01, refractory_us=100, seed=1)
+C1 = dict(W=240, H=180, T=200)
+CONFIG1_SIM = dict(c_pos=0.2, c_neg=0.2, sigma_c=0.0, c_min=0.01, refractory_us=0, seed=0)
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "Mpixel-frames/s (events/s alongside), plain event simulation"
+
+
+def render_config2(seed: int = 0, device="cuda", n_frames: int = HD["T"]) -> torch.Tensor:
+    sc = scenes.TextureScene(HD["W"], HD["H"], seed=seed)
+    return scenes.render_frames(sc, n_frames, device=device, chunk=32)
+
+
+def render_config1(seed: int = 0, device="cuda", n_frames: int = C1["T"]) -> torch.Tensor:
+    return scenes.render_frames(scenes.SinusoidScene(C1["W"], C1["H"], seed=seed), n_frames,
+                                device=device)
+
+
+WORKLOADS = {
+    "hd": dict(dims=HD, sim=CONFIG2_SIM, render=render_config2,
+               name="plain HD: 1280x720 FP32, 2000 frames @1000 FPS, value-noise texture + "
+                    "affine camera + 16 occluders, C+0.2 C-0.25 sigma0.03 refractory 100us"),
+    "c1": dict(dims=C1, sim=CONFIG1_SIM, render=render_config1,
+               name="plain 240x180 FP32, 200 frames @1000 FPS, 8 translating sinusoids, "
+                    "C+-0.2, no noise, no refractory"),
+}
+
+
+# --------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2602_15018_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".h", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(px_frames_per_launch: int, workload: str):
+    """DRAM bytes per emission launch from the committed ncu summary, scaled by
+    pixel-frames; None when absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", f"emit_kernel_{workload}.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"bench: dram_bytes_per_px_frame=([0-9.eE+-]+) source=([0-9a-f]+)", txt)
+    if not m or m.group(2) != kernel_source_hash():
+        return None
+    return float(m.group(1)) * px_frames_per_launch
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, local_rank: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        self.sel = vis.split(",")[local_rank].strip() if vis else str(local_rank)
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.sel], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [c.strip() for c in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        rows = [r for (t, r) in self.rows if t0 - 0.25 <= t <= t1 + 0.25 and len(r) >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = sorted({n for r in rows for n, v in zip(self.NAMES, r[4:8]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args):
+    from paper_2602_15018_gb300 import EventSim
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    wl = WORKLOADS[args.workload]
+    W, H, T = wl["dims"]["W"], wl["dims"]["H"], wl["dims"]["T"]
+    npix = W * H
+    frames = wl["render"](seed=args.seed + rank, device=dev)
+    torch.cuda.synchronize()
+
+    sim = EventSim(W, H, **wl["sim"], max_frames_per_step=T)
+    span = T * DT
+    cap = npix * T // 8
+    out = torch.empty(cap, dtype=torch.int64, device=dev)
+
+    def one_step(k):
+        nonlocal out
+        sim.step(frames, k * span, DT)
+        n, _ = sim.pending()
+        if n > out.numel():
+            out = torch.empty(int(n * 1.25), dtype=torch.int64, device=dev)
+        ev, _ = sim.drain(to="cuda", out=out)
+        return int(ev.numel())
+
+    k = 0
+    for _ in range(args.warmup):
+        one_step(k)
+        k += 1
+    # the stream-time budget of timestamps (2^32 us) bounds the number of steps
+    if (k + args.steps + 1) * span > 0xFFFFFFFE:
+        raise SystemExit("too many steps for the 2^32 us timestamp range")
+    sim.set_profiling(True)
+    st0 = sim.stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = sim.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    tw0 = time.time()
+    e0.record(stream)
+    n_events = 0
+    for _ in range(args.steps):
+        n_events += one_step(k)
+        k += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tw1 = time.time()
+    if dist:
+        dist.barrier()
+    clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st1 = sim.stats()
+    sim.set_profiling(False)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        ev_t = torch.tensor([n_events], device=dev, dtype=torch.float64)
+        dist.all_reduce(ev_t, op=dist.ReduceOp.SUM)
+        n_events_all = int(ev_t.item())
+    else:
+        n_events_all = n_events
+
+    px_frames_step = T * npix
+    total_px = px_frames_step * args.steps * ws
+    value = total_px / (ms / 1e3) / 1e6
+    launches = int(st1["kernel_launches"] - st0["kernel_launches"])
+    timed = st1["timed_steps"] - st0["timed_steps"]
+    emit_ms = (st1["emit_ms"] - st0["emit_ms"]) / max(1, timed)
+    sort_ms = (st1["sort_ms"] - st0["sort_ms"]) / max(1, timed)
+    ev_per_step = n_events / max(1, args.steps)
+    alg_bytes = 4.0 * px_frames_step + 32.0 * npix + 4.0 * ev_per_step
+    peak, peak_src = measured_peaks()
+    achieved = alg_bytes / (emit_ms / 1e3) / 1e9
+    traffic = profiled_traffic(px_frames_step, args.workload)
+
+    # end to end through the C ABI with host buffers (pinned frames in, host events out)
+    e2e = None
+    if args.e2e_steps > 0:
+        host_frames = frames.cpu().pin_memory()
+        del frames
+        torch.cuda.empty_cache()
+        host_out = np.empty(cap, np.uint64)
+        sim2 = EventSim(W, H, **wl["sim"], max_frames_per_step=T)
+        d2h = 0
+
+        def e2e_step(kk):
+            nonlocal host_out
+            sim2.step_host(host_frames, kk * span, DT)
+            n, _ = sim2.pending()
+            if n > host_out.size:
+                host_out = np.empty(int(n * 1.25), np.uint64)
+            ev, _ = sim2.drain(to="cpu")
+            return ev.nbytes
+
+        for kk in range(min(args.warmup, 2)):
+            e2e_step(kk)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for kk in range(args.e2e_steps):
+            d2h += e2e_step(kk + 2)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": round(px_frames_step * args.e2e_steps * ws / e2e_s / 1e6, 1),
+               "unit": "Mpixel-frames/s",
+               "h2d_bytes_per_step": 4 * px_frames_step,
+               "d2h_bytes_per_step": int(d2h / args.e2e_steps)}
+        sim2.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, dev)
+
+    if rank == 0:
+        clk = clocks.summary(tw0, tw1)
+        line = {
+            "metric": METRIC,
+            "value": round(value, 1),
+            "unit": "Mpixel-frames/s",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms / args.steps, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic (seeded procedural scenes rendered on the device)",
+            "config": {"workload": wl["name"], "width": W, "height": H, "frames_per_step": T,
+                       "dt_us": DT, "streams_per_gpu": 1,
+                       "parallelism": f"replicas x{ws} (independent sensor streams)",
+                       "l2": "inputs 4*T*H*W bytes per step, far larger than L2; no flush"},
+            "events_per_s": round(n_events_all / (ms / 1e3), 1),
+            "events_per_step": round(ev_per_step, 1),
+            "gpu_launches": launches,
+            "kernel_ms": {"emit": round(emit_ms, 4), "sort": round(sort_ms, 4)},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": None if traffic is None else int(traffic),
+                         "kernel": "emit_kernel", "peak_source": peak_src},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def _oracle_sample_frames(args, dev):
+    wl = WORKLOADS[args.workload]
+    n = min(args.cpu_frames, wl["dims"]["T"])
+    fr = wl["render"](seed=args.seed, device=dev if dev is not None else "cpu", n_frames=n)
+    return fr.cpu().numpy(), n
+
+
+def cpu_baseline(args, dev):
+    """The oracle as it stands (single thread) on the first frames of the workload."""
+    import oracle
+    wl = WORKLOADS[args.workload]
+    W, H = wl["dims"]["W"], wl["dims"]["H"]
+    fr, n = _oracle_sample_frames(args, dev)
+    sim = oracle.OracleSim(W, H, **{k: v for k, v in wl["sim"].items()})
+    t0 = time.perf_counter()
+    ev, _ = sim.step(fr, 0, DT)
+    s = time.perf_counter() - t0
+    px = n * W * H
+    return {"value": round(px / s / 1e6, 2), "unit": "Mpixel-frames/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"first {n} frames of the workload ({px} pixel-frames, {len(ev)} events), "
+                      f"single-threaded C oracle, {s:.1f} s"}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# --------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    wl = WORKLOADS[args.workload]
+    W, H = wl["dims"]["W"], wl["dims"]["H"]
+    dev = None
+    if torch.cuda.is_available():
+        dev = torch.device("cuda", local)
+    fr, n = _oracle_sample_frames(args, dev)
+    # size each step so that warm-up + timed steps take about two minutes
+    cal = oracle.OracleSim(W, H, **wl["sim"])
+    t0 = time.perf_counter()
+    cal.step(fr[: min(n, 9)], 0, DT)
+    per_frame = (time.perf_counter() - t0) / max(1, min(n, 9) - 1)
+    n = int(max(2, min(n, 120.0 / (args.steps + args.warmup) / max(per_frame, 1e-4))))
+    fr = np.ascontiguousarray(fr[:n])
+    sim = oracle.OracleSim(W, H, **wl["sim"])
+    t_next = 0
+    for _ in range(args.warmup):
+        sim.step(fr, t_next, DT)
+        t_next += n * DT
+    times, n_ev = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ev, _ = sim.step(fr, t_next, DT)
+        times.append(time.perf_counter() - t0)
+        n_ev += len(ev)
+        t_next += n * DT
+    s = sum(times)
+    px = n * W * H * args.steps
+    val = px / s / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 2), "unit": "Mpixel-frames/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * s / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded procedural scenes)",
+        "config": {"workload": wl["name"], "width": W, "height": H,
+                   "frames_per_step": n, "dt_us": DT,
+                   "sample": f"each step: {n} frames of the workload (bounded sample)"},
+        "events_per_s": round(n_ev / s, 1),
+        "cpu_baseline": {"value": round(val, 2), "unit": "Mpixel-frames/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"{n} frames x {args.steps} steps, single-threaded C oracle"},
+        "e2e": {"value": round(val, 2), "unit": "Mpixel-frames/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="hd")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-frames", type=int, default=480)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

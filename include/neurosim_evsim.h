@@ -154,6 +154,26 @@ int neurosim_evsim_get_thresholds(neurosim_evsim *h, float *c_pos, float *c_neg)
 /* Frees all device and host resources of the handle (synchronises first). */
 void neurosim_evsim_destroy(neurosim_evsim *h);
 
+/* Counters of a handle (all since create; replays after overflow included). */
+typedef struct neurosim_evsim_stats {
+    uint64_t steps;            /* step launches enqueued                        */
+    uint64_t kernel_launches;  /* CUDA kernels launched by the library           */
+    uint64_t px_frames;        /* pixel-frames processed by those steps          */
+    uint64_t events_drained;   /* records handed out by drains                   */
+    uint64_t timed_steps;      /* steps enqueued while profiling was on          */
+    double emit_ms;            /* summed emission-kernel time of timed steps     */
+    double sort_ms;            /* summed interval count + scan + sort time       */
+} neurosim_evsim_stats;
+
+/* Turns per-step timing on (1) or off (0).  When on, every step records CUDA
+ * events on the handle's stream around the emission kernel and around the
+ * interval sort; neurosim_evsim_get_stats sums them.  Leave off while
+ * capturing a CUDA graph. */
+int neurosim_evsim_set_profiling(neurosim_evsim *h, int32_t enable);
+
+/* Synchronises the handle's stream and fills *out. */
+int neurosim_evsim_get_stats(neurosim_evsim *h, neurosim_evsim_stats *out);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *neurosim_last_error(void);
 

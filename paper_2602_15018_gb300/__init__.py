@@ -1,0 +1,9 @@
+"""GB300-native event-generation path of Neurosim (arXiv 2602.15018).
+
+The compute path is the CUDA library libneurosim_evsim.so (C ABI in
+include/neurosim_evsim.h); this package only binds it.
+"""
+from .evsim import EventSim, device_log  # noqa: F401
+from ._lib import NeurosimError, lib  # noqa: F401
+
+__all__ = ["EventSim", "device_log", "NeurosimError", "lib"]

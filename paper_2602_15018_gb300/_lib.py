@@ -1,0 +1,111 @@
+"""ctypes declarations of libneurosim_evsim.so (C ABI: include/neurosim_evsim.h).
+
+Argument marshalling only: every step of the event path runs in the CUDA
+library.  Importing the binding never falls back to anything else: if the
+shared library is missing, `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libneurosim_evsim.so")
+
+NEUROSIM_OK = 0
+STATUS = {1: "E_INVALID", 2: "E_CUDA", 3: "E_TIME", 4: "E_OVERFLOW", 5: "E_TIMEOUT",
+          6: "E_NOMEM", 7: "E_STATE"}
+
+# Every exported function of the C ABI, by header section.
+EXPORTS = [
+    "neurosim_evsim_default_params", "neurosim_evsim_create", "neurosim_evsim_step",
+    "neurosim_evsim_step_host", "neurosim_evsim_pending", "neurosim_evsim_drain_events",
+    "neurosim_evsim_get_state", "neurosim_evsim_set_state", "neurosim_evsim_get_thresholds",
+    "neurosim_evsim_destroy", "neurosim_last_error", "neurosim_abi_version",
+    "neurosim_debug_log", "neurosim_evsim_set_profiling", "neurosim_evsim_get_stats",
+]
+
+
+class NeurosimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    """Mirror of neurosim_evsim_params."""
+    _fields_ = [
+        ("width", C.c_int32), ("height", C.c_int32),
+        ("c_pos", C.c_float), ("c_neg", C.c_float), ("sigma_c", C.c_float),
+        ("c_min", C.c_float), ("refractory_us", C.c_uint32), ("log_eps", C.c_float),
+        ("input_is_log", C.c_int32), ("seed", C.c_uint64),
+        ("c_pos_map", C.POINTER(C.c_float)), ("c_neg_map", C.POINTER(C.c_float)),
+        ("event_capacity", C.c_uint64), ("max_frames_per_step", C.c_int32),
+        ("max_pending_intervals", C.c_int32), ("threads_per_block", C.c_int32),
+        ("pipeline_stages", C.c_int32), ("reserved", C.c_int32 * 6),
+    ]
+
+
+class Stats(C.Structure):
+    """Mirror of neurosim_evsim_stats."""
+    _fields_ = [("steps", C.c_uint64), ("kernel_launches", C.c_uint64),
+                ("px_frames", C.c_uint64), ("events_drained", C.c_uint64),
+                ("timed_steps", C.c_uint64), ("emit_ms", C.c_double), ("sort_ms", C.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(
+                    f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; "
+                    "g.build()'` (needs nvcc)")
+            L = C.CDLL(LIB_PATH)
+            vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+            f32p, u32p = C.POINTER(C.c_float), C.POINTER(C.c_uint32)
+            L.neurosim_evsim_default_params.restype = None
+            L.neurosim_evsim_default_params.argtypes = [C.POINTER(Params)]
+            L.neurosim_evsim_create.restype = C.c_int
+            L.neurosim_evsim_create.argtypes = [C.POINTER(Params), vp, C.POINTER(vp)]
+            L.neurosim_evsim_step.restype = C.c_int
+            L.neurosim_evsim_step.argtypes = [vp, vp, i32, i64, i32]
+            L.neurosim_evsim_step_host.restype = C.c_int
+            L.neurosim_evsim_step_host.argtypes = [vp, vp, i32, i64, i32]
+            L.neurosim_evsim_pending.restype = C.c_int
+            L.neurosim_evsim_pending.argtypes = [vp, C.POINTER(u64), C.POINTER(i64)]
+            L.neurosim_evsim_drain_events.restype = C.c_int
+            L.neurosim_evsim_drain_events.argtypes = [vp, vp, u64, i32, C.POINTER(u64),
+                                                      C.POINTER(i64), i64, C.POINTER(i64)]
+            L.neurosim_evsim_get_state.restype = C.c_int
+            L.neurosim_evsim_get_state.argtypes = [vp, f32p, f32p, u32p, C.POINTER(i64),
+                                                   C.POINTER(i32)]
+            L.neurosim_evsim_set_state.restype = C.c_int
+            L.neurosim_evsim_set_state.argtypes = [vp, f32p, f32p, u32p, i64, i32]
+            L.neurosim_evsim_get_thresholds.restype = C.c_int
+            L.neurosim_evsim_get_thresholds.argtypes = [vp, f32p, f32p]
+            L.neurosim_evsim_destroy.restype = None
+            L.neurosim_evsim_destroy.argtypes = [vp]
+            L.neurosim_last_error.restype = C.c_char_p
+            L.neurosim_last_error.argtypes = []
+            L.neurosim_abi_version.restype = C.c_int32
+            L.neurosim_abi_version.argtypes = []
+            L.neurosim_debug_log.restype = C.c_int
+            L.neurosim_debug_log.argtypes = [vp, vp, i64, vp]
+            L.neurosim_evsim_set_profiling.restype = C.c_int
+            L.neurosim_evsim_set_profiling.argtypes = [vp, i32]
+            L.neurosim_evsim_get_stats.restype = C.c_int
+            L.neurosim_evsim_get_stats.argtypes = [vp, C.POINTER(Stats)]
+            _lib = L
+    return _lib
+
+
+def check(rc: int) -> None:
+    if rc != NEUROSIM_OK:
+        msg = lib().neurosim_last_error()
+        raise NeurosimError(rc, msg.decode() if msg else "")

@@ -1,0 +1,114 @@
+// Internal declarations shared by the kernels (evsim_kernels.cu) and the C-ABI
+// host code (evsim_api.cu) of libneurosim_evsim.so.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nsim {
+
+constexpr uint32_t kTlastNone = 0xFFFFFFFFu;   // "no event yet" marker of t_last
+constexpr uint32_t kNoChunk = 0xFFFFFFFFu;     // chunk not stored (page overflow)
+
+// Bits of Ctl::err.
+constexpr uint32_t kErrPageOverflow = 1u;   // intermediate key pages exhausted
+constexpr uint32_t kErrOutOverflow = 2u;    // output record buffer exhausted
+constexpr uint32_t kErrTimeout = 4u;        // a bounded mbarrier wait gave up
+
+constexpr int kPPT = 4;                  // pixels per thread (one 16-byte vector)
+constexpr int kMaxTilesPerStream = 8192; // chunk prefix of one segment fits in shared memory
+constexpr int kSortThreads = 512;
+constexpr int kMaxDigitBits = 6;         // radix digit width of the segment sort
+
+// Device control block of one simulator (or one batch).
+struct Ctl {
+    unsigned long long run_total;       // records written since the last drain (demand)
+    unsigned long long out_demand_max;  // largest run_total seen (for regrowth)
+    unsigned int page_ctr;              // key pages handed out in the current step
+    unsigned int page_demand_max;       // largest page_ctr over the steps since reset
+    unsigned int err;                   // kErr* bits
+    unsigned int pad;
+};
+
+// One sensor stream inside a step launch.
+struct StreamDesc {
+    const float* frames;          // [T][npix] FP32 (device)
+    const float* ref_in;          // per-pixel state read at the start of the step
+    const float* lprev_in;
+    const uint32_t* tlast_in;
+    float* ref_out;               // per-pixel state written at the end of the step
+    float* lprev_out;
+    uint32_t* tlast_out;
+    const float* cpos;            // per-pixel thresholds, or nullptr for uniform
+    const float* cneg;
+    float cpos_u, cneg_u;         // uniform thresholds (used when maps are null)
+    float log_eps;
+    int32_t input_is_log;
+    uint32_t refractory;          // us; 0 = off
+    int32_t W, npix;
+    int32_t n_tiles;              // work items (tiles) of this stream
+    int32_t item_base;            // index of its first work item in the launch
+    int32_t seg_base;             // index of its first segment in the launch
+    int32_t n_segs;               // intervals this stream closes in the step
+    int32_t init;                 // 1: frame 0 initialises the state
+    int32_t vec;                  // 1: frames 16-byte aligned rows -> bulk copies
+    int32_t pix_bits;             // bits of npix - 1 (>= 1)
+    int32_t D0;                   // length of the first interval (us)
+    int64_t ta0;                  // start time of the first interval (us)
+    int64_t chunk_base;           // chunk-table offset of (segment 0, tile 0)
+    int64_t out_seg_index;        // slot of segment 0 in the pending offset array
+};
+
+// Everything one step launch needs (passed by value as a __grid_constant__).
+struct StepLaunch {
+    const StreamDesc* streams_dev;  // device array when n_streams > 1
+    StreamDesc s0;                  // the stream when n_streams == 1
+    int32_t n_streams;
+    int32_t n_items;                // sum of n_tiles
+    int32_t n_segs;                 // sum of n_segs
+    int32_t T;                      // frames per stream in this step
+    int32_t dt;                     // us
+    int32_t key64;                  // 1: 64-bit intermediate keys
+    int32_t t_bits;                 // bits of the largest in-interval offset
+    int32_t threads;                // emission CTA size (128, 256, 512)
+    int32_t stages;                 // emission frame stages in shared memory
+    int32_t grid_emit;
+    int32_t grid_sort;
+    int32_t sort_smem;              // dynamic shared memory of the sort CTA
+    int32_t max_tiles;              // largest n_tiles over the streams
+    void* keys;                     // paged intermediate key buffer
+    uint32_t n_pages, page_keys;
+    void* temp;                     // sort scratch (same size as keys)
+    uint2* chunks;                  // [segments][tiles] (offset, count)
+    uint32_t* seg_count;            // [n_segs]
+    int64_t* seg_rel;               // [n_segs] start relative to this step's first record
+    int64_t* seg_abs;               // [n_segs] start in the output buffer
+    int64_t* seg_off_out;           // pending per-interval offsets (for the drain)
+    uint64_t* out;                  // output records
+    uint64_t out_cap;
+    Ctl* ctl;
+    cudaStream_t stream;
+    uint64_t wait_limit_ns;         // bound of every device-side wait
+    cudaEvent_t ev_begin;           // optional timing events (nullptr: none):
+    cudaEvent_t ev_emitted;         //   before emission, after emission,
+    cudaEvent_t ev_sorted;          //   after the interval sort
+};
+
+// Enqueues emission, segment count, segment scan and segment sort; adds the
+// number of kernels launched to *launches.
+cudaError_t launch_step(const StepLaunch& L, uint64_t* launches);
+
+// Emission launch geometry helpers.
+size_t emit_smem_bytes(int threads, int stages);
+cudaError_t emit_occupancy(int threads, int stages, int key64, int* blocks_per_sm);
+cudaError_t sort_configure(int* smem_bytes);
+
+// Create-time per-pixel thresholds: C+-_u = max(c_min, C+- + sigma * z+-_u).
+cudaError_t launch_threshold_maps(float* cpos, float* cneg, int64_t npix, float c_pos,
+                                  float c_neg, float sigma, float c_min, uint64_t seed,
+                                  cudaStream_t stream);
+
+// Debug/verification: y = library log(x).
+cudaError_t launch_debug_log(const float* x, float* y, int64_t n, cudaStream_t stream);
+
+}  // namespace nsim

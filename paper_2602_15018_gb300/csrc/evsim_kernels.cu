@@ -1,0 +1,947 @@
+// Event-generation kernels for sm_103a (GB300).
+//
+// Model: arXiv 2602.15018, Sec. 2 ("Neurosim simulates event cameras at
+// multi-kilohertz rates"): per-pixel state holding the level of the last
+// triggered event, contrast-threshold crossings, a variable number of events
+// per frame gathered with few global atomics.  Sec. 1 fixes the event tuple
+// (integer microsecond timestamp, pixel, polarity).
+//
+// Readings of the silent points (shared with the header's model statement):
+// L = log(clamp(I, 0, 1e6) + eps) with this file's FP32 log (or clamp(I, -32,
+// 32) for log input); linear interpolation of L between frames; one crossing
+// at a time with sequential FP32 adds (ref moves to the crossed level);
+// t = ta + floor(frac * D) with frac = (lvl - a) / (b - a) in FP32;
+// refractory suppression that still moves ref; output interval-major and
+// ascending by (t, y, x, p) inside an interval.
+//
+// Every floating-point operation of the model is an explicitly rounded
+// intrinsic (__fadd_rn, __fmul_rn, __fdiv_rn, __fmaf_rn) so that no compiler
+// contraction or approximation can change a result.
+//
+// Kernels of one step:
+//   emit_kernel     one CTA per tile of THREADS*4 contiguous pixels (grid
+//                   strided over tiles of all streams); the pixel state stays
+//                   in registers across all T frames; frames stream into a
+//                   ring of shared-memory stages by cp.async.bulk with an
+//                   mbarrier per stage; per frame a warp/block scan compacts
+//                   the events of the tile into one contiguous chunk of a
+//                   paged key buffer (one global atomic per page, not per
+//                   frame); chunk (offset, count) goes to a table indexed by
+//                   (interval, tile).
+//   seg_count       sums the chunk counts of each interval.
+//   seg_scan        exclusive scan of the interval sizes -> output offsets.
+//   sort_kernel     one CTA per interval: gathers the interval's chunks in
+//                   tile order (so pixel order), then a stable LSD radix sort
+//                   on the in-interval time offset in shared memory, writing
+//                   the packed 64-bit records in (t, y, x, p) order.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "evsim_internal.h"
+
+namespace nsim {
+namespace {
+
+// --------------------------------------------------------------------------
+// FP32 natural log used by the model (textbook atanh-series method):
+// x = m 2^e with m in [sqrt(1/2), sqrt(2)); s = (m - 1)/(m + 1);
+// log m = 2 (s + s^3/3 + s^5/5 + s^7/7 + s^9/9); log x = log m + e ln2, with
+// ln2 split into a 16-bit head (exact product with e) and a tail.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ float model_log(float x)
+{
+    if (!(x > 0.0f)) return (x == 0.0f) ? __int_as_float(0xff800000) : __int_as_float(0x7fc00000);
+    if (x == __int_as_float(0x7f800000)) return x;
+    int e = 0;
+    uint32_t bits = __float_as_uint(x);
+    if (bits < 0x00800000u) {                 // subnormal: scale by 2^24
+        x = __fmul_rn(x, 16777216.0f);
+        bits = __float_as_uint(x);
+        e = -24;
+    }
+    e += (int)(bits >> 23) - 127;
+    float m = __uint_as_float((bits & 0x007fffffu) | 0x3f800000u);
+    if (m > 0x1.6a09e6p+0f) {                 // sqrt(2) rounded to FP32
+        m = __fmul_rn(m, 0.5f);
+        e += 1;
+    }
+    const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float z = __fmul_rn(s, s);
+    float q = __fmaf_rn(z, 0x1.c71c72p-4f, 0x1.24924ap-3f);   // 1/9, 1/7
+    q = __fmaf_rn(z, q, 0x1.99999ap-3f);                       // 1/5
+    q = __fmaf_rn(z, q, 0x1.555556p-2f);                       // 1/3
+    const float s2 = __fadd_rn(s, s);
+    const float lm = __fmaf_rn(s2, __fmul_rn(z, q), s2);
+    const float fe = (float)e;
+    const float tail = __fmaf_rn(fe, 0x1.7f7d1cp-20f, lm);     // ln2 tail
+    return __fmaf_rn(fe, 0x1.62e4p-1f, tail);                   // ln2 head (16 bits)
+}
+
+__device__ __forceinline__ float to_log(float v, float eps, int is_log)
+{
+    if (is_log) return fminf(fmaxf(v, -32.0f), 32.0f);
+    return model_log(__fadd_rn(fminf(fmaxf(v, 0.0f), 1.0e6f), eps));
+}
+
+// Crossings of one pixel over one interval (a at ta, b at ta + D).  Advances
+// ref and t_last.  EMIT: writes one key per emitted event to out[].
+// Returns the number of emitted events.
+template <bool EMIT, typename KeyT>
+__device__ __forceinline__ int pixel_events(float& r, uint32_t& tl, float a, float b, float cp,
+                                            float cn, uint32_t ta, float Df, uint32_t R,
+                                            KeyT pixkey, int tshift, KeyT* out)
+{
+    int n = 0;
+    if (b > a) {
+        const float den = __fsub_rn(b, a);
+        for (;;) {
+            const float lvl = __fadd_rn(r, cp);
+            if (!(lvl <= b)) break;
+            const float frac = __fdiv_rn(__fsub_rn(lvl, a), den);
+            const float tf = fmaxf(floorf(__fmul_rn(frac, Df)), 0.0f);
+            const uint32_t toff = (uint32_t)tf;
+            const uint32_t t = ta + toff;
+            r = lvl;
+            if (R != 0u && tl != kTlastNone && (int64_t)t - (int64_t)tl < (int64_t)R) continue;
+            if (EMIT) out[n] = ((KeyT)toff << tshift) | pixkey | (KeyT)1;
+            ++n;
+            tl = t;
+        }
+    } else if (b < a) {
+        const float den = __fsub_rn(b, a);
+        for (;;) {
+            const float lvl = __fsub_rn(r, cn);
+            if (!(lvl >= b)) break;
+            const float frac = __fdiv_rn(__fsub_rn(lvl, a), den);
+            const float tf = fmaxf(floorf(__fmul_rn(frac, Df)), 0.0f);
+            const uint32_t toff = (uint32_t)tf;
+            const uint32_t t = ta + toff;
+            r = lvl;
+            if (R != 0u && tl != kTlastNone && (int64_t)t - (int64_t)tl < (int64_t)R) continue;
+            if (EMIT) out[n] = ((KeyT)toff << tshift) | pixkey;
+            ++n;
+            tl = t;
+        }
+    }
+    return n;
+}
+
+// --------------------------------------------------------------------------
+// mbarrier / bulk-copy helpers (inline PTX, sm_90+ forms valid on sm_103a)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase `parity` of `bar` to complete; gives up after limit_ns.
+__device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 31u) == 0u && global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// As above, with an absolute deadline on the global timer.
+__device__ __noinline__ bool mbar_wait_deadline(uint64_t* bar, uint32_t parity, uint64_t deadline)
+{
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 31u) == 31u && global_ns() > deadline) return false;
+    }
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size % 16 == 0),
+// completion signalled as transaction bytes on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar, uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ const StreamDesc* stream_of_item(const StepLaunch& L, int item)
+{
+    if (L.n_streams == 1) return &L.s0;
+    int lo = 0, hi = L.n_streams - 1;            // last stream with item_base <= item
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.streams_dev[mid].item_base <= item) lo = mid; else hi = mid - 1;
+    }
+    return &L.streams_dev[lo];
+}
+
+__device__ __forceinline__ const StreamDesc* stream_of_seg(const StepLaunch& L, int seg)
+{
+    if (L.n_streams == 1) return &L.s0;
+    int lo = 0, hi = L.n_streams - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.streams_dev[mid].seg_base <= seg) lo = mid; else hi = mid - 1;
+    }
+    return &L.streams_dev[lo];
+}
+
+__device__ __forceinline__ int64_t interval_start(const StreamDesc& sd, int j, int dt)
+{
+    return sd.ta0 + (j == 0 ? 0 : (int64_t)sd.D0 + (int64_t)(j - 1) * dt);
+}
+
+// --------------------------------------------------------------------------
+// Emission kernel
+// --------------------------------------------------------------------------
+template <int THREADS, typename KeyT>
+__global__ void __launch_bounds__(THREADS) emit_kernel(const __grid_constant__ StepLaunch L)
+{
+    constexpr int TILE = THREADS * kPPT;
+    constexpr int NW = THREADS / 32;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* stage_buf = reinterpret_cast<float*>(smem_raw);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)L.stages * TILE * sizeof(float));
+    __shared__ int s_wtot[NW];
+    __shared__ int s_wexcl[NW];
+    __shared__ uint32_t s_base;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int S = L.stages;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&mbar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    KeyT* const keys = reinterpret_cast<KeyT*>(L.keys);
+    const uint64_t pol = l2_evict_first_policy();
+    uint32_t use = 0;                 // stage uses so far (drives stage index and parity)
+    uint32_t pg_cur = 0, pg_end = 0;  // thread 0: free range of the current key page
+
+    for (int item = blockIdx.x; item < L.n_items; item += gridDim.x) {
+        const StreamDesc* sdp = stream_of_item(L, item);
+        const float* frames = sdp->frames;
+        const int npix = sdp->npix;
+        const int W = sdp->W;
+        (void)W;
+        const int tile = item - sdp->item_base;
+        const int p0 = tile * TILE;
+        const int np = min(TILE, npix - p0);
+        const int my0 = tid * kPPT;
+        const int nv = max(0, min(kPPT, np - my0));
+        const int pix0 = p0 + my0;
+        const int init = sdp->init;
+        const int vec = sdp->vec;
+        const int is_log = sdp->input_is_log;
+        const float eps = sdp->log_eps;
+        const uint32_t R = sdp->refractory;
+        const int tshift = sdp->pix_bits + 1;
+        const int T = L.T;
+        const int64_t chunk_row0 = sdp->chunk_base + tile;
+        const int n_tiles = sdp->n_tiles;
+
+        float ref[kPPT], lp[kPPT], cp[kPPT], cn[kPPT];
+        uint32_t tl[kPPT];
+#pragma unroll
+        for (int k = 0; k < kPPT; ++k) {
+            ref[k] = 0.0f; lp[k] = 0.0f; tl[k] = kTlastNone;
+            cp[k] = sdp->cpos_u; cn[k] = sdp->cneg_u;
+        }
+        if (nv == kPPT) {
+            if (!init) {
+                const float4 r4 = *reinterpret_cast<const float4*>(sdp->ref_in + pix0);
+                const float4 l4 = *reinterpret_cast<const float4*>(sdp->lprev_in + pix0);
+                const uint4 t4 = *reinterpret_cast<const uint4*>(sdp->tlast_in + pix0);
+                ref[0] = r4.x; ref[1] = r4.y; ref[2] = r4.z; ref[3] = r4.w;
+                lp[0] = l4.x; lp[1] = l4.y; lp[2] = l4.z; lp[3] = l4.w;
+                tl[0] = t4.x; tl[1] = t4.y; tl[2] = t4.z; tl[3] = t4.w;
+            }
+            if (sdp->cpos != nullptr) {
+                const float4 a4 = *reinterpret_cast<const float4*>(sdp->cpos + pix0);
+                const float4 b4 = *reinterpret_cast<const float4*>(sdp->cneg + pix0);
+                cp[0] = a4.x; cp[1] = a4.y; cp[2] = a4.z; cp[3] = a4.w;
+                cn[0] = b4.x; cn[1] = b4.y; cn[2] = b4.z; cn[3] = b4.w;
+            }
+        } else {
+            for (int k = 0; k < nv; ++k) {
+                if (!init) {
+                    ref[k] = sdp->ref_in[pix0 + k];
+                    lp[k] = sdp->lprev_in[pix0 + k];
+                    tl[k] = sdp->tlast_in[pix0 + k];
+                }
+                if (sdp->cpos != nullptr) {
+                    cp[k] = sdp->cpos[pix0 + k];
+                    cn[k] = sdp->cneg[pix0 + k];
+                }
+            }
+        }
+
+        // pipeline prologue: frames 0 .. S-1 of this tile into the stage ring
+        const uint32_t tile_bytes = (uint32_t)np * (uint32_t)sizeof(float);
+        if (vec && tid == 0) {
+            const int pre = min(S, T);
+            for (int f = 0; f < pre; ++f) {
+                const uint32_t u = use + (uint32_t)f;
+                const int st = (int)(u % (uint32_t)S);
+                mbar_expect_tx(&mbar[st], tile_bytes);
+                bulk_g2s(stage_buf + (size_t)st * TILE, frames + (int64_t)f * npix + p0, tile_bytes,
+                         &mbar[st], pol);
+            }
+        }
+
+        bool aborted = false;
+        int abort_f = 0;
+        for (int f = 0; f < T; ++f) {
+            float v[kPPT] = {0.0f, 0.0f, 0.0f, 0.0f};
+            bool ok = true;
+            if (vec) {
+                const uint32_t u = use + (uint32_t)f;
+                const int st = (int)(u % (uint32_t)S);
+                ok = mbar_wait_bounded(&mbar[st], (u / (uint32_t)S) & 1u, L.wait_limit_ns);
+                if (ok && nv > 0) {
+                    const float4 q =
+                        *reinterpret_cast<const float4*>(stage_buf + (size_t)st * TILE + my0);
+                    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+                }
+            } else {
+                const float* src = frames + (int64_t)f * npix + pix0;
+                for (int k = 0; k < nv; ++k) v[k] = __ldcs(src + k);
+            }
+
+            float Lv[kPPT];
+#pragma unroll
+            for (int k = 0; k < kPPT; ++k) Lv[k] = to_log(v[k], eps, is_log);
+
+            const bool closes = !(init && f == 0);
+            const int j = f - init;                     // interval index when closes
+            const int D = (j == 0) ? sdp->D0 : L.dt;
+            const float Df = (float)D;
+            const uint32_t ta = closes ? (uint32_t)interval_start(*sdp, j, L.dt) : 0u;
+
+            float r0[kPPT];
+            uint32_t tl0[kPPT];
+            int cnt = 0;
+            if (!closes) {
+#pragma unroll
+                for (int k = 0; k < kPPT; ++k) {
+                    if (k < nv) { ref[k] = Lv[k]; lp[k] = Lv[k]; tl[k] = kTlastNone; }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kPPT; ++k) {
+                    r0[k] = ref[k];
+                    tl0[k] = tl[k];
+                    if (k < nv)
+                        cnt += pixel_events<false, KeyT>(ref[k], tl[k], lp[k], Lv[k], cp[k], cn[k],
+                                                         ta, Df, R, (KeyT)0, tshift, nullptr);
+                }
+            }
+
+            // warp inclusive scan of the per-thread counts
+            int incl = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int nb = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += nb;
+            }
+            if (lane == 31) s_wtot[warp] = incl;
+
+            if (__syncthreads_or(!ok)) { aborted = true; abort_f = f; break; }   // barrier A
+
+            if (vec && tid == 0 && f + S < T) {      // refill the stage just consumed
+                const uint32_t u = use + (uint32_t)f;
+                const int st = (int)(u % (uint32_t)S);
+                fence_proxy_async_smem();
+                mbar_expect_tx(&mbar[st], tile_bytes);
+                bulk_g2s(stage_buf + (size_t)st * TILE, frames + (int64_t)(f + S) * npix + p0,
+                         tile_bytes, &mbar[st], pol);
+            }
+
+            if (closes) {
+                if (warp == 0) {
+                    const int w = (lane < NW) ? s_wtot[lane] : 0;
+                    int wi = w;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int nb = __shfl_up_sync(0xffffffffu, wi, d);
+                        if (lane >= d) wi += nb;
+                    }
+                    if (lane < NW) s_wexcl[lane] = wi - w;
+                    const int total = __shfl_sync(0xffffffffu, wi, 31);
+                    if (lane == 0) {
+                        uint32_t base = kNoChunk;
+                        if (total > 0) {
+                            if (pg_end - pg_cur >= (uint32_t)total) {
+                                base = pg_cur;
+                                pg_cur += (uint32_t)total;
+                            } else {
+                                const uint32_t k = ((uint32_t)total + L.page_keys - 1u) / L.page_keys;
+                                const uint32_t first = atomicAdd(&L.ctl->page_ctr, k);
+                                if ((uint64_t)first + k <= (uint64_t)L.n_pages) {
+                                    base = first * L.page_keys;
+                                    pg_cur = base + (uint32_t)total;
+                                    pg_end = (first + k) * L.page_keys;
+                                } else {
+                                    atomicOr(&L.ctl->err, kErrPageOverflow);
+                                    pg_cur = pg_end = 0u;
+                                }
+                            }
+                        }
+                        L.chunks[chunk_row0 + (int64_t)j * n_tiles] =
+                            make_uint2(base == kNoChunk ? 0u : base,
+                                       base == kNoChunk ? 0u : (uint32_t)total);
+                        s_base = base;
+                    }
+                }
+                __syncthreads();                                       // barrier B
+                const uint32_t base = s_base;
+                if (cnt > 0 && base != kNoChunk) {
+                    KeyT* out = keys + (size_t)base + (size_t)(s_wexcl[warp] + incl - cnt);
+                    int w = 0;
+#pragma unroll
+                    for (int k = 0; k < kPPT; ++k) {
+                        if (k < nv) {
+                            float rr = r0[k];
+                            uint32_t tt = tl0[k];
+                            w += pixel_events<true, KeyT>(rr, tt, lp[k], Lv[k], cp[k], cn[k], ta, Df,
+                                                          R, (KeyT)(pix0 + k) << 1, tshift, out + w);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kPPT; ++k) lp[k] = Lv[k];
+            }
+        }
+
+        if (aborted) {
+            // Copies of frames [abort_f, min(T, abort_f + S)) may still be in
+            // flight into this CTA's stages: give them one bounded window to
+            // land before the CTA exits, then report the timeout.
+            if (tid == 0) {
+                atomicOr(&L.ctl->err, kErrTimeout);
+                if (vec) {
+                    const uint64_t deadline = global_ns() + L.wait_limit_ns;
+                    for (int fr = abort_f; fr < min(T, abort_f + S); ++fr) {
+                        const uint32_t u = use + (uint32_t)fr;
+                        if (!mbar_wait_deadline(&mbar[u % (uint32_t)S], (u / (uint32_t)S) & 1u, deadline))
+                            break;
+                    }
+                }
+            }
+            __syncthreads();
+            return;
+        }
+        if (vec) use += (uint32_t)T;
+
+        if (nv == kPPT) {
+            *reinterpret_cast<float4*>(sdp->ref_out + pix0) = make_float4(ref[0], ref[1], ref[2], ref[3]);
+            *reinterpret_cast<float4*>(sdp->lprev_out + pix0) = make_float4(lp[0], lp[1], lp[2], lp[3]);
+            *reinterpret_cast<uint4*>(sdp->tlast_out + pix0) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
+        } else {
+            for (int k = 0; k < nv; ++k) {
+                sdp->ref_out[pix0 + k] = ref[k];
+                sdp->lprev_out[pix0 + k] = lp[k];
+                sdp->tlast_out[pix0 + k] = tl[k];
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Segment sizes and offsets
+// --------------------------------------------------------------------------
+__global__ void seg_count_kernel(const __grid_constant__ StepLaunch L)
+{
+    const int warps = blockDim.x >> 5;
+    const int seg = blockIdx.x * warps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (seg >= L.n_segs) return;
+    const StreamDesc* sdp = stream_of_seg(L, seg);
+    const int j = seg - sdp->seg_base;
+    const uint2* row = L.chunks + sdp->chunk_base + (int64_t)j * sdp->n_tiles;
+    uint32_t s = 0;
+    for (int i = lane; i < sdp->n_tiles; i += 32) s += row[i].y;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (lane == 0) L.seg_count[seg] = s;
+}
+
+// Single CTA: exclusive scan of segment sizes; appends the step's records
+// after the ones pending from earlier steps.
+__global__ void __launch_bounds__(1024) seg_scan_kernel(const __grid_constant__ StepLaunch L)
+{
+    __shared__ unsigned long long s_w[32];
+    __shared__ unsigned long long s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned long long base = L.ctl->run_total;
+    if (tid == 0) s_carry = 0ull;
+    __syncthreads();
+    for (int c0 = 0; c0 < L.n_segs; c0 += 1024) {
+        const int seg = c0 + tid;
+        const unsigned long long v = (seg < L.n_segs) ? L.seg_count[seg] : 0ull;
+        unsigned long long incl = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long nb = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += nb;
+        }
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = s_w[lane], wi = w;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long nb = __shfl_up_sync(0xffffffffu, wi, d);
+                if (lane >= d) wi += nb;
+            }
+            s_w[lane] = wi - w;
+        }
+        __syncthreads();
+        const unsigned long long rel = s_carry + s_w[warp] + incl - v;
+        if (seg < L.n_segs) {
+            L.seg_rel[seg] = (int64_t)rel;
+            L.seg_abs[seg] = (int64_t)(base + rel);
+            const StreamDesc* sdp = stream_of_seg(L, seg);
+            L.seg_off_out[sdp->out_seg_index + (seg - sdp->seg_base)] = (int64_t)(base + rel);
+        }
+        __syncthreads();
+        if (tid == 1023) s_carry = rel + v;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        Ctl* c = L.ctl;
+        const unsigned long long total = base + s_carry;
+        c->run_total = total;
+        if (total > c->out_demand_max) c->out_demand_max = total;
+        if (total > L.out_cap) c->err |= kErrOutOverflow;
+        if (c->page_ctr > c->page_demand_max) c->page_demand_max = c->page_ctr;
+        c->page_ctr = 0u;                      // pages are free again for the next step
+    }
+}
+
+// --------------------------------------------------------------------------
+// Per-interval stable LSD radix sort on the time offset
+// --------------------------------------------------------------------------
+template <typename KeyT>
+struct ChunkSrc {          // logical key i of the interval, gathered from its chunks
+    const KeyT* keys;
+    const uint32_t* cpre;  // shared: exclusive prefix of chunk counts, nt + 1 entries
+    const uint32_t* coff;  // shared: page offset of each chunk
+    int nt;
+    __device__ __forceinline__ KeyT operator()(uint32_t i) const
+    {
+        int lo = 0, hi = nt - 1;                 // last chunk with cpre <= i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cpre[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        return keys[(size_t)coff[lo] + (i - cpre[lo])];
+    }
+};
+
+template <typename KeyT>
+struct ArraySrc {
+    const KeyT* p;
+    __device__ __forceinline__ KeyT operator()(uint32_t i) const { return p[i]; }
+};
+
+struct RecordSink {        // final pass: packed 64-bit records
+    uint64_t* out;
+    uint32_t ta;
+    int W;
+    int tshift;
+    uint32_t pixmask;
+    template <typename KeyT>
+    __device__ __forceinline__ void put(uint32_t pos, KeyT key) const
+    {
+        const uint32_t toff = (uint32_t)(key >> tshift);
+        const uint32_t pix = (uint32_t)(key >> 1) & pixmask;
+        const uint32_t y = pix / (uint32_t)W;
+        const uint32_t x = pix - y * (uint32_t)W;
+        out[pos] = ((uint64_t)(ta + toff) << 32) | ((uint64_t)y << 17) | ((uint64_t)x << 1) |
+                   (uint64_t)(key & (KeyT)1);
+    }
+};
+
+template <typename KeyT>
+struct KeySink {
+    KeyT* p;
+    __device__ __forceinline__ void put(uint32_t pos, KeyT key) const { p[pos] = key; }
+};
+
+// One stable counting pass of the CTA over [0, N): digit = (key >> shift) & (NB-1).
+// Warp w owns the contiguous range [w N / NW, (w+1) N / NW); inside a warp,
+// groups of 32 consecutive keys are ranked with match_any, so the pass keeps
+// the input order of equal digits.
+template <int THREADS, typename KeyT, typename Src, typename Sink>
+__device__ __forceinline__ void radix_pass(const Src& src, const Sink& sink, uint32_t N, int shift,
+                                           int NB, uint32_t* hist /*[NW][64]*/, uint32_t* binbase)
+{
+    constexpr int NW = THREADS / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lo = (uint32_t)(((uint64_t)N * warp) / NW);
+    const uint32_t hi = (uint32_t)(((uint64_t)N * (warp + 1)) / NW);
+    uint32_t* h = hist + warp * 64;
+    for (int d = lane; d < 64; d += 32) h[d] = 0u;
+    __syncwarp();
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t g = lo; g < hi; g += 32) {
+        const uint32_t i = g + lane;
+        const bool act = i < hi;
+        const unsigned m = __ballot_sync(0xffffffffu, act);
+        if (act) {
+            const KeyT key = src(i);
+            const uint32_t d = (uint32_t)(key >> shift) & (uint32_t)(NB - 1);
+            const unsigned peers = __match_any_sync(m, d);
+            if ((peers & lt) == 0u) h[d] += (uint32_t)__popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    if (tid < NB) {
+        uint32_t run = 0;
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t c = hist[w * 64 + tid];
+            hist[w * 64 + tid] = run;
+            run += c;
+        }
+        binbase[tid] = run;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t a = (lane < NB) ? binbase[lane] : 0u;
+        const uint32_t b = (lane + 32 < NB) ? binbase[lane + 32] : 0u;
+        uint32_t ia = a;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t nb = __shfl_up_sync(0xffffffffu, ia, d);
+            if (lane >= d) ia += nb;
+        }
+        const uint32_t tot_a = __shfl_sync(0xffffffffu, ia, 31);
+        uint32_t ib = b;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t nb = __shfl_up_sync(0xffffffffu, ib, d);
+            if (lane >= d) ib += nb;
+        }
+        __syncwarp();
+        if (lane < NB) binbase[lane] = ia - a;
+        if (lane + 32 < NB) binbase[lane + 32] = tot_a + ib - b;
+    }
+    __syncthreads();
+    for (uint32_t g = lo; g < hi; g += 32) {
+        const uint32_t i = g + lane;
+        const bool act = i < hi;
+        const unsigned m = __ballot_sync(0xffffffffu, act);
+        KeyT key = 0;
+        uint32_t d = 0;
+        unsigned peers = 0;
+        if (act) {
+            key = src(i);
+            d = (uint32_t)(key >> shift) & (uint32_t)(NB - 1);
+            peers = __match_any_sync(m, d);
+            const uint32_t pos = binbase[d] + h[d] + (uint32_t)__popc(peers & lt);
+            sink.put(pos, key);
+        }
+        __syncwarp();
+        if (act && (peers & lt) == 0u) h[d] += (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(kSortThreads) sort_kernel(const __grid_constant__ StepLaunch L)
+{
+    constexpr int THREADS = kSortThreads;
+    constexpr int NW = THREADS / 32;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int maxnt = L.max_tiles;
+    const int cpre_len = (maxnt + 1 + 3) & ~3;                       // keep 16-byte alignment
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem_raw);         // NW * 64
+    uint32_t* binbase = hist + NW * 64;                               // 64
+    uint32_t* cpre = binbase + 64;                                    // maxnt + 1
+    uint32_t* coff = cpre + cpre_len;                                 // maxnt
+    KeyT* sbuf = reinterpret_cast<KeyT*>(coff + cpre_len);
+    const size_t fixed = (size_t)(NW * 64 + 64 + 2 * cpre_len) * sizeof(uint32_t);
+    const uint32_t cap = (L.sort_smem > (int)fixed)
+                             ? (uint32_t)(((size_t)L.sort_smem - fixed) / sizeof(KeyT)) : 0u;
+
+    const int tid = threadIdx.x;
+    const int tb = L.t_bits;
+    const int npass = (tb + kMaxDigitBits - 1) / kMaxDigitBits;
+    const int bits = (tb + npass - 1) / npass;
+    const int NB = 1 << bits;
+
+    for (int seg = blockIdx.x; seg < L.n_segs; seg += gridDim.x) {
+        const uint32_t N = L.seg_count[seg];
+        const int64_t abs0 = L.seg_abs[seg];
+        if (N == 0u || (uint64_t)abs0 + N > L.out_cap) continue;    // overflow flagged by scan
+        const StreamDesc* sdp = stream_of_seg(L, seg);
+        const int j = seg - sdp->seg_base;
+        const int nt = sdp->n_tiles;
+        const uint2* row = L.chunks + sdp->chunk_base + (int64_t)j * nt;
+
+        // exclusive prefix of the chunk counts (tile order = pixel order)
+        __shared__ uint32_t s_carry;
+        __shared__ uint32_t s_w[NW];
+        if (tid == 0) s_carry = 0u;
+        __syncthreads();
+        for (int c0 = 0; c0 < nt; c0 += THREADS) {
+            const int c = c0 + tid;
+            uint2 e = make_uint2(0u, 0u);
+            if (c < nt) e = row[c];
+            uint32_t incl = e.y;
+            const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t nb = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += nb;
+            }
+            if (lane == 31) s_w[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t w = (lane < NW) ? s_w[lane] : 0u;
+                uint32_t wi = w;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t nb = __shfl_up_sync(0xffffffffu, wi, d);
+                    if (lane >= d) wi += nb;
+                }
+                if (lane < NW) s_w[lane] = wi - w;
+            }
+            __syncthreads();
+            const uint32_t ex = s_carry + s_w[warp] + incl - e.y;
+            if (c < nt) { cpre[c] = ex; coff[c] = e.x; }
+            __syncthreads();
+            if (tid == THREADS - 1) s_carry = ex + e.y;
+            __syncthreads();
+        }
+        if (tid == 0) cpre[nt] = s_carry;
+        __syncthreads();
+
+        const int tshift = sdp->pix_bits + 1;
+        const uint32_t ta = (uint32_t)interval_start(*sdp, j, L.dt);
+        const RecordSink rsink{L.out + abs0, ta, sdp->W, tshift, (1u << sdp->pix_bits) - 1u};
+        const bool fit = (npass <= 2) ? (N <= cap) : (2u * N <= cap);
+        KeyT* X = fit ? sbuf : reinterpret_cast<KeyT*>(L.temp) + L.seg_rel[seg];
+        KeyT* Y = fit ? sbuf + N : reinterpret_cast<KeyT*>(L.out + abs0);
+        const ChunkSrc<KeyT> csrc{reinterpret_cast<const KeyT*>(L.keys), cpre, coff, nt};
+
+        if (npass == 1) {
+            radix_pass<THREADS, KeyT>(csrc, rsink, N, tshift, NB, hist, binbase);
+        } else {
+            // pass p writes to X when (npass - 2 - p) is even, else to Y; last pass -> records
+            KeyT* dst0 = ((npass - 2) % 2 == 0) ? X : Y;
+            radix_pass<THREADS, KeyT>(csrc, KeySink<KeyT>{dst0}, N, tshift, NB, hist, binbase);
+            KeyT* cur = dst0;
+            for (int p = 1; p < npass - 1; ++p) {
+                KeyT* dst = ((npass - 2 - p) % 2 == 0) ? X : Y;
+                radix_pass<THREADS, KeyT>(ArraySrc<KeyT>{cur}, KeySink<KeyT>{dst}, N,
+                                          tshift + p * bits, NB, hist, binbase);
+                cur = dst;
+            }
+            radix_pass<THREADS, KeyT>(ArraySrc<KeyT>{cur}, rsink, N, tshift + (npass - 1) * bits,
+                                      NB, hist, binbase);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Create-time thresholds and the log check kernel
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1ull) * 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// Irwin-Hall(12) normal: twelve 20-bit uniforms summed, minus 6 * 2^20, times 2^-20.
+__device__ __forceinline__ float normal_ih12(uint64_t seed, uint64_t slot)
+{
+    int64_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc += (int64_t)(splitmix64_at(seed, slot * 12ull + (uint64_t)k) >> 44);
+    return __fmul_rn((float)(acc - 6ll * (1ll << 20)), 0x1p-20f);
+}
+
+__global__ void threshold_kernel(float* cpos, float* cneg, int64_t npix, float c_pos, float c_neg,
+                                 float sigma, float c_min, uint64_t seed)
+{
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < npix;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        float vp = c_pos, vn = c_neg;
+        if (sigma != 0.0f) {
+            vp = __fadd_rn(c_pos, __fmul_rn(sigma, normal_ih12(seed, (uint64_t)u * 2ull)));
+            vn = __fadd_rn(c_neg, __fmul_rn(sigma, normal_ih12(seed, (uint64_t)u * 2ull + 1ull)));
+        }
+        cpos[u] = fmaxf(c_min, vp);
+        cneg[u] = fmaxf(c_min, vn);
+    }
+}
+
+__global__ void debug_log_kernel(const float* x, float* y, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = model_log(x[i]);
+}
+
+template <int THREADS>
+cudaError_t launch_emit_t(const StepLaunch& L, size_t smem)
+{
+    if (L.key64) {
+        auto k = emit_kernel<THREADS, uint64_t>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<L.grid_emit, THREADS, smem, L.stream>>>(L);
+    } else {
+        auto k = emit_kernel<THREADS, uint32_t>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<L.grid_emit, THREADS, smem, L.stream>>>(L);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t emit_smem_bytes(int threads, int stages)
+{
+    return (size_t)stages * threads * kPPT * sizeof(float) + (size_t)stages * sizeof(uint64_t);
+}
+
+cudaError_t emit_occupancy(int threads, int stages, int key64, int* blocks_per_sm)
+{
+    const size_t smem = emit_smem_bytes(threads, stages);
+    const void* fn = nullptr;
+#define NSIM_PICK(TH)                                                                      \
+    if (threads == TH)                                                                     \
+        fn = key64 ? (const void*)emit_kernel<TH, uint64_t> : (const void*)emit_kernel<TH, uint32_t>;
+    NSIM_PICK(128) NSIM_PICK(256) NSIM_PICK(512)
+#undef NSIM_PICK
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
+}
+
+cudaError_t sort_configure(int* smem_bytes)
+{
+    // two sort CTAs per SM: ~113 KB of shared memory each
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    int want = 113 * 1024;
+    if (want > optin) want = optin;
+    e = cudaFuncSetAttribute(sort_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sort_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    if (e != cudaSuccess) return e;
+    *smem_bytes = want;
+    return cudaSuccess;
+}
+
+cudaError_t launch_step(const StepLaunch& L, uint64_t* launches)
+{
+    cudaError_t e = cudaSuccess;
+    if (L.ev_begin && (e = cudaEventRecord(L.ev_begin, L.stream)) != cudaSuccess) return e;
+    const size_t smem = emit_smem_bytes(L.threads, L.stages);
+    switch (L.threads) {
+    case 128: e = launch_emit_t<128>(L, smem); break;
+    case 256: e = launch_emit_t<256>(L, smem); break;
+    case 512: e = launch_emit_t<512>(L, smem); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    *launches += 1;
+    if (L.ev_emitted && (e = cudaEventRecord(L.ev_emitted, L.stream)) != cudaSuccess) return e;
+    if (L.n_segs > 0) {
+        const int wpb = 8;
+        seg_count_kernel<<<(L.n_segs + wpb - 1) / wpb, wpb * 32, 0, L.stream>>>(L);
+        seg_scan_kernel<<<1, 1024, 0, L.stream>>>(L);
+        if (L.key64)
+            sort_kernel<uint64_t><<<L.grid_sort, kSortThreads, L.sort_smem, L.stream>>>(L);
+        else
+            sort_kernel<uint32_t><<<L.grid_sort, kSortThreads, L.sort_smem, L.stream>>>(L);
+        *launches += 3;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (L.ev_sorted && (e = cudaEventRecord(L.ev_sorted, L.stream)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_threshold_maps(float* cpos, float* cneg, int64_t npix, float c_pos, float c_neg,
+                                  float sigma, float c_min, uint64_t seed, cudaStream_t stream)
+{
+    const int threads = 256;
+    int64_t blocks = (npix + threads - 1) / threads;
+    if (blocks > 65535) blocks = 65535;
+    threshold_kernel<<<(unsigned)blocks, threads, 0, stream>>>(cpos, cneg, npix, c_pos, c_neg, sigma,
+                                                                c_min, seed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_log(const float* x, float* y, int64_t n, cudaStream_t stream)
+{
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256;
+    int64_t blocks = (n + threads - 1) / threads;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    debug_log_kernel<<<(unsigned)blocks, threads, 0, stream>>>(x, y, n);
+    return cudaGetLastError();
+}
+
+}  // namespace nsim

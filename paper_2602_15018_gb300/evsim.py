@@ -1,0 +1,189 @@
+"""Python face of the event simulator: one `EventSim` per sensor.
+
+Thin wrapper over the C ABI (include/neurosim_evsim.h): it turns tensors into
+pointers and sizes and keeps the frames of pending steps alive until the
+drain (the library may replay them after a buffer overflow).  PyTorch only
+supplies device memory and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from ._lib import Params, Stats, check, lib
+
+
+class EventSim:
+    """Contrast-threshold DVS simulator for one sensor (arXiv 2602.15018, Sec. 2).
+
+    step(frames, t0_us, dt_us) enqueues frames [T, H, W] (FP32, CUDA, contiguous)
+    at times t0 + f dt; drain() returns the events of all pending steps as
+    packed uint64 records ([63:32] t | [31:17] y | [16:1] x | [0] p) in
+    interval-major (t, y, x, p) order, plus per-interval offsets.
+    """
+
+    def __init__(self, width: int, height: int, c_pos: float = 0.2, c_neg: float = 0.2,
+                 sigma_c: float = 0.0, c_min: float = 0.01, refractory_us: int = 0,
+                 log_eps: float = 1e-3, input_is_log: bool = False, seed: int = 0,
+                 c_pos_map=None, c_neg_map=None, event_capacity: int = 0,
+                 max_frames_per_step: int = 0, max_pending_intervals: int = 0,
+                 threads_per_block: int = 0, pipeline_stages: int = 0,
+                 stream: torch.cuda.Stream | None = None, device=None):
+        L = lib()
+        self.W, self.H = int(width), int(height)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        p = Params()
+        L.neurosim_evsim_default_params(C.byref(p))
+        p.width, p.height = self.W, self.H
+        p.c_pos, p.c_neg, p.sigma_c, p.c_min = c_pos, c_neg, sigma_c, c_min
+        p.refractory_us = int(refractory_us)
+        p.log_eps = log_eps
+        p.input_is_log = int(bool(input_is_log))
+        p.seed = int(seed)
+        keep = []
+        if c_pos_map is not None:
+            cp = np.ascontiguousarray(c_pos_map, np.float32).reshape(-1)
+            cn = np.ascontiguousarray(c_neg_map, np.float32).reshape(-1)
+            keep += [cp, cn]
+            p.c_pos_map = cp.ctypes.data_as(C.POINTER(C.c_float))
+            p.c_neg_map = cn.ctypes.data_as(C.POINTER(C.c_float))
+        p.event_capacity = int(event_capacity)
+        p.max_frames_per_step = int(max_frames_per_step)
+        p.max_pending_intervals = int(max_pending_intervals)
+        p.threads_per_block = int(threads_per_block)
+        p.pipeline_stages = int(pipeline_stages)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream()
+            h = C.c_void_p()
+            check(L.neurosim_evsim_create(C.byref(p), C.c_void_p(self.stream.cuda_stream),
+                                          C.byref(h)))
+        self._h = h
+        self._keep = []          # frames of pending steps (replayed on overflow)
+
+    # ------------------------------------------------------------------ steps
+    def step(self, frames: torch.Tensor, t0_us: int, dt_us: int) -> None:
+        if not (frames.is_cuda and frames.dtype == torch.float32 and frames.is_contiguous()):
+            raise ValueError("frames must be a contiguous float32 CUDA tensor [T, H, W]")
+        T = frames.numel() // (self.W * self.H)
+        if T * self.W * self.H != frames.numel():
+            raise ValueError("frames size is not a multiple of H*W")
+        check(lib().neurosim_evsim_step(self._h, C.c_void_p(frames.data_ptr()), T, int(t0_us),
+                                        int(dt_us)))
+        self._keep.append(frames)
+
+    def step_host(self, frames, t0_us: int, dt_us: int) -> None:
+        """Step from HOST frames (numpy or CPU tensor, float32, C-contiguous)."""
+        if isinstance(frames, torch.Tensor):
+            if frames.is_cuda or frames.dtype != torch.float32 or not frames.is_contiguous():
+                raise ValueError("host frames must be a contiguous float32 CPU tensor")
+            ptr = frames.data_ptr()
+            n = frames.numel()
+        else:
+            if frames.dtype != np.float32 or not frames.flags["C_CONTIGUOUS"]:
+                raise ValueError("host frames must be C-contiguous float32")
+            ptr = frames.ctypes.data
+            n = frames.size
+        T = n // (self.W * self.H)
+        check(lib().neurosim_evsim_step_host(self._h, C.c_void_p(ptr), T, int(t0_us), int(dt_us)))
+        self._keep.append(frames)
+
+    # ------------------------------------------------------------------ output
+    def pending(self):
+        n_ev, n_seg = C.c_uint64(0), C.c_int64(0)
+        check(lib().neurosim_evsim_pending(self._h, C.byref(n_ev), C.byref(n_seg)))
+        return int(n_ev.value), int(n_seg.value)
+
+    def drain(self, to: str = "cpu", out: torch.Tensor | None = None):
+        """Returns (events, seg_offsets).
+
+        to="cpu": events as a numpy uint64 array; to="cuda": an int64 CUDA tensor
+        holding the same 64-bit records (or `out`, a preallocated int64 CUDA
+        tensor, sliced to the count)."""
+        n_ev, n_seg = self.pending()
+        seg = np.zeros(n_seg + 1, np.int64)
+        n_out, n_segs = C.c_uint64(0), C.c_int64(0)
+        segp = seg.ctypes.data_as(C.POINTER(C.c_int64))
+        if to == "cuda":
+            if out is None:
+                out = torch.empty(max(n_ev, 1), dtype=torch.int64, device=self.device)
+            check(lib().neurosim_evsim_drain_events(
+                self._h, C.c_void_p(out.data_ptr()), out.numel(), 1, C.byref(n_out), segp,
+                seg.size, C.byref(n_segs)))
+            ev = out[: n_out.value]
+        else:
+            buf = np.empty(max(n_ev, 1), np.uint64)
+            check(lib().neurosim_evsim_drain_events(
+                self._h, C.c_void_p(buf.ctypes.data), buf.size, 0, C.byref(n_out), segp,
+                seg.size, C.byref(n_segs)))
+            ev = buf[: n_out.value]
+        self._keep = []
+        return ev, seg
+
+    # ------------------------------------------------------------------ state
+    def get_state(self):
+        n = self.W * self.H
+        ref = np.empty(n, np.float32)
+        lp = np.empty(n, np.float32)
+        tl = np.empty(n, np.uint32)
+        tau, has = C.c_int64(0), C.c_int32(0)
+        check(lib().neurosim_evsim_get_state(
+            self._h, ref.ctypes.data_as(C.POINTER(C.c_float)),
+            lp.ctypes.data_as(C.POINTER(C.c_float)), tl.ctypes.data_as(C.POINTER(C.c_uint32)),
+            C.byref(tau), C.byref(has)))
+        return dict(ref=ref, lprev=lp, tlast=tl, tau_prev=int(tau.value), has_prev=bool(has.value))
+
+    def set_state(self, ref, lprev, tlast, tau_prev: int, has_prev: bool = True) -> None:
+        ref = np.ascontiguousarray(ref, np.float32).reshape(-1)
+        lp = np.ascontiguousarray(lprev, np.float32).reshape(-1)
+        tl = np.ascontiguousarray(tlast, np.uint32).reshape(-1)
+        check(lib().neurosim_evsim_set_state(
+            self._h, ref.ctypes.data_as(C.POINTER(C.c_float)),
+            lp.ctypes.data_as(C.POINTER(C.c_float)), tl.ctypes.data_as(C.POINTER(C.c_uint32)),
+            int(tau_prev), int(bool(has_prev))))
+
+    def thresholds(self):
+        n = self.W * self.H
+        cp = np.empty(n, np.float32)
+        cn = np.empty(n, np.float32)
+        check(lib().neurosim_evsim_get_thresholds(
+            self._h, cp.ctypes.data_as(C.POINTER(C.c_float)), cn.ctypes.data_as(C.POINTER(C.c_float))))
+        return cp.reshape(self.H, self.W), cn.reshape(self.H, self.W)
+
+    def set_profiling(self, enable: bool) -> None:
+        check(lib().neurosim_evsim_set_profiling(self._h, int(bool(enable))))
+
+    def stats(self) -> dict:
+        st = Stats()
+        check(lib().neurosim_evsim_get_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().neurosim_evsim_destroy(self._h)
+            self._h = None
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def device_log(x: torch.Tensor) -> torch.Tensor:
+    """The library's FP32 log on a CUDA tensor (verification of the model's log)."""
+    if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+        raise ValueError("x must be a contiguous float32 CUDA tensor")
+    y = torch.empty_like(x)
+    check(lib().neurosim_debug_log(C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.numel(),
+                                   C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return y

@@ -1,0 +1,98 @@
+"""The C-ABI library loads and exports what include/*.h declares (no GPU needed)."""
+import ctypes as C
+import glob
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2602_15018_gb300 import build
+    try:
+        build._nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not available")
+    return build.build()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(neurosim_\w+)\s*\(", txt, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("neurosim_evsim_create", "neurosim_evsim_step",
+                     "neurosim_evsim_drain_events", "neurosim_evsim_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    lib = C.CDLL(built)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    from paper_2602_15018_gb300 import _lib
+    assert set(_lib.EXPORTS) == set(declared_functions())
+
+
+def test_abi_version_and_defaults(built):
+    from paper_2602_15018_gb300 import _lib
+    L = _lib.lib()
+    assert L.neurosim_abi_version() == 1
+    p = _lib.Params()
+    L.neurosim_evsim_default_params(C.byref(p))
+    assert abs(p.c_pos - 0.2) < 1e-7 and abs(p.c_min - 0.01) < 1e-7 and p.width == 0
+    assert abs(p.log_eps - 1e-3) < 1e-9 and p.input_is_log == 0
+
+
+def test_struct_layout_matches_header(built):
+    """Offsets of every field of the two public structs, C compiler vs ctypes."""
+    from paper_2602_15018_gb300 import _lib
+    structs = {"neurosim_evsim_params": _lib.Params, "neurosim_evsim_stats": _lib.Stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "neurosim_evsim.h"',
+             "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "layout.c")
+        exe = os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines))
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
+        out = subprocess.check_output([exe], text=True).split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            s, f, v = ln.split()
+            got[(s, f)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py)
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_no_gpu_fails_loudly(built):
+    """Without a CUDA device the library reports an error instead of computing."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2602_15018_gb300 import _lib
+    L = _lib.lib()
+    p = _lib.Params()
+    L.neurosim_evsim_default_params(C.byref(p))
+    p.width, p.height = 8, 8
+    h = C.c_void_p()
+    rc = L.neurosim_evsim_create(C.byref(p), None, C.byref(h))
+    assert rc != 0 and not h.value

@@ -1,0 +1,296 @@
+"""GPU parity: the CUDA event path against the FP32-mirrored oracle, bit for bit.
+
+The event set, its order and the interval offsets must be identical (the
+oracle mirrors the FP32 operation order, so the tolerance is zero); the
+per-pixel state after a step must be identical too.  Inputs are seeded
+synthetic scenes with the shapes of the workloads: 240x180 sinusoids, HD
+value-noise texture with occluders, mixed odd sizes.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+DT = 1000
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _sims(W, H, **kw):
+    from paper_2602_15018_gb300 import EventSim
+    gkw = {k: v for k, v in kw.items() if k not in ("precision",)}
+    g = EventSim(W, H, **gkw)
+    cp, cn = g.thresholds()
+    okw = {k: v for k, v in kw.items() if k in ("refractory_us", "log_eps", "input_is_log")}
+    o = oracle.OracleSim(W, H, c_pos_map=cp, c_neg_map=cn, **okw)
+    return g, o
+
+
+def _first_diff(a, b):
+    n = min(len(a), len(b))
+    d = np.nonzero(a[:n] != b[:n])[0]
+    i = int(d[0]) if len(d) else n
+    return i, (oracle.unpack(a[i:i + 1]) if i < len(a) else None), \
+        (oracle.unpack(b[i:i + 1]) if i < len(b) else None)
+
+
+def assert_same(ev, seg, rev, rseg, what=""):
+    assert np.array_equal(seg, rseg), f"{what}: interval offsets differ"
+    if not np.array_equal(ev, rev):
+        i, ga, ob = _first_diff(ev, rev)
+        raise AssertionError(f"{what}: events differ (gpu {len(ev)}, oracle {len(rev)}); first at "
+                             f"{i}: gpu {ga} oracle {ob}")
+
+
+def _check_state(g, o):
+    st = g.get_state()
+    assert np.array_equal(st["ref"], o.ref), "ref differs"
+    assert np.array_equal(st["lprev"], o.lprev), "lprev differs"
+    tl = o.tlast.copy()
+    tl[tl < 0] = 0xFFFFFFFF
+    assert np.array_equal(st["tlast"].astype(np.int64), tl), "tlast differs"
+    assert st["tau_prev"] == o.tau
+
+
+def test_log_bit_exact_domain():
+    """Device log == oracle log on every FP32 value of [1e-8, 1e6 + 1]."""
+    from paper_2602_15018_gb300 import device_log
+    lo = int(np.float32(1e-8).view(np.uint32))
+    hi = int(np.float32(1e6 + 1).view(np.uint32))
+    chunk = 1 << 26
+    for b0 in range(lo, hi + 1, chunk):
+        bits = np.arange(b0, min(hi + 1, b0 + chunk), dtype=np.uint32)
+        x = bits.view(np.float32)
+        y = device_log(torch.from_numpy(x).cuda()).cpu().numpy()
+        assert np.array_equal(y.view(np.uint32), oracle.mylog(x).view(np.uint32)), hex(b0)
+
+
+def test_log_bit_exact_sampled_full_range():
+    """Every 17th positive float (subnormals to max) and the special values."""
+    from paper_2602_15018_gb300 import device_log
+    bits = np.arange(1, 0x7F800000, 17, dtype=np.uint32)
+    x = np.concatenate([bits.view(np.float32),
+                        np.array([0.0, np.inf, -1.0, np.nan, -0.0], np.float32)])
+    y = device_log(torch.from_numpy(x).cuda()).cpu().numpy()
+    r = oracle.mylog(x)
+    assert np.array_equal(np.isnan(y), np.isnan(r))
+    m = ~np.isnan(r)
+    assert np.array_equal(y[m].view(np.uint32), r[m].view(np.uint32))
+
+
+@pytest.mark.parametrize("C", [0.1, 0.2, 0.25])
+def test_random_log_8x8(C):
+    fr = scenes.random_log_frames(8, 8, 6, seed=int(C * 100), lo=-1.0, hi=1.0)
+    g, o = _sims(8, 8, c_pos=C, c_neg=C, input_is_log=True)
+    g.step(torch.from_numpy(fr).cuda(), 0, DT)
+    ev, seg = g.drain()
+    rev, rseg = o.step(fr, 0, DT)
+    assert_same(ev, seg, rev, rseg, f"8x8 C={C}")
+    _check_state(g, o)
+    g.close()
+
+
+def test_ramps_closed_form_on_gpu():
+    for s in (0.0625, 0.09375, -0.0625, 0.75):
+        fr = scenes.log_ramp(5, 3, 41, 0.0, s)
+        g, o = _sims(5, 3, c_pos=0.25, c_neg=0.25, input_is_log=True)
+        g.step(torch.from_numpy(fr).cuda(), 0, DT)
+        ev, seg = g.drain()
+        rev, rseg = o.step(fr, 0, DT)
+        assert_same(ev, seg, rev, rseg, f"ramp {s}")
+        g.close()
+
+
+def test_config1_sinusoids_240x180_full():
+    """240x180, 200 frames at 1000 FPS, C+ = C- = 0.2, no noise, no refractory."""
+    W, H, T = 240, 180, 200
+    for seed in (0, 1):
+        fr = scenes.render_frames(scenes.SinusoidScene(W, H, seed=seed), T)
+        g, o = _sims(W, H, c_pos=0.2, c_neg=0.2, max_frames_per_step=T)
+        g.step(fr.cuda(), 0, DT)
+        ev, seg = g.drain()
+        rev, rseg = o.step(fr.numpy(), 0, DT)
+        assert_same(ev, seg, rev, rseg, f"config1 seed {seed}")
+        assert len(ev) > 100000
+        _check_state(g, o)
+        g.close()
+
+
+@pytest.mark.parametrize("W,H,threads", [(320, 181, 256), (346, 260, 128), (33, 17, 256),
+                                         (7, 5, 128), (1024, 1, 512), (1, 700, 256)])
+def test_texture_odd_sizes(W, H, threads):
+    """Ragged tiles, frames that are not 16-byte aligned per row (W*H % 4 != 0)."""
+    T = 40
+    fr = scenes.render_frames(scenes.TextureScene(W, H, seed=W + H, speed=(300., 600.)), T)
+    kw = dict(c_pos=0.2, c_neg=0.25, sigma_c=0.03, refractory_us=100, seed=W * 7 + H,
+              max_frames_per_step=T, threads_per_block=threads)
+    g, o = _sims(W, H, **kw)
+    g.step(fr.cuda(), 5000, DT)
+    ev, seg = g.drain()
+    rev, rseg = o.step(fr.numpy(), 5000, DT)
+    assert_same(ev, seg, rev, rseg, f"{W}x{H}")
+    _check_state(g, o)
+    g.close()
+
+
+def test_threshold_maps_match_oracle():
+    W, H = 300, 200
+    from paper_2602_15018_gb300 import EventSim
+    g = EventSim(W, H, c_pos=0.2, c_neg=0.25, sigma_c=0.03, c_min=0.01, seed=12345)
+    cp, cn = g.thresholds()
+    ocp, ocn = oracle.threshold_maps(W, H, 0.2, 0.25, 0.03, 0.01, 12345)
+    assert np.array_equal(cp, ocp) and np.array_equal(cn, ocn)
+    g.close()
+
+
+def test_multi_step_gaps_host_and_device_drain():
+    """Steps with uneven gaps between them, host-memory frames, several steps
+    between drains, drains to device memory; state identical after each drain."""
+    W, H = 160, 96
+    sc = scenes.TextureScene(W, H, seed=4, speed=(300., 600.))
+    fr = scenes.render_frames(sc, 60).numpy()
+    g, o = _sims(W, H, c_pos=0.2, c_neg=0.25, sigma_c=0.02, refractory_us=150, seed=8,
+                 max_frames_per_step=32)
+    plan = [(0, 1, 0), (1, 9, 2500), (9, 10, 13000), (10, 30, 20000), (30, 31, 41500),
+            (31, 60, 43000)]
+    batches = [[0, 1], [2, 3], [4, 5]]
+    for b, idx in enumerate(batches):
+        rev_all, rseg_all = [], [0]
+        for k in idx:
+            f0, f1, t0 = plan[k]
+            chunk = np.ascontiguousarray(fr[f0:f1])
+            if k % 2:
+                g.step_host(chunk, t0, DT)
+            else:
+                g.step(torch.from_numpy(chunk).cuda(), t0, DT)
+            rev, rseg = o.step(chunk, t0, DT)
+            rev_all.append(rev)
+            rseg_all.extend((rseg[1:] + rseg_all[-1]).tolist())
+        if b == 1:
+            ev_t, seg = g.drain(to="cuda")
+            ev = ev_t.cpu().numpy().view(np.uint64)
+        else:
+            ev, seg = g.drain()
+        assert_same(ev, seg, np.concatenate(rev_all), np.array(rseg_all), f"batch {b}")
+        _check_state(g, o)
+    g.close()
+
+
+def test_overflow_regrowth_is_exact():
+    """A tiny initial capacity must regrow and replay without changing a bit."""
+    W, H, T = 240, 180, 60
+    fr = scenes.render_frames(scenes.SinusoidScene(W, H, seed=3), T)
+    g, o = _sims(W, H, c_pos=0.2, c_neg=0.2, max_frames_per_step=T, event_capacity=1000)
+    g.step(fr[:30].contiguous().cuda(), 0, DT)
+    g.step(fr[30:].contiguous().cuda(), 30 * DT, DT)
+    n, nseg = g.pending()
+    ev, seg = g.drain()
+    rev, rseg = o.step(fr.numpy(), 0, DT)
+    assert n == len(rev) and nseg == T - 1
+    assert_same(ev, seg, rev, rseg, "overflow")
+    g.close()
+
+
+def test_checkpoint_resume_bit_identical():
+    W, H = 128, 72
+    fr = scenes.render_frames(scenes.TextureScene(W, H, seed=9, speed=(300., 600.)), 40)
+    kw = dict(c_pos=0.2, c_neg=0.25, sigma_c=0.03, refractory_us=100, seed=1,
+              max_frames_per_step=40)
+    from paper_2602_15018_gb300 import EventSim
+    a = EventSim(W, H, **kw)
+    a.step(fr.cuda(), 0, DT)
+    ea, sa = a.drain()
+    b = EventSim(W, H, **kw)
+    b.step(fr[:17].contiguous().cuda(), 0, DT)
+    e1, s1 = b.drain()
+    st = b.get_state()
+    b.close()
+    c = EventSim(W, H, **kw)
+    c.set_state(st["ref"], st["lprev"], st["tlast"], st["tau_prev"], st["has_prev"])
+    c.step(fr[17:].contiguous().cuda(), 17 * DT, DT)
+    e2, s2 = c.drain()
+    assert np.array_equal(np.concatenate([e1, e2]), ea)
+    assert np.array_equal(np.concatenate([s1, s2[1:] + s1[-1]]), sa)
+    a.close()
+    c.close()
+
+
+def test_error_codes():
+    from paper_2602_15018_gb300 import EventSim, NeurosimError
+    with pytest.raises(NeurosimError, match="E_INVALID"):
+        EventSim(0, 10)
+    with pytest.raises(NeurosimError, match="E_INVALID"):
+        EventSim(10, 10, c_pos=0.0)
+    g = EventSim(8, 8, max_frames_per_step=4, input_is_log=True)
+    fr = torch.zeros(2, 8, 8, device="cuda")
+    g.step(fr, 1000, DT)
+    with pytest.raises(NeurosimError, match="E_TIME"):
+        g.step(fr, 1500, DT)          # not after the last frame (2000)
+    with pytest.raises(NeurosimError, match="E_TIME"):
+        g.step(fr, 5000, 0)
+    with pytest.raises(NeurosimError, match="E_INVALID"):
+        g.step(torch.zeros(5, 8, 8, device="cuda"), 9000, DT)   # more than max frames
+    with pytest.raises(NeurosimError, match="E_STATE"):
+        g.set_state(np.zeros(64), np.zeros(64), np.zeros(64), 0)
+    g.step(torch.full((1, 8, 8), float("nan"), device="cuda"), 3000, DT)
+    ev, seg = g.drain()            # NaN log input clamps to -32: OFF events, no fault
+    assert len(ev) > 0 and np.all(oracle.unpack(ev)[3] == 0)
+    g.close()
+
+
+def test_hd_full_size_sampled_pixels():
+    """The HD workload at full size (1280x720, 2000 frames, C+ 0.2, C- 0.25,
+    sigma 0.03, refractory 100 us) in the benchmark's launch configuration:
+    every event of 4096 sampled pixels against the oracle run on those pixels'
+    full time series, plus whole-stream invariants."""
+    import bench
+    W, H, T = 1280, 720, 2000
+    frames = bench.render_config2(seed=0, device="cuda")
+    from paper_2602_15018_gb300 import EventSim
+    g = EventSim(W, H, **bench.CONFIG2_SIM, max_frames_per_step=T)
+    g.step(frames, 0, DT)
+    ev, seg = g.drain()
+    cp, cn = g.thresholds()
+    ocp, ocn = oracle.threshold_maps(W, H, 0.2, 0.25, 0.03, 0.01, bench.CONFIG2_SIM["seed"])
+    assert np.array_equal(cp, ocp) and np.array_equal(cn, ocn)
+    assert len(seg) == T
+    t, x, y, p = oracle.unpack(ev)
+    # whole stream: t inside its interval, ascending records per interval
+    j = np.repeat(np.arange(T - 1), np.diff(seg))
+    assert np.all(t >= j * DT) and np.all(t <= (j + 1) * DT)
+    d = np.diff(ev)
+    same = j[1:] == j[:-1]
+    assert np.all(ev[1:][same] >= ev[:-1][same])
+    # sampled pixels, full time series
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(W * H, 4096, replace=False))
+    sub = frames.reshape(T, -1)[:, torch.from_numpy(pick).cuda()].cpu().numpy()
+    o = oracle.OracleSim(len(pick), 1, c_pos_map=ocp.ravel()[pick], c_neg_map=ocn.ravel()[pick],
+                         refractory_us=100)
+    rev, rseg = o.step(sub.reshape(T, 1, -1), 0, DT)
+    rt, rx, _, rp = oracle.unpack(rev)
+    rj = np.repeat(np.arange(T - 1), np.diff(rseg))
+    pix = y.astype(np.int64) * W + x
+    sel = np.isin(pix, pick)
+    gj, gt, gpix, gp = j[sel], t[sel], pix[sel], p[sel]
+    opix = pick[rx]
+    key_g = np.lexsort((gp, gt, gpix, gj))
+    key_o = np.lexsort((rp, rt, opix, rj))
+    assert np.array_equal(gj[key_g], rj[key_o])
+    assert np.array_equal(gpix[key_g], opix[key_o])
+    assert np.array_equal(gt[key_g], rt[key_o])
+    assert np.array_equal(gp[key_g], rp[key_o])
+    assert sel.sum() > 1000
+    g.close()
+    del frames
+    torch.cuda.empty_cache()
