@@ -182,6 +182,9 @@ def run_ours(args):
     W, H, T = wl["dims"]["W"], wl["dims"]["H"], wl["dims"]["T"]
     npix = W * H
     frames = wl["render"](seed=args.seed + rank, device=dev)
+    # Steps alternate forward and time-reversed playback of the rendered clip,
+    # so that every step continues the previous one without a scene cut.
+    frames_rev = frames.flip(0).contiguous()
     torch.cuda.synchronize()
 
     sim = EventSim(W, H, **wl["sim"], max_frames_per_step=T)
@@ -191,7 +194,7 @@ def run_ours(args):
 
     def one_step(k):
         nonlocal out
-        sim.step(frames, k * span, DT)
+        sim.step(frames if k % 2 == 0 else frames_rev, k * span, DT)
         n, _ = sim.pending()
         if n > out.numel():
             out = torch.empty(int(n * 1.25), dtype=torch.int64, device=dev)
@@ -258,7 +261,8 @@ def run_ours(args):
     e2e = None
     if args.e2e_steps > 0:
         host_frames = frames.cpu().pin_memory()
-        del frames
+        host_frames_rev = frames_rev.cpu().pin_memory()
+        del frames, frames_rev
         torch.cuda.empty_cache()
         host_out = np.empty(cap, np.uint64)
         sim2 = EventSim(W, H, **wl["sim"], max_frames_per_step=T)
@@ -266,7 +270,7 @@ def run_ours(args):
 
         def e2e_step(kk):
             nonlocal host_out
-            sim2.step_host(host_frames, kk * span, DT)
+            sim2.step_host(host_frames if kk % 2 == 0 else host_frames_rev, kk * span, DT)
             n, _ = sim2.pending()
             if n > host_out.size:
                 host_out = np.empty(int(n * 1.25), np.uint64)

@@ -63,7 +63,7 @@ typedef struct neurosim_evsim neurosim_evsim;
 
 typedef struct neurosim_evsim_params {
     int32_t width;               /* 1..65535 pixels                            */
-    int32_t height;              /* 1..32767 pixels                            */
+    int32_t height;              /* 1..32767 pixels; width*height <= 2^22      */
     float c_pos;                 /* mean ON threshold in log units (> 0)       */
     float c_neg;                 /* mean OFF threshold in log units (> 0)      */
     float sigma_c;               /* per-pixel threshold std; 0 disables noise  */
@@ -79,8 +79,10 @@ typedef struct neurosim_evsim_params {
                                     Grows on overflow (see drain).            */
     int32_t max_frames_per_step; /* frames per step call; 0 = 1024             */
     int32_t max_pending_intervals; /* intervals between drains; 0 = 65536      */
-    int32_t threads_per_block;   /* emission CTA size (128/256/512); 0 = auto  */
-    int32_t pipeline_stages;     /* frame stages in shared memory; 0 = auto    */
+    int32_t pixels_per_thread;   /* emission pixels per CUDA thread: 8 or 16
+                                    (a warp owns 32x that many pixels); 0 = auto */
+    int32_t prefetch_frames;     /* frames each thread keeps in flight: 2 or 3;
+                                    0 = auto                                    */
     int32_t reserved[6];         /* must be zero                               */
 } neurosim_evsim_params;
 

@@ -42,8 +42,8 @@ class Params(C.Structure):
         ("input_is_log", C.c_int32), ("seed", C.c_uint64),
         ("c_pos_map", C.POINTER(C.c_float)), ("c_neg_map", C.POINTER(C.c_float)),
         ("event_capacity", C.c_uint64), ("max_frames_per_step", C.c_int32),
-        ("max_pending_intervals", C.c_int32), ("threads_per_block", C.c_int32),
-        ("pipeline_stages", C.c_int32), ("reserved", C.c_int32 * 6),
+        ("max_pending_intervals", C.c_int32), ("pixels_per_thread", C.c_int32),
+        ("prefetch_frames", C.c_int32), ("reserved", C.c_int32 * 6),
     ]
 
 

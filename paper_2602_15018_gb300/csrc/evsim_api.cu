@@ -100,7 +100,7 @@ struct neurosim_evsim {
     int device = 0;
     int sms = 0;
     int W = 0, H = 0, npix = 0, pix_bits = 1;
-    int threads = 256, stages = 8, n_tiles = 0;
+    int ppt = 16, pf = 2, n_tiles = 0;
     int grid_emit32 = 0, grid_emit64 = 0, sort_smem = 0;
     int Tmax = 1024;
     int64_t max_pending = 65536;
@@ -217,8 +217,8 @@ int validate(const neurosim_evsim_params* p)
     if (!p) return fail(NEUROSIM_E_INVALID, "params is NULL");
     if (p->width < 1 || p->width > 65535 || p->height < 1 || p->height > 32767)
         return fail(NEUROSIM_E_INVALID, "width must be in [1, 65535] and height in [1, 32767]");
-    if ((int64_t)p->width * p->height > (int64_t)kMaxTilesPerStream * 512 * kPPT)
-        return fail(NEUROSIM_E_INVALID, "width*height must be <= %d", kMaxTilesPerStream * 512 * kPPT);
+    if ((int64_t)p->width * p->height > (int64_t)kMaxTilesPerStream * 32 * 16)
+        return fail(NEUROSIM_E_INVALID, "width*height must be <= %d", kMaxTilesPerStream * 32 * 16);
     const bool maps = p->c_pos_map != nullptr || p->c_neg_map != nullptr;
     if (maps && (p->c_pos_map == nullptr || p->c_neg_map == nullptr))
         return fail(NEUROSIM_E_INVALID, "c_pos_map and c_neg_map must be given together");
@@ -234,11 +234,10 @@ int validate(const neurosim_evsim_params* p)
     if (p->max_frames_per_step < 0 || p->max_frames_per_step > (1 << 20))
         return fail(NEUROSIM_E_INVALID, "max_frames_per_step must be in [0, 2^20]");
     if (p->max_pending_intervals < 0) return fail(NEUROSIM_E_INVALID, "max_pending_intervals < 0");
-    if (p->threads_per_block != 0 && p->threads_per_block != 128 && p->threads_per_block != 256 &&
-        p->threads_per_block != 512)
-        return fail(NEUROSIM_E_INVALID, "threads_per_block must be 0, 128, 256 or 512");
-    if (p->pipeline_stages != 0 && (p->pipeline_stages < 2 || p->pipeline_stages > 16))
-        return fail(NEUROSIM_E_INVALID, "pipeline_stages must be 0 or in [2, 16]");
+    if (p->pixels_per_thread != 0 && p->pixels_per_thread != 8 && p->pixels_per_thread != 16)
+        return fail(NEUROSIM_E_INVALID, "pixels_per_thread must be 0, 8 or 16");
+    if (p->prefetch_frames != 0 && p->prefetch_frames != 2 && p->prefetch_frames != 3)
+        return fail(NEUROSIM_E_INVALID, "prefetch_frames must be 0, 2 or 3");
     for (int i = 0; i < 6; ++i)
         if (p->reserved[i] != 0) return fail(NEUROSIM_E_INVALID, "reserved fields must be zero");
     return NEUROSIM_OK;
@@ -303,8 +302,8 @@ int enqueue_step(neurosim_evsim* h, const float* frames_dev, int32_t T, int64_t 
     L.dt = dt;
     L.key64 = key64;
     L.t_bits = t_bits;
-    L.threads = h->threads;
-    L.stages = h->stages;
+    L.ppt = h->ppt;
+    L.pf = h->pf;
     L.grid_emit = key64 ? h->grid_emit64 : h->grid_emit32;
     L.grid_sort = std::max(1, std::min(n_segs, h->sms * 2));
     L.sort_smem = h->sort_smem;
@@ -468,20 +467,20 @@ int neurosim_evsim_create(const neurosim_evsim_params* p, void* cuda_stream, neu
     h->max_pending = p->max_pending_intervals ? p->max_pending_intervals : 65536;
     if (h->max_pending < h->Tmax) h->max_pending = h->Tmax;
 
-    h->threads = p->threads_per_block ? p->threads_per_block : 256;
-    while ((h->npix + h->threads * kPPT - 1) / (h->threads * kPPT) > kMaxTilesPerStream && h->threads < 512)
-        h->threads *= 2;
-    h->n_tiles = (h->npix + h->threads * kPPT - 1) / (h->threads * kPPT);
+    h->ppt = p->pixels_per_thread ? p->pixels_per_thread : 16;
+    if ((h->npix + 32 * h->ppt - 1) / (32 * h->ppt) > kMaxTilesPerStream) h->ppt = 16;
+    h->n_tiles = (h->npix + 32 * h->ppt - 1) / (32 * h->ppt);
     if (h->n_tiles > kMaxTilesPerStream)
-        return bail(fail(NEUROSIM_E_INVALID, "too many pixels for threads_per_block %d", h->threads));
-    h->stages = p->pipeline_stages ? p->pipeline_stages : 8;
+        return bail(fail(NEUROSIM_E_INVALID, "too many pixels for pixels_per_thread %d", h->ppt));
+    h->pf = p->prefetch_frames ? p->prefetch_frames : 2;
     int bps32 = 0, bps64 = 0;
-    if (emit_occupancy(h->threads, h->stages, 0, &bps32) != cudaSuccess ||
-        emit_occupancy(h->threads, h->stages, 1, &bps64) != cudaSuccess || bps32 < 1 || bps64 < 1)
-        return bail(fail(NEUROSIM_E_CUDA, "emission kernel does not fit (threads %d, stages %d)",
-                         h->threads, h->stages));
-    h->grid_emit32 = std::min(h->n_tiles, h->sms * bps32);
-    h->grid_emit64 = std::min(h->n_tiles, h->sms * bps64);
+    if (emit_occupancy(h->ppt, h->pf, 0, &bps32) != cudaSuccess ||
+        emit_occupancy(h->ppt, h->pf, 1, &bps64) != cudaSuccess || bps32 < 1 || bps64 < 1)
+        return bail(fail(NEUROSIM_E_CUDA, "emission kernel does not fit (ppt %d, prefetch %d)",
+                         h->ppt, h->pf));
+    const int wpc = emit_warps_per_cta(h->ppt);
+    h->grid_emit32 = std::min((h->n_tiles + wpc - 1) / wpc, h->sms * bps32);
+    h->grid_emit64 = std::min((h->n_tiles + wpc - 1) / wpc, h->sms * bps64);
     if (sort_configure(&h->sort_smem) != cudaSuccess)
         return bail(fail(NEUROSIM_E_CUDA, "cannot configure the sort kernel"));
 

@@ -1,0 +1,600 @@
+// Emission kernel of the event path (included by evsim_kernels.cu, inside the
+// anonymous namespace; uses model_log, stream_of_item and the StepLaunch of
+// evsim_internal.h).
+//
+// Model: arXiv 2602.15018, Sec. 2 — per-pixel state with the level of the last
+// triggered event, contrast-threshold crossings, timestamps between frames,
+// a variable number of events per frame gathered with few global atomics.
+//
+// Work split: one warp owns a tile of 32 * PPT contiguous pixels of one stream
+// for all T frames of the step; warps never wait on each other.  Tile-local
+// pixel p = q*128 + lane*4 + c (q < PPT/4, c < 4) is loaded by lane `lane`
+// as part of its q-th float4, so every load instruction of the warp reads 512
+// contiguous bytes.  The exact per-pixel state (ref, t_last, last computed
+// log intensity), the raw inputs of the current and previous frame and the
+// pixel's filter bounds live in the warp's slice of shared memory, indexed by
+// p; per-pixel thresholds are read from global memory when needed.
+//
+// Fast path (every pixel, every frame): the raw input v is compared with
+// bounds vd < v < vu chosen so that inside them the model's log intensity of
+// v lies strictly between ref - C- and ref + C+: no crossing is possible and
+// only L_prev moves.  In the log domain the bounds are the exact FP32 levels
+// ref + C+ and ref - C- (the clamp to [-32, 32] keeps the implication).  For
+// intensities, x = fl(clamp(v, 0, 1e6) + eps) is monotone in v, and
+//   xu = 2^((ref + C+) log2 e) (1 - 1e-4),  vu = fl(xu - eps),
+//   xd = 2^((ref - C-) log2 e) (1 + 1e-4),  vd = fl(xd - eps),
+// with the 1e-4 margin about 30 times the combined error of ex2.approx, the
+// FP32 roundings and the 2-ulp bound of the model's log on [1e-8, 1e6 + 1];
+// the filter may send a pixel to the slow path for nothing, never the other
+// way.  A NaN input fails both comparisons and is always tested exactly.
+//
+// Slow path: the warp's pixels outside their bounds are compacted into a
+// list in pixel order and handed out one per lane, 32 per round, so that
+// neighbouring pixels that trigger together are processed in parallel.  Each
+// lane runs the exact FP32 model for its pixel, commits the state, keeps the
+// first two keys in registers; a warp prefix of the counts (list order =
+// pixel order) places the keys of the tile's events in this interval as one
+// contiguous chunk of the paged key buffer (one global atomic per page, not
+// per frame).  More than one round, or more than two events for a pixel,
+// takes the general path that regenerates keys from values saved in scratch
+// slots of shared memory.
+
+constexpr float kBoundMargin = 1.0e-4f;
+constexpr float kMaxIntensity = 1.0e6f;
+
+// L2 eviction policies: frames are read once and should leave L2 first; the
+// per-pixel thresholds are re-read on every slow path and should stay.
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ float4 ld_stream4(const float* p, uint64_t pol)
+{
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ float ld_stream(const float* p, uint64_t pol)
+{
+    float v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ float ld_keep(const float* p, uint64_t pol)
+{
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ float ex2_approx(float v)
+{
+    float r;
+    asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ float transform_in(float v, float eps, int is_log)
+{
+    if (is_log) return fminf(fmaxf(v, -32.0f), 32.0f);
+    return __fadd_rn(fminf(fmaxf(v, 0.0f), kMaxIntensity), eps);
+}
+
+__device__ __forceinline__ float model_L(float v, float eps, int is_log)
+{
+    const float x = transform_in(v, eps, is_log);
+    return is_log ? x : model_log(x);
+}
+
+// Raw-input bound below which no ON crossing of level `up` is possible.
+__device__ __forceinline__ float raw_bound_up(float up, float eps, int is_log)
+{
+    if (is_log) return up;
+    const float xu = __fmul_rn(ex2_approx(__fmul_rn(up, 1.44269504f)), 1.0f - kBoundMargin);
+    if (!(xu > eps)) return __int_as_float(0xff800000);                        // test every input
+    if (xu > __fadd_rn(kMaxIntensity, eps)) return __int_as_float(0x7f800000);  // unreachable
+    return __fsub_rn(xu, eps);
+}
+
+// Raw-input bound above which no OFF crossing of level `dn` is possible.
+__device__ __forceinline__ float raw_bound_dn(float dn, float eps, int is_log)
+{
+    if (is_log) return dn;
+    const float xd = __fmul_rn(ex2_approx(__fmul_rn(dn, 1.44269504f)), 1.0f + kBoundMargin);
+    if (xd < eps) return __int_as_float(0xff800000);                              // every input is above
+    if (!(xd < __fadd_rn(kMaxIntensity, eps))) return __int_as_float(0x7f800000);  // test every input
+    return __fsub_rn(xd, eps);
+}
+
+// Crossings of one pixel over one interval (L_a at ta, L_b at ta + D), both
+// polarities in one loop: ON uses +C+, OFF uses -C- (fl(r - c) == fl(r + -c)).
+// Advances ref and t_last.  MODE 0: count only; MODE 1: also keep keys 0 and
+// 1 in k0 / k1; MODE 2: write every key to out[].  Returns the count.
+template <int MODE, typename KeyT>
+__device__ __forceinline__ int pixel_events(float& r, uint32_t& tl, float a, float b, float cp,
+                                            float cn, uint32_t ta, float Df, uint32_t R,
+                                            KeyT pixkey, int tshift, KeyT& k0, KeyT& k1,
+                                            KeyT* out)
+{
+    if (!(b != a)) return 0;
+    const bool on = b > a;
+    const float c = on ? cp : -cn;
+    const float den = __fsub_rn(b, a);
+    const KeyT pol = on ? (KeyT)1 : (KeyT)0;
+    int n = 0;
+    for (;;) {
+        const float lvl = __fadd_rn(r, c);
+        if (on ? !(lvl <= b) : !(lvl >= b)) break;
+        const float frac = __fdiv_rn(__fsub_rn(lvl, a), den);
+        const float tf = fmaxf(floorf(__fmul_rn(frac, Df)), 0.0f);
+        const uint32_t toff = (uint32_t)tf;
+        const uint32_t t = ta + toff;
+        r = lvl;
+        if (R != 0u && tl != kTlastNone && (int64_t)t - (int64_t)tl < (int64_t)R) continue;
+        if (MODE != 0) {
+            const KeyT key = ((KeyT)toff << tshift) | pixkey | pol;
+            if (MODE == 2) out[n] = key;
+            else if (n == 0) k0 = key;
+            else if (n == 1) k1 = key;
+        }
+        ++n;
+        tl = t;
+    }
+    return n;
+}
+
+// Per-warp shared-memory slice (arrays of WPX = 32*PPT entries indexed by the
+// tile-local pixel, plus the trigger list and the lanes' "L cached" masks).
+template <int PPT>
+struct WarpSlice {
+    static constexpr int WPX = 32 * PPT;
+    static constexpr int FLOATS = 7 * WPX + WPX + 32;   // 7 arrays, list (u32), masks
+    float* base;
+    __device__ __forceinline__ float* vs(int parity) const { return base + parity * WPX; }
+    __device__ __forceinline__ float* vu() const { return base + 2 * WPX; }
+    __device__ __forceinline__ float* vd() const { return base + 3 * WPX; }
+    __device__ __forceinline__ float* ref() const { return base + 4 * WPX; }
+    __device__ __forceinline__ uint32_t* tl() const { return reinterpret_cast<uint32_t*>(base + 5 * WPX); }
+    __device__ __forceinline__ float* lb() const { return base + 6 * WPX; }
+    __device__ __forceinline__ uint32_t* list() const { return reinterpret_cast<uint32_t*>(base + 7 * WPX); }
+    __device__ __forceinline__ uint32_t* lvm() const { return reinterpret_cast<uint32_t*>(base + 8 * WPX); }
+};
+
+// Everything the slow path needs about the current tile and interval.
+struct TileCtx {
+    const float* cpos;   // per-pixel thresholds of the stream (global), or null
+    const float* cneg;
+    float cpos_u, cneg_u;
+    uint32_t ta;
+    float Df;
+    uint32_t R;
+    float eps;
+    int is_log;
+    int tshift;
+    int g0;              // global index of the tile's pixel 0
+    int cur;             // parity of the current frame's input slot
+    uint64_t keep;       // L2 evict_last policy for the thresholds
+};
+
+__device__ __forceinline__ void thresholds_of(const TileCtx& c, int p, float& cp, float& cn)
+{
+    if (c.cpos) {
+        cp = ld_keep(c.cpos + c.g0 + p, c.keep);
+        cn = ld_keep(c.cneg + c.g0 + p, c.keep);
+    } else {
+        cp = c.cpos_u;
+        cn = c.cneg_u;
+    }
+}
+
+// L_a of pixel p: cached L of the previous frame if its owner lane's mask says
+// so, else the model's log of the previous input.
+template <int PPT>
+__device__ __forceinline__ float L_prev(const WarpSlice<PPT>& s, const TileCtx& c, int p)
+{
+    const int owner = (p & 127) >> 2;
+    const int bit = ((p >> 7) << 2) | (p & 3);
+    if ((s.lvm()[owner] >> bit) & 1u) return s.lb()[p];
+    return model_L(s.vs(c.cur ^ 1)[p], c.eps, c.is_log);
+}
+
+// General path for one warp-frame: any number of list entries and events.
+// Pass 1 commits every entry and saves (L_a, ref, t_last) before the step in
+// the vu / vd / previous-input slots and its count in the list entry; then
+// the keys are regenerated into out[] in list order; then fresh bounds.
+template <int PPT, typename KeyT>
+__device__ __noinline__ void slow_general(const WarpSlice<PPT> s, const TileCtx c, int lane,
+                                          int n_list, KeyT* keys, uint32_t page_keys, uint32_t n_pages,
+                                          unsigned int* page_ctr, unsigned int* err,
+                                          uint32_t& pg_cur, uint32_t& pg_end, uint32_t* chunk_off,
+                                          uint32_t* chunk_cnt)
+{
+    uint32_t* vprev_bits = reinterpret_cast<uint32_t*>(s.vs(c.cur ^ 1));
+    uint32_t total = 0;
+    for (int r0 = 0; r0 < n_list; r0 += 32) {
+        const int e = r0 + lane;
+        int n = 0;
+        if (e < n_list) {
+            const int p = (int)(s.list()[e] & 1023u);
+            float cp, cn;
+            thresholds_of(c, p, cp, cn);
+            const float b = model_L(s.vs(c.cur)[p], c.eps, c.is_log);
+            const float a = L_prev(s, c, p);
+            float r = s.ref()[p];
+            uint32_t tl = s.tl()[p];
+            s.vu()[p] = a;
+            s.vd()[p] = r;
+            vprev_bits[p] = tl;
+            s.lb()[p] = b;
+            KeyT d0 = 0, d1 = 0;
+            n = pixel_events<0, KeyT>(r, tl, a, b, cp, cn, c.ta, c.Df, c.R, (KeyT)0, 0, d0, d1, nullptr);
+            s.ref()[p] = r;
+            s.tl()[p] = tl;
+            s.list()[e] = (uint32_t)p | ((uint32_t)n << 10);
+        }
+        int sum = n;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+        total += (uint32_t)sum;
+    }
+    __syncwarp();
+    // one contiguous chunk for the whole warp-frame
+    uint32_t base = kNoChunk;
+    if (total > 0u) {
+        if (pg_end - pg_cur >= total) {
+            base = pg_cur;
+            pg_cur += total;
+        } else {
+            const uint32_t np_ = (total + page_keys - 1u) / page_keys;
+            uint32_t first = 0u;
+            if (lane == 0) first = atomicAdd(page_ctr, np_);
+            first = __shfl_sync(0xffffffffu, first, 0);
+            if ((uint64_t)first + np_ <= (uint64_t)n_pages) {
+                base = first * page_keys;
+                pg_cur = base + total;
+                pg_end = (first + np_) * page_keys;
+            } else {
+                if (lane == 0) atomicOr(err, kErrPageOverflow);
+                pg_cur = pg_end = 0u;
+            }
+        }
+    }
+    *chunk_off = base == kNoChunk ? 0u : base;
+    *chunk_cnt = base == kNoChunk ? 0u : total;
+    uint32_t carry = 0;
+    for (int r0 = 0; r0 < n_list; r0 += 32) {
+        const int e = r0 + lane;
+        const uint32_t ent = (e < n_list) ? s.list()[e] : 0u;
+        const int p = (int)(ent & 1023u);
+        const int n = (int)(ent >> 10);
+        int incl = n;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int nb = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += nb;
+        }
+        if (e < n_list) {
+            float cp, cn;
+            thresholds_of(c, p, cp, cn);
+            if (base != kNoChunk && n > 0) {
+                float r = s.vd()[p];
+                uint32_t tl = vprev_bits[p];
+                KeyT d0 = 0, d1 = 0;
+                pixel_events<2, KeyT>(r, tl, s.vu()[p], s.lb()[p], cp, cn, c.ta, c.Df, c.R,
+                                      (KeyT)(c.g0 + p) << 1, c.tshift, d0, d1,
+                                      keys + (size_t)base + carry + (uint32_t)(incl - n));
+            }
+            const float rr = s.ref()[p];
+            s.vu()[p] = raw_bound_up(__fadd_rn(rr, cp), c.eps, c.is_log);
+            s.vd()[p] = raw_bound_dn(__fsub_rn(rr, cn), c.eps, c.is_log);
+        }
+        carry += (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
+    }
+}
+
+template <int PPT>
+__device__ __forceinline__ void load_frame(float4 (&b)[PPT / 4], const float* p, int nvq, int vec,
+                                           int lane_left, uint64_t pol)
+{
+    // p points at the lane's first float of group 0; group q is 128 floats further.
+#pragma unroll
+    for (int q = 0; q < PPT / 4; ++q) {
+        if (vec) {
+            b[q] = (q < nvq) ? ld_stream4(p + q * 128, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            float e[4];
+            const int left = lane_left - q * 128;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) e[m] = (m < left) ? ld_stream(p + q * 128 + m, pol) : 0.0f;
+            b[q] = make_float4(e[0], e[1], e[2], e[3]);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t outside4(const float4 v, const float4 u, const float4 d)
+{
+    return ((v.x < u.x && v.x > d.x) ? 0u : 1u) | ((v.y < u.y && v.y > d.y) ? 0u : 2u) |
+           ((v.z < u.z && v.z > d.z) ? 0u : 4u) | ((v.w < u.w && v.w > d.w) ? 0u : 8u);
+}
+
+template <int PPT, int WARPS, int PF, typename KeyT>
+__global__ void __launch_bounds__(WARPS * 32) emit_kernel(const __grid_constant__ StepLaunch L)
+{
+    constexpr int NQ = PPT / 4;
+    constexpr int WPX = 32 * PPT;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const WarpSlice<PPT> s{reinterpret_cast<float*>(smem_raw) + (size_t)wib * WarpSlice<PPT>::FLOATS};
+    KeyT* const keys = reinterpret_cast<KeyT*>(L.keys);
+    uint32_t pg_cur = 0u, pg_end = 0u;      // warp-uniform free range of the warp's key page
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
+    const int gw = blockIdx.x * WARPS + wib;
+    const int nw = gridDim.x * WARPS;
+
+    for (int item = gw; item < L.n_items; item += nw) {
+        const StreamDesc* sdp = stream_of_item(L, item);
+        const int npix = sdp->npix;
+        const int tile = item - sdp->item_base;
+        const int init = sdp->init;
+        const int vec = sdp->vec;
+        const int T = L.T;
+        const int dt = L.dt;
+        const int D0 = sdp->D0;
+        const int64_t ta0 = sdp->ta0;
+        uint2* const chunk_col = L.chunks + sdp->chunk_base + tile;
+        const int n_tiles = sdp->n_tiles;
+        TileCtx c;
+        c.cpos = sdp->cpos;
+        c.cneg = sdp->cneg;
+        c.cpos_u = sdp->cpos_u;
+        c.cneg_u = sdp->cneg_u;
+        c.R = sdp->refractory;
+        c.eps = sdp->log_eps;
+        c.is_log = sdp->input_is_log;
+        c.tshift = sdp->pix_bits + 1;
+        c.g0 = tile * WPX;
+        c.keep = pol_keep;
+        const int lane_g = c.g0 + lane * 4;                  // global pixel of (q=0, c=0)
+        const int lane_left = npix - lane_g;                 // valid pixels from there on
+        int nvq = 0;                                         // complete float4 groups (vec)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) nvq += (lane_left - q * 128 >= 4) ? 1 : 0;
+        uint32_t valid = 0u;                                 // bit q*4+m: pixel exists
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) valid |= (lane_left - q * 128 > m ? 1u : 0u) << (q * 4 + m);
+
+        // state -> shared memory
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int p = q * 128 + lane * 4;
+            const int g = c.g0 + p;
+            float r[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+            uint32_t t[4] = {kTlastNone, kTlastNone, kTlastNone, kTlastNone};
+            if (!init) {
+                if (((valid >> (q * 4)) & 15u) == 15u) {
+                    const float4 r4 = *reinterpret_cast<const float4*>(sdp->ref_in + g);
+                    const float4 l4 = *reinterpret_cast<const float4*>(sdp->lprev_in + g);
+                    const uint4 t4 = *reinterpret_cast<const uint4*>(sdp->tlast_in + g);
+                    r[0] = r4.x; r[1] = r4.y; r[2] = r4.z; r[3] = r4.w;
+                    l[0] = l4.x; l[1] = l4.y; l[2] = l4.z; l[3] = l4.w;
+                    t[0] = t4.x; t[1] = t4.y; t[2] = t4.z; t[3] = t4.w;
+                } else {
+                    for (int m = 0; m < 4; ++m)
+                        if ((valid >> (q * 4 + m)) & 1u) {
+                            r[m] = sdp->ref_in[g + m];
+                            l[m] = sdp->lprev_in[g + m];
+                            t[m] = sdp->tlast_in[g + m];
+                        }
+                }
+            }
+            float u[4], d[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                float cp, cn;
+                if ((valid >> (q * 4 + m)) & 1u) thresholds_of(c, p + m, cp, cn);
+                else cp = cn = 1.0f;
+                const bool ok = !init && ((valid >> (q * 4 + m)) & 1u);
+                u[m] = ok ? raw_bound_up(__fadd_rn(r[m], cp), c.eps, c.is_log) : __int_as_float(0x7f800000);
+                d[m] = ok ? raw_bound_dn(__fsub_rn(r[m], cn), c.eps, c.is_log) : __int_as_float(0xff800000);
+            }
+            *reinterpret_cast<float4*>(s.ref() + p) = make_float4(r[0], r[1], r[2], r[3]);
+            *reinterpret_cast<float4*>(s.lb() + p) = make_float4(l[0], l[1], l[2], l[3]);
+            *reinterpret_cast<uint4*>(s.tl() + p) = make_uint4(t[0], t[1], t[2], t[3]);
+            *reinterpret_cast<float4*>(s.vu() + p) = make_float4(u[0], u[1], u[2], u[3]);
+            *reinterpret_cast<float4*>(s.vd() + p) = make_float4(d[0], d[1], d[2], d[3]);
+        }
+        uint32_t lvalid = init ? 0u : valid;   // lb holds L of the previous frame
+
+        // frame pipeline: PF frames in flight per lane
+        const float* fp = sdp->frames + lane_g;
+        float4 buf[PF][NQ];
+#pragma unroll
+        for (int u = 0; u < PF; ++u)
+            if (u < T) load_frame<PPT>(buf[u], fp + (int64_t)u * npix, nvq, vec, lane_left, pol_stream);
+
+        for (int f0 = 0; f0 < T; f0 += PF) {
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int f = f0 + u;
+                if (f >= T) break;
+                c.cur = f & 1;
+                float* vc = s.vs(c.cur);
+                uint32_t trig = 0u;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const int p = q * 128 + lane * 4;
+                    *reinterpret_cast<float4*>(vc + p) = buf[u][q];
+                    trig |= outside4(buf[u][q], *reinterpret_cast<const float4*>(s.vu() + p),
+                                     *reinterpret_cast<const float4*>(s.vd() + p)) << (q * 4);
+                }
+                trig &= valid;
+                if (f + PF < T) load_frame<PPT>(buf[u], fp + (int64_t)(f + PF) * npix, nvq, vec, lane_left, pol_stream);
+                if (init && f == 0) {
+                    for (int k = 0; k < PPT; ++k) {
+                        if (!((valid >> k) & 1u)) continue;
+                        const int p = (k >> 2) * 128 + lane * 4 + (k & 3);
+                        float cp, cn;
+                        thresholds_of(c, p, cp, cn);
+                        const float Lv = model_L(vc[p], c.eps, c.is_log);
+                        s.ref()[p] = Lv;
+                        s.lb()[p] = Lv;
+                        s.vu()[p] = raw_bound_up(__fadd_rn(Lv, cp), c.eps, c.is_log);
+                        s.vd()[p] = raw_bound_dn(__fsub_rn(Lv, cn), c.eps, c.is_log);
+                    }
+                    lvalid = valid;
+                    continue;
+                }
+                const int j = f - init;                       // interval index
+                if (!__any_sync(0xffffffffu, trig != 0u)) {
+                    if (lane == 0) chunk_col[(int64_t)j * n_tiles] = make_uint2(0u, 0u);
+                    lvalid = 0u;
+                    continue;
+                }
+                c.ta = (uint32_t)(ta0 + (j == 0 ? 0 : (int64_t)D0 + (int64_t)(j - 1) * dt));
+                c.Df = (float)(j == 0 ? D0 : dt);
+
+                // trigger list in pixel order: group q, then lane, then component
+                uint32_t packed = 0u;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) packed |= (uint32_t)__popc((trig >> (q * 4)) & 15u) << (q * 8);
+                uint32_t incl = packed;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t nb = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d) incl += nb;
+                }
+                const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+                const uint32_t ex = incl - packed;
+                int n_list = 0;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    int pos = n_list + (int)((ex >> (q * 8)) & 255u);
+                    uint32_t m = (trig >> (q * 4)) & 15u;
+                    while (m) {
+                        const int cbit = __ffs(m) - 1;
+                        m &= m - 1u;
+                        s.list()[pos++] = (uint32_t)(q * 128 + lane * 4 + cbit);
+                    }
+                    n_list += (int)((tot >> (q * 8)) & 255u);
+                }
+                s.lvm()[lane] = lvalid;
+                __syncwarp();
+
+                if (n_list <= 32) {
+                    // one round: lane e handles list entry e
+                    int n = 0;
+                    KeyT k0 = 0, k1 = 0;
+                    int p = 0;
+                    float cp = 0.f, cn = 0.f, a = 0.f, b = 0.f, r0 = 0.f;
+                    uint32_t tl0 = 0u;
+                    if (lane < n_list) {
+                        p = (int)s.list()[lane];
+                        thresholds_of(c, p, cp, cn);
+                        b = model_L(vc[p], c.eps, c.is_log);
+                        a = L_prev(s, c, p);
+                        r0 = s.ref()[p];
+                        tl0 = s.tl()[p];
+                        float r = r0;
+                        uint32_t tl = tl0;
+                        n = pixel_events<1, KeyT>(r, tl, a, b, cp, cn, c.ta, c.Df, c.R,
+                                                  (KeyT)(c.g0 + p) << 1, c.tshift, k0, k1, nullptr);
+                        s.ref()[p] = r;
+                        s.tl()[p] = tl;
+                        s.lb()[p] = b;
+                        s.vu()[p] = raw_bound_up(__fadd_rn(r, cp), c.eps, c.is_log);
+                        s.vd()[p] = raw_bound_dn(__fsub_rn(r, cn), c.eps, c.is_log);
+                    }
+                    int excl_n;
+                    uint32_t total;
+                    if (__any_sync(0xffffffffu, n > 3)) {
+                        int in = n;
+#pragma unroll
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const int nb = __shfl_up_sync(0xffffffffu, in, d);
+                            if (lane >= d) in += nb;
+                        }
+                        excl_n = in - n;
+                        total = (uint32_t)__shfl_sync(0xffffffffu, in, 31);
+                    } else {
+                        const uint32_t b0 = __ballot_sync(0xffffffffu, (n & 1) != 0);
+                        const uint32_t b1 = __ballot_sync(0xffffffffu, (n & 2) != 0);
+                        excl_n = __popc(b0 & lt) + 2 * __popc(b1 & lt);
+                        total = (uint32_t)(__popc(b0) + 2 * __popc(b1));
+                    }
+                    uint32_t base = kNoChunk;
+                    if (total > 0u) {
+                        if (pg_end - pg_cur >= total) {
+                            base = pg_cur;
+                            pg_cur += total;
+                        } else {
+                            const uint32_t np_ = (total + L.page_keys - 1u) / L.page_keys;
+                            uint32_t first = 0u;
+                            if (lane == 0) first = atomicAdd(&L.ctl->page_ctr, np_);
+                            first = __shfl_sync(0xffffffffu, first, 0);
+                            if ((uint64_t)first + np_ <= (uint64_t)L.n_pages) {
+                                base = first * L.page_keys;
+                                pg_cur = base + total;
+                                pg_end = (first + np_) * L.page_keys;
+                            } else {
+                                if (lane == 0) atomicOr(&L.ctl->err, kErrPageOverflow);
+                                pg_cur = pg_end = 0u;
+                            }
+                        }
+                    }
+                    if (lane == 0)
+                        chunk_col[(int64_t)j * n_tiles] =
+                            make_uint2(base == kNoChunk ? 0u : base, base == kNoChunk ? 0u : total);
+                    if (base != kNoChunk && n > 0) {
+                        KeyT* out = keys + (size_t)base + (size_t)excl_n;
+                        if (n <= 2) {
+                            out[0] = k0;
+                            if (n == 2) out[1] = k1;
+                        } else {
+                            float r = r0;
+                            uint32_t tl = tl0;
+                            pixel_events<2, KeyT>(r, tl, a, b, cp, cn, c.ta, c.Df, c.R,
+                                                  (KeyT)(c.g0 + p) << 1, c.tshift, k0, k1, out);
+                        }
+                    }
+                } else {
+                    uint32_t off = 0u, cntv = 0u;
+                    slow_general<PPT, KeyT>(s, c, lane, n_list, keys, L.page_keys, L.n_pages,
+                                            &L.ctl->page_ctr, &L.ctl->err, pg_cur, pg_end, &off, &cntv);
+                    if (lane == 0) chunk_col[(int64_t)j * n_tiles] = make_uint2(off, cntv);
+                }
+                __syncwarp();
+                lvalid = trig;
+            }
+        }
+
+        // shared memory -> state
+        const float* vl = s.vs((T - 1) & 1);
+        for (int k = 0; k < PPT; ++k) {
+            if (!((valid >> k) & 1u)) continue;
+            const int p = (k >> 2) * 128 + lane * 4 + (k & 3);
+            const int g = c.g0 + p;
+            sdp->ref_out[g] = s.ref()[p];
+            sdp->tlast_out[g] = s.tl()[p];
+            sdp->lprev_out[g] = ((lvalid >> k) & 1u) ? s.lb()[p] : model_L(vl[p], c.eps, c.is_log);
+        }
+        __syncwarp();
+    }
+}

@@ -15,7 +15,6 @@ constexpr uint32_t kErrPageOverflow = 1u;   // intermediate key pages exhausted
 constexpr uint32_t kErrOutOverflow = 2u;    // output record buffer exhausted
 constexpr uint32_t kErrTimeout = 4u;        // a bounded mbarrier wait gave up
 
-constexpr int kPPT = 4;                  // pixels per thread (one 16-byte vector)
 constexpr int kMaxTilesPerStream = 8192; // chunk prefix of one segment fits in shared memory
 constexpr int kSortThreads = 512;
 constexpr int kMaxDigitBits = 6;         // radix digit width of the segment sort
@@ -46,7 +45,7 @@ struct StreamDesc {
     int32_t input_is_log;
     uint32_t refractory;          // us; 0 = off
     int32_t W, npix;
-    int32_t n_tiles;              // work items (tiles) of this stream
+    int32_t n_tiles;              // work items (warp tiles of 32*ppt pixels) of this stream
     int32_t item_base;            // index of its first work item in the launch
     int32_t seg_base;             // index of its first segment in the launch
     int32_t n_segs;               // intervals this stream closes in the step
@@ -70,8 +69,8 @@ struct StepLaunch {
     int32_t dt;                     // us
     int32_t key64;                  // 1: 64-bit intermediate keys
     int32_t t_bits;                 // bits of the largest in-interval offset
-    int32_t threads;                // emission CTA size (128, 256, 512)
-    int32_t stages;                 // emission frame stages in shared memory
+    int32_t ppt;                    // emission pixels per lane (8 or 16; warp tile 32*ppt)
+    int32_t pf;                     // frames each lane keeps in flight (2 or 3)
     int32_t grid_emit;
     int32_t grid_sort;
     int32_t sort_smem;              // dynamic shared memory of the sort CTA
@@ -98,9 +97,10 @@ struct StepLaunch {
 // number of kernels launched to *launches.
 cudaError_t launch_step(const StepLaunch& L, uint64_t* launches);
 
-// Emission launch geometry helpers.
-size_t emit_smem_bytes(int threads, int stages);
-cudaError_t emit_occupancy(int threads, int stages, int key64, int* blocks_per_sm);
+// Emission launch geometry helpers (CTA = 64/ppt warps).
+int emit_warps_per_cta(int ppt);
+size_t emit_smem_bytes(int ppt);
+cudaError_t emit_occupancy(int ppt, int pf, int key64, int* blocks_per_sm);
 cudaError_t sort_configure(int* smem_bytes);
 
 // Create-time per-pixel thresholds: C+-_u = max(c_min, C+- + sigma * z+-_u).

@@ -19,13 +19,12 @@
 // contraction or approximation can change a result.
 //
 // Kernels of one step:
-//   emit_kernel     one CTA per tile of THREADS*4 contiguous pixels (grid
-//                   strided over tiles of all streams); the pixel state stays
-//                   in registers across all T frames; frames stream into a
-//                   ring of shared-memory stages by cp.async.bulk with an
-//                   mbarrier per stage; per frame a warp/block scan compacts
-//                   the events of the tile into one contiguous chunk of a
-//                   paged key buffer (one global atomic per page, not per
+//   emit_kernel     (evsim_emit.cuh) one warp per tile of 32*PPT contiguous
+//                   pixels for all T frames, no block-level barriers; a cheap
+//                   per-pixel filter on the raw input, the exact model on a
+//                   warp-converged slow path; the events of a warp tile in
+//                   one interval form one contiguous chunk (pixel order) of
+//                   a paged key buffer (one global atomic per page, not per
 //                   frame); chunk (offset, count) goes to a table indexed by
 //                   (interval, tile).
 //   seg_count       sums the chunk counts of each interval.
@@ -77,140 +76,6 @@ __device__ __forceinline__ float model_log(float x)
     return __fmaf_rn(fe, 0x1.62e4p-1f, tail);                   // ln2 head (16 bits)
 }
 
-__device__ __forceinline__ float to_log(float v, float eps, int is_log)
-{
-    if (is_log) return fminf(fmaxf(v, -32.0f), 32.0f);
-    return model_log(__fadd_rn(fminf(fmaxf(v, 0.0f), 1.0e6f), eps));
-}
-
-// Crossings of one pixel over one interval (a at ta, b at ta + D).  Advances
-// ref and t_last.  EMIT: writes one key per emitted event to out[].
-// Returns the number of emitted events.
-template <bool EMIT, typename KeyT>
-__device__ __forceinline__ int pixel_events(float& r, uint32_t& tl, float a, float b, float cp,
-                                            float cn, uint32_t ta, float Df, uint32_t R,
-                                            KeyT pixkey, int tshift, KeyT* out)
-{
-    int n = 0;
-    if (b > a) {
-        const float den = __fsub_rn(b, a);
-        for (;;) {
-            const float lvl = __fadd_rn(r, cp);
-            if (!(lvl <= b)) break;
-            const float frac = __fdiv_rn(__fsub_rn(lvl, a), den);
-            const float tf = fmaxf(floorf(__fmul_rn(frac, Df)), 0.0f);
-            const uint32_t toff = (uint32_t)tf;
-            const uint32_t t = ta + toff;
-            r = lvl;
-            if (R != 0u && tl != kTlastNone && (int64_t)t - (int64_t)tl < (int64_t)R) continue;
-            if (EMIT) out[n] = ((KeyT)toff << tshift) | pixkey | (KeyT)1;
-            ++n;
-            tl = t;
-        }
-    } else if (b < a) {
-        const float den = __fsub_rn(b, a);
-        for (;;) {
-            const float lvl = __fsub_rn(r, cn);
-            if (!(lvl >= b)) break;
-            const float frac = __fdiv_rn(__fsub_rn(lvl, a), den);
-            const float tf = fmaxf(floorf(__fmul_rn(frac, Df)), 0.0f);
-            const uint32_t toff = (uint32_t)tf;
-            const uint32_t t = ta + toff;
-            r = lvl;
-            if (R != 0u && tl != kTlastNone && (int64_t)t - (int64_t)tl < (int64_t)R) continue;
-            if (EMIT) out[n] = ((KeyT)toff << tshift) | pixkey;
-            ++n;
-            tl = t;
-        }
-    }
-    return n;
-}
-
-// --------------------------------------------------------------------------
-// mbarrier / bulk-copy helpers (inline PTX, sm_90+ forms valid on sm_103a)
-// --------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred P;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, P;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0u;
-}
-
-__device__ __forceinline__ uint64_t global_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Waits for the phase `parity` of `bar` to complete; gives up after limit_ns.
-__device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 31u) == 0u && global_ns() - t0 > limit_ns) return false;
-    }
-}
-
-// As above, with an absolute deadline on the global timer.
-__device__ __noinline__ bool mbar_wait_deadline(uint64_t* bar, uint32_t parity, uint64_t deadline)
-{
-    for (uint32_t it = 0;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 31u) == 31u && global_ns() > deadline) return false;
-    }
-}
-
-__device__ __forceinline__ uint64_t l2_evict_first_policy()
-{
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-// 1-D bulk copy global -> shared (16-byte aligned addresses, size % 16 == 0),
-// completion signalled as transaction bytes on `bar`.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar, uint64_t pol)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 __device__ __forceinline__ const StreamDesc* stream_of_item(const StepLaunch& L, int item)
 {
     if (L.n_streams == 1) return &L.s0;
@@ -238,262 +103,7 @@ __device__ __forceinline__ int64_t interval_start(const StreamDesc& sd, int j, i
     return sd.ta0 + (j == 0 ? 0 : (int64_t)sd.D0 + (int64_t)(j - 1) * dt);
 }
 
-// --------------------------------------------------------------------------
-// Emission kernel
-// --------------------------------------------------------------------------
-template <int THREADS, typename KeyT>
-__global__ void __launch_bounds__(THREADS) emit_kernel(const __grid_constant__ StepLaunch L)
-{
-    constexpr int TILE = THREADS * kPPT;
-    constexpr int NW = THREADS / 32;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float* stage_buf = reinterpret_cast<float*>(smem_raw);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)L.stages * TILE * sizeof(float));
-    __shared__ int s_wtot[NW];
-    __shared__ int s_wexcl[NW];
-    __shared__ uint32_t s_base;
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int S = L.stages;
-    if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&mbar[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-
-    KeyT* const keys = reinterpret_cast<KeyT*>(L.keys);
-    const uint64_t pol = l2_evict_first_policy();
-    uint32_t use = 0;                 // stage uses so far (drives stage index and parity)
-    uint32_t pg_cur = 0, pg_end = 0;  // thread 0: free range of the current key page
-
-    for (int item = blockIdx.x; item < L.n_items; item += gridDim.x) {
-        const StreamDesc* sdp = stream_of_item(L, item);
-        const float* frames = sdp->frames;
-        const int npix = sdp->npix;
-        const int W = sdp->W;
-        (void)W;
-        const int tile = item - sdp->item_base;
-        const int p0 = tile * TILE;
-        const int np = min(TILE, npix - p0);
-        const int my0 = tid * kPPT;
-        const int nv = max(0, min(kPPT, np - my0));
-        const int pix0 = p0 + my0;
-        const int init = sdp->init;
-        const int vec = sdp->vec;
-        const int is_log = sdp->input_is_log;
-        const float eps = sdp->log_eps;
-        const uint32_t R = sdp->refractory;
-        const int tshift = sdp->pix_bits + 1;
-        const int T = L.T;
-        const int64_t chunk_row0 = sdp->chunk_base + tile;
-        const int n_tiles = sdp->n_tiles;
-
-        float ref[kPPT], lp[kPPT], cp[kPPT], cn[kPPT];
-        uint32_t tl[kPPT];
-#pragma unroll
-        for (int k = 0; k < kPPT; ++k) {
-            ref[k] = 0.0f; lp[k] = 0.0f; tl[k] = kTlastNone;
-            cp[k] = sdp->cpos_u; cn[k] = sdp->cneg_u;
-        }
-        if (nv == kPPT) {
-            if (!init) {
-                const float4 r4 = *reinterpret_cast<const float4*>(sdp->ref_in + pix0);
-                const float4 l4 = *reinterpret_cast<const float4*>(sdp->lprev_in + pix0);
-                const uint4 t4 = *reinterpret_cast<const uint4*>(sdp->tlast_in + pix0);
-                ref[0] = r4.x; ref[1] = r4.y; ref[2] = r4.z; ref[3] = r4.w;
-                lp[0] = l4.x; lp[1] = l4.y; lp[2] = l4.z; lp[3] = l4.w;
-                tl[0] = t4.x; tl[1] = t4.y; tl[2] = t4.z; tl[3] = t4.w;
-            }
-            if (sdp->cpos != nullptr) {
-                const float4 a4 = *reinterpret_cast<const float4*>(sdp->cpos + pix0);
-                const float4 b4 = *reinterpret_cast<const float4*>(sdp->cneg + pix0);
-                cp[0] = a4.x; cp[1] = a4.y; cp[2] = a4.z; cp[3] = a4.w;
-                cn[0] = b4.x; cn[1] = b4.y; cn[2] = b4.z; cn[3] = b4.w;
-            }
-        } else {
-            for (int k = 0; k < nv; ++k) {
-                if (!init) {
-                    ref[k] = sdp->ref_in[pix0 + k];
-                    lp[k] = sdp->lprev_in[pix0 + k];
-                    tl[k] = sdp->tlast_in[pix0 + k];
-                }
-                if (sdp->cpos != nullptr) {
-                    cp[k] = sdp->cpos[pix0 + k];
-                    cn[k] = sdp->cneg[pix0 + k];
-                }
-            }
-        }
-
-        // pipeline prologue: frames 0 .. S-1 of this tile into the stage ring
-        const uint32_t tile_bytes = (uint32_t)np * (uint32_t)sizeof(float);
-        if (vec && tid == 0) {
-            const int pre = min(S, T);
-            for (int f = 0; f < pre; ++f) {
-                const uint32_t u = use + (uint32_t)f;
-                const int st = (int)(u % (uint32_t)S);
-                mbar_expect_tx(&mbar[st], tile_bytes);
-                bulk_g2s(stage_buf + (size_t)st * TILE, frames + (int64_t)f * npix + p0, tile_bytes,
-                         &mbar[st], pol);
-            }
-        }
-
-        bool aborted = false;
-        int abort_f = 0;
-        for (int f = 0; f < T; ++f) {
-            float v[kPPT] = {0.0f, 0.0f, 0.0f, 0.0f};
-            bool ok = true;
-            if (vec) {
-                const uint32_t u = use + (uint32_t)f;
-                const int st = (int)(u % (uint32_t)S);
-                ok = mbar_wait_bounded(&mbar[st], (u / (uint32_t)S) & 1u, L.wait_limit_ns);
-                if (ok && nv > 0) {
-                    const float4 q =
-                        *reinterpret_cast<const float4*>(stage_buf + (size_t)st * TILE + my0);
-                    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-                }
-            } else {
-                const float* src = frames + (int64_t)f * npix + pix0;
-                for (int k = 0; k < nv; ++k) v[k] = __ldcs(src + k);
-            }
-
-            float Lv[kPPT];
-#pragma unroll
-            for (int k = 0; k < kPPT; ++k) Lv[k] = to_log(v[k], eps, is_log);
-
-            const bool closes = !(init && f == 0);
-            const int j = f - init;                     // interval index when closes
-            const int D = (j == 0) ? sdp->D0 : L.dt;
-            const float Df = (float)D;
-            const uint32_t ta = closes ? (uint32_t)interval_start(*sdp, j, L.dt) : 0u;
-
-            float r0[kPPT];
-            uint32_t tl0[kPPT];
-            int cnt = 0;
-            if (!closes) {
-#pragma unroll
-                for (int k = 0; k < kPPT; ++k) {
-                    if (k < nv) { ref[k] = Lv[k]; lp[k] = Lv[k]; tl[k] = kTlastNone; }
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < kPPT; ++k) {
-                    r0[k] = ref[k];
-                    tl0[k] = tl[k];
-                    if (k < nv)
-                        cnt += pixel_events<false, KeyT>(ref[k], tl[k], lp[k], Lv[k], cp[k], cn[k],
-                                                         ta, Df, R, (KeyT)0, tshift, nullptr);
-                }
-            }
-
-            // warp inclusive scan of the per-thread counts
-            int incl = cnt;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int nb = __shfl_up_sync(0xffffffffu, incl, d);
-                if (lane >= d) incl += nb;
-            }
-            if (lane == 31) s_wtot[warp] = incl;
-
-            if (__syncthreads_or(!ok)) { aborted = true; abort_f = f; break; }   // barrier A
-
-            if (vec && tid == 0 && f + S < T) {      // refill the stage just consumed
-                const uint32_t u = use + (uint32_t)f;
-                const int st = (int)(u % (uint32_t)S);
-                fence_proxy_async_smem();
-                mbar_expect_tx(&mbar[st], tile_bytes);
-                bulk_g2s(stage_buf + (size_t)st * TILE, frames + (int64_t)(f + S) * npix + p0,
-                         tile_bytes, &mbar[st], pol);
-            }
-
-            if (closes) {
-                if (warp == 0) {
-                    const int w = (lane < NW) ? s_wtot[lane] : 0;
-                    int wi = w;
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const int nb = __shfl_up_sync(0xffffffffu, wi, d);
-                        if (lane >= d) wi += nb;
-                    }
-                    if (lane < NW) s_wexcl[lane] = wi - w;
-                    const int total = __shfl_sync(0xffffffffu, wi, 31);
-                    if (lane == 0) {
-                        uint32_t base = kNoChunk;
-                        if (total > 0) {
-                            if (pg_end - pg_cur >= (uint32_t)total) {
-                                base = pg_cur;
-                                pg_cur += (uint32_t)total;
-                            } else {
-                                const uint32_t k = ((uint32_t)total + L.page_keys - 1u) / L.page_keys;
-                                const uint32_t first = atomicAdd(&L.ctl->page_ctr, k);
-                                if ((uint64_t)first + k <= (uint64_t)L.n_pages) {
-                                    base = first * L.page_keys;
-                                    pg_cur = base + (uint32_t)total;
-                                    pg_end = (first + k) * L.page_keys;
-                                } else {
-                                    atomicOr(&L.ctl->err, kErrPageOverflow);
-                                    pg_cur = pg_end = 0u;
-                                }
-                            }
-                        }
-                        L.chunks[chunk_row0 + (int64_t)j * n_tiles] =
-                            make_uint2(base == kNoChunk ? 0u : base,
-                                       base == kNoChunk ? 0u : (uint32_t)total);
-                        s_base = base;
-                    }
-                }
-                __syncthreads();                                       // barrier B
-                const uint32_t base = s_base;
-                if (cnt > 0 && base != kNoChunk) {
-                    KeyT* out = keys + (size_t)base + (size_t)(s_wexcl[warp] + incl - cnt);
-                    int w = 0;
-#pragma unroll
-                    for (int k = 0; k < kPPT; ++k) {
-                        if (k < nv) {
-                            float rr = r0[k];
-                            uint32_t tt = tl0[k];
-                            w += pixel_events<true, KeyT>(rr, tt, lp[k], Lv[k], cp[k], cn[k], ta, Df,
-                                                          R, (KeyT)(pix0 + k) << 1, tshift, out + w);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < kPPT; ++k) lp[k] = Lv[k];
-            }
-        }
-
-        if (aborted) {
-            // Copies of frames [abort_f, min(T, abort_f + S)) may still be in
-            // flight into this CTA's stages: give them one bounded window to
-            // land before the CTA exits, then report the timeout.
-            if (tid == 0) {
-                atomicOr(&L.ctl->err, kErrTimeout);
-                if (vec) {
-                    const uint64_t deadline = global_ns() + L.wait_limit_ns;
-                    for (int fr = abort_f; fr < min(T, abort_f + S); ++fr) {
-                        const uint32_t u = use + (uint32_t)fr;
-                        if (!mbar_wait_deadline(&mbar[u % (uint32_t)S], (u / (uint32_t)S) & 1u, deadline))
-                            break;
-                    }
-                }
-            }
-            __syncthreads();
-            return;
-        }
-        if (vec) use += (uint32_t)T;
-
-        if (nv == kPPT) {
-            *reinterpret_cast<float4*>(sdp->ref_out + pix0) = make_float4(ref[0], ref[1], ref[2], ref[3]);
-            *reinterpret_cast<float4*>(sdp->lprev_out + pix0) = make_float4(lp[0], lp[1], lp[2], lp[3]);
-            *reinterpret_cast<uint4*>(sdp->tlast_out + pix0) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
-        } else {
-            for (int k = 0; k < nv; ++k) {
-                sdp->ref_out[pix0 + k] = ref[k];
-                sdp->lprev_out[pix0 + k] = lp[k];
-                sdp->tlast_out[pix0 + k] = tl[k];
-            }
-        }
-    }
-}
+#include "evsim_emit.cuh"
 
 // --------------------------------------------------------------------------
 // Segment sizes and offsets
@@ -837,43 +447,51 @@ __global__ void debug_log_kernel(const float* x, float* y, int64_t n)
         y[i] = model_log(x[i]);
 }
 
-template <int THREADS>
+template <int PPT, int PF>
 cudaError_t launch_emit_t(const StepLaunch& L, size_t smem)
 {
-    if (L.key64) {
-        auto k = emit_kernel<THREADS, uint64_t>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<L.grid_emit, THREADS, smem, L.stream>>>(L);
-    } else {
-        auto k = emit_kernel<THREADS, uint32_t>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<L.grid_emit, THREADS, smem, L.stream>>>(L);
-    }
+    constexpr int WARPS = 64 / PPT;
+    const void* fn = L.key64 ? (const void*)emit_kernel<PPT, WARPS, PF, uint64_t>
+                             : (const void*)emit_kernel<PPT, WARPS, PF, uint32_t>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (L.key64)
+        emit_kernel<PPT, WARPS, PF, uint64_t><<<L.grid_emit, WARPS * 32, smem, L.stream>>>(L);
+    else
+        emit_kernel<PPT, WARPS, PF, uint32_t><<<L.grid_emit, WARPS * 32, smem, L.stream>>>(L);
     return cudaGetLastError();
+}
+
+const void* emit_fn(int ppt, int pf, int key64)
+{
+#define NSIM_PICK(P, F)                                                                    \
+    if (ppt == P && pf == F)                                                               \
+        return key64 ? (const void*)emit_kernel<P, 64 / P, F, uint64_t>                   \
+                     : (const void*)emit_kernel<P, 64 / P, F, uint32_t>;
+    NSIM_PICK(8, 2) NSIM_PICK(8, 3) NSIM_PICK(16, 2) NSIM_PICK(16, 3)
+#undef NSIM_PICK
+    return nullptr;
 }
 
 }  // namespace
 
-size_t emit_smem_bytes(int threads, int stages)
+int emit_warps_per_cta(int ppt) { return 64 / ppt; }
+
+size_t emit_smem_bytes(int ppt)
 {
-    return (size_t)stages * threads * kPPT * sizeof(float) + (size_t)stages * sizeof(uint64_t);
+    const size_t per_warp = (ppt == 8) ? WarpSlice<8>::FLOATS : WarpSlice<16>::FLOATS;
+    return (size_t)emit_warps_per_cta(ppt) * per_warp * sizeof(float);
 }
 
-cudaError_t emit_occupancy(int threads, int stages, int key64, int* blocks_per_sm)
+cudaError_t emit_occupancy(int ppt, int pf, int key64, int* blocks_per_sm)
 {
-    const size_t smem = emit_smem_bytes(threads, stages);
-    const void* fn = nullptr;
-#define NSIM_PICK(TH)                                                                      \
-    if (threads == TH)                                                                     \
-        fn = key64 ? (const void*)emit_kernel<TH, uint64_t> : (const void*)emit_kernel<TH, uint32_t>;
-    NSIM_PICK(128) NSIM_PICK(256) NSIM_PICK(512)
-#undef NSIM_PICK
+    const void* fn = emit_fn(ppt, pf, key64);
     if (!fn) return cudaErrorInvalidValue;
+    const size_t smem = emit_smem_bytes(ppt);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, emit_warps_per_cta(ppt) * 32,
+                                                         smem);
 }
 
 cudaError_t sort_configure(int* smem_bytes)
@@ -898,13 +516,12 @@ cudaError_t launch_step(const StepLaunch& L, uint64_t* launches)
 {
     cudaError_t e = cudaSuccess;
     if (L.ev_begin && (e = cudaEventRecord(L.ev_begin, L.stream)) != cudaSuccess) return e;
-    const size_t smem = emit_smem_bytes(L.threads, L.stages);
-    switch (L.threads) {
-    case 128: e = launch_emit_t<128>(L, smem); break;
-    case 256: e = launch_emit_t<256>(L, smem); break;
-    case 512: e = launch_emit_t<512>(L, smem); break;
-    default: return cudaErrorInvalidValue;
-    }
+    const size_t smem = emit_smem_bytes(L.ppt);
+    if (L.ppt == 8 && L.pf == 2) e = launch_emit_t<8, 2>(L, smem);
+    else if (L.ppt == 8 && L.pf == 3) e = launch_emit_t<8, 3>(L, smem);
+    else if (L.ppt == 16 && L.pf == 2) e = launch_emit_t<16, 2>(L, smem);
+    else if (L.ppt == 16 && L.pf == 3) e = launch_emit_t<16, 3>(L, smem);
+    else return cudaErrorInvalidValue;
     if (e != cudaSuccess) return e;
     *launches += 1;
     if (L.ev_emitted && (e = cudaEventRecord(L.ev_emitted, L.stream)) != cudaSuccess) return e;

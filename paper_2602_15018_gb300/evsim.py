@@ -29,7 +29,7 @@ class EventSim:
                  log_eps: float = 1e-3, input_is_log: bool = False, seed: int = 0,
                  c_pos_map=None, c_neg_map=None, event_capacity: int = 0,
                  max_frames_per_step: int = 0, max_pending_intervals: int = 0,
-                 threads_per_block: int = 0, pipeline_stages: int = 0,
+                 pixels_per_thread: int = 0, prefetch_frames: int = 0,
                  stream: torch.cuda.Stream | None = None, device=None):
         L = lib()
         self.W, self.H = int(width), int(height)
@@ -53,8 +53,8 @@ class EventSim:
         p.event_capacity = int(event_capacity)
         p.max_frames_per_step = int(max_frames_per_step)
         p.max_pending_intervals = int(max_pending_intervals)
-        p.threads_per_block = int(threads_per_block)
-        p.pipeline_stages = int(pipeline_stages)
+        p.pixels_per_thread = int(pixels_per_thread)
+        p.prefetch_frames = int(prefetch_frames)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream()
             h = C.c_void_p()

@@ -126,14 +126,14 @@ def test_config1_sinusoids_240x180_full():
         g.close()
 
 
-@pytest.mark.parametrize("W,H,threads", [(320, 181, 256), (346, 260, 128), (33, 17, 256),
-                                         (7, 5, 128), (1024, 1, 512), (1, 700, 256)])
-def test_texture_odd_sizes(W, H, threads):
+@pytest.mark.parametrize("W,H,ppt,pf", [(320, 181, 16, 2), (346, 260, 8, 3), (33, 17, 16, 3),
+                                         (7, 5, 8, 2), (1024, 1, 16, 2), (1, 700, 8, 2)])
+def test_texture_odd_sizes(W, H, ppt, pf):
     """Ragged tiles, frames that are not 16-byte aligned per row (W*H % 4 != 0)."""
     T = 40
     fr = scenes.render_frames(scenes.TextureScene(W, H, seed=W + H, speed=(300., 600.)), T)
     kw = dict(c_pos=0.2, c_neg=0.25, sigma_c=0.03, refractory_us=100, seed=W * 7 + H,
-              max_frames_per_step=T, threads_per_block=threads)
+              max_frames_per_step=T, pixels_per_thread=ppt, prefetch_frames=pf)
     g, o = _sims(W, H, **kw)
     g.step(fr.cuda(), 5000, DT)
     ev, seg = g.drain()
