@@ -186,6 +186,49 @@ int32_t neurosim_abi_version(void);
  * floats x_dev into y_dev on cuda_stream; for verification of the log. */
 int neurosim_debug_log(const float *x_dev, float *y_dev, int64_t n, void *cuda_stream);
 
+/* One step of the event model that allocates nothing.  The paper has no
+ * counterpart: this is a library convenience for callers that cannot call
+ * cudaMalloc (code inside a CUDA graph being captured, real-time loops that
+ * must never enter the allocator, hosts that only borrow device buffers).
+ * The caller owns every buffer; the library keeps its intermediates (event
+ * keys, chunk table, per-interval counts, control block) in one fixed 32 MiB
+ * device array compiled into the library (held by every GPU that loads it,
+ * until exit).
+ *
+ * Inputs (DEVICE memory unless noted): frames_dev FP32 [n_frames][height]
+ * [width] at times t0_us + f * dt_us; thresholds c_pos_dev / c_neg_dev
+ * (height*width each, 16-byte aligned) or both NULL for the uniform c_pos /
+ * c_neg (>= 1e-3); refractory_us, log_eps, input_is_log as in the params.
+ * State: with has_prev = 1, ref_in / lprev_in / tlast_in hold the state after
+ * the frame at tau_prev (as returned by a previous call); with has_prev = 0
+ * the first frame initialises the state and emits nothing.  The new state is
+ * written to ref_out / lprev_out / tlast_out (all 16-byte aligned; they must
+ * not overlap the input arrays, so that a failed call can be repeated from
+ * the same inputs).  Outputs: events_dev receives the step's records in
+ * output order (capacity events_capacity), seg_offsets_dev the n_intervals + 1
+ * DEVICE int64 offsets (n_intervals = n_frames - 1 + has_prev), *n_events
+ * (HOST) the record count.
+ * Errors: NEUROSIM_E_INVALID for bad sizes, NULL or misaligned pointers and
+ * for steps whose chunk table (n_intervals x ceil(width*height / 512) entries)
+ * does not fit half of the fixed array; NEUROSIM_E_OVERFLOW when the events
+ * exceed events_capacity (*n_events = the count needed) or the array's key
+ * area — then the outputs are not usable and the call can be repeated with a
+ * larger buffer or fewer frames.  Synchronises cuda_stream before returning.
+ * Every call shares the one array and it keeps the last call's contents (the
+ * control block is cleared at the start of each call): calls whose GPU work
+ * overlaps — on different streams with no order between them — race.  The
+ * first call on a device looks up the array's device address and sets up the
+ * kernels; make it before any stream capture. */
+int neurosim_evsim_step_noalloc(const float *frames_dev, int32_t n_frames, int32_t width,
+                                int32_t height, int64_t t0_us, int32_t dt_us,
+                                const float *c_pos_dev, const float *c_neg_dev, float c_pos,
+                                float c_neg, uint32_t refractory_us, float log_eps,
+                                int32_t input_is_log, const float *ref_in, const float *lprev_in,
+                                const uint32_t *tlast_in, float *ref_out, float *lprev_out,
+                                uint32_t *tlast_out, int32_t has_prev, int64_t tau_prev,
+                                uint64_t *events_dev, uint64_t events_capacity,
+                                int64_t *seg_offsets_dev, uint64_t *n_events, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

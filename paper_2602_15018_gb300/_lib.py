@@ -24,6 +24,7 @@ EXPORTS = [
     "neurosim_evsim_get_state", "neurosim_evsim_set_state", "neurosim_evsim_get_thresholds",
     "neurosim_evsim_destroy", "neurosim_last_error", "neurosim_abi_version",
     "neurosim_debug_log", "neurosim_evsim_set_profiling", "neurosim_evsim_get_stats",
+    "neurosim_evsim_step_noalloc",
 ]
 
 
@@ -101,6 +102,11 @@ def lib():
             L.neurosim_evsim_set_profiling.argtypes = [vp, i32]
             L.neurosim_evsim_get_stats.restype = C.c_int
             L.neurosim_evsim_get_stats.argtypes = [vp, C.POINTER(Stats)]
+            L.neurosim_evsim_step_noalloc.restype = C.c_int
+            L.neurosim_evsim_step_noalloc.argtypes = [
+                vp, i32, i32, i32, i64, i32, vp, vp, C.c_float, C.c_float, C.c_uint32,
+                C.c_float, i32, vp, vp, vp, vp, vp, vp, i32, i64, vp, u64, vp,
+                C.POINTER(u64), vp]
             _lib = L
     return _lib
 

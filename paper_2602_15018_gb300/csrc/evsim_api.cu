@@ -425,6 +425,11 @@ int resolve(neurosim_evsim* h, Ctl* c)
 
 }  // namespace
 
+namespace nsim {
+// Sets the calling thread's last-error message (used by the other C-ABI units).
+int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace nsim
+
 extern "C" {
 
 void neurosim_evsim_default_params(neurosim_evsim_params* p)

@@ -111,4 +111,10 @@ cudaError_t launch_threshold_maps(float* cpos, float* cneg, int64_t npix, float 
 // Debug/verification: y = library log(x).
 cudaError_t launch_debug_log(const float* x, float* y, int64_t n, cudaStream_t stream);
 
+// *dst = ctl->run_total (closing offset of the interval list), on `stream`.
+cudaError_t launch_write_total(const Ctl* ctl, int64_t* dst, cudaStream_t stream);
+
+// Sets the calling thread's neurosim_last_error() message; returns `code`.
+int report_error(int code, const char* msg);
+
 }  // namespace nsim

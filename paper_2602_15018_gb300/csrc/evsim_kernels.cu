@@ -447,6 +447,12 @@ __global__ void debug_log_kernel(const float* x, float* y, int64_t n)
         y[i] = model_log(x[i]);
 }
 
+// Closing offset of the interval list: the record count after the step.
+__global__ void write_total_kernel(const Ctl* ctl, int64_t* dst)
+{
+    *dst = (int64_t)ctl->run_total;
+}
+
 template <int PPT, int PF>
 cudaError_t launch_emit_t(const StepLaunch& L, size_t smem)
 {
@@ -558,6 +564,12 @@ cudaError_t launch_debug_log(const float* x, float* y, int64_t n, cudaStream_t s
     int64_t blocks = (n + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
     debug_log_kernel<<<(unsigned)blocks, threads, 0, stream>>>(x, y, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_write_total(const Ctl* ctl, int64_t* dst, cudaStream_t stream)
+{
+    write_total_kernel<<<1, 1, 0, stream>>>(ctl, dst);
     return cudaGetLastError();
 }
 
