@@ -179,8 +179,10 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     wl = WORKLOADS[args.workload]
     W, H, T = wl["dims"]["W"], wl["dims"]["H"], wl["dims"]["T"]
+    if args.frames:
+        T = args.frames     # shorter clip of the same scene (small profiling cases)
     npix = W * H
-    frames = wl["render"](seed=args.seed + rank, device=dev)
+    frames = wl["render"](seed=args.seed + rank, device=dev, n_frames=T)
     # Steps alternate forward and time-reversed playback of the rendered clip,
     # so that every step continues the previous one without a scene cut.
     frames_rev = frames.flip(0).contiguous()
@@ -419,7 +421,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="hd")
@@ -427,6 +429,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-frames", type=int, default=480)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="frames per step (default: the workload's); for small profiling cases")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
