@@ -176,6 +176,132 @@ int neurosim_evsim_set_profiling(neurosim_evsim *h, int32_t enable);
 /* Synchronises the handle's stream and fills *out. */
 int neurosim_evsim_get_stats(neurosim_evsim *h, neurosim_evsim_stats *out);
 
+/* ------------------------------------------------------------------------
+ * Batched sensors: many independent streams in one launch per step.
+ *
+ * Sec. 4 (event-based RL paragraph) and the RL appendix run several
+ * independent simulation instances concurrently on one GPU; a batch steps
+ * all of their event cameras together: one emission launch over a flattened
+ * (stream, tile) work list, one interval sort over every (stream, interval),
+ * streams of different resolutions and parameters side by side.  Each
+ * stream's events are exactly those of a single-stream simulator fed the
+ * same frames.
+ *
+ * Every step consumes frames_per_step frames per stream from device buffers
+ * registered with neurosim_evsim_batch_set_frames.  Everything that changes
+ * from step to step (times, state buffer, pending intervals, record count)
+ * lives in device memory, so neurosim_evsim_batch_step allocates nothing,
+ * never synchronises, and may be captured into a CUDA graph on the batch's
+ * stream and replayed; the caller refills the registered frame buffers
+ * between replays.  Frame j of step k (k = 0, 1, ...) is at
+ * t0_us + (1 + k * frames_per_step + j) * dt_us; frame t0_us is the one
+ * given to neurosim_evsim_batch_init.
+ * ---------------------------------------------------------------------- */
+typedef struct neurosim_evsim_batch neurosim_evsim_batch;
+
+typedef struct {
+    int32_t n_streams;           /* >= 1                                          */
+    int32_t frames_per_step;     /* T >= 1, frames per stream per step            */
+    int32_t dt_us;               /* frame spacing, 1 <= dt_us < 2^24              */
+    int32_t max_pending_steps;   /* steps that may run between drains (0 = 4)     */
+    int64_t t0_us;               /* time of the initialising frame, >= 0          */
+    uint64_t event_capacity;     /* records kept between drains (0 = auto:
+                                    sum(W*H) * T * max_pending_steps / 16)        */
+    int32_t pixels_per_thread;   /* emission tile: 0 (16), 8 or 16                */
+    int32_t prefetch_frames;     /* frames in flight per lane: 0 (2), 2 or 3      */
+    int32_t reserved[6];         /* must be zero                                  */
+} neurosim_evsim_batch_params;
+
+/* Fills *p with defaults (n_streams 1, T 16, dt 1000 us). */
+void neurosim_evsim_batch_default_params(neurosim_evsim_batch_params *p);
+
+/* Creates a batch of bp->n_streams sensors; streams[i] describes sensor i
+ * exactly as for neurosim_evsim_create (its event_capacity,
+ * max_frames_per_step, max_pending_intervals, pixels_per_thread and
+ * prefetch_frames are ignored; threshold maps are copied).  Device work runs
+ * on cuda_stream (NULL = legacy default stream).  Errors: NEUROSIM_E_INVALID
+ * (params), NEUROSIM_E_NOMEM, NEUROSIM_E_CUDA. */
+int neurosim_evsim_batch_create(const neurosim_evsim_params *streams,
+                                const neurosim_evsim_batch_params *bp, void *cuda_stream,
+                                neurosim_evsim_batch **out);
+
+/* Registers the frame buffers the steps read: frames_dev is a HOST array of
+ * n_streams DEVICE pointers, stream i's buffer holding frames_per_step FP32
+ * frames [T][H_i][W_i].  The buffers stay owned by the caller and must stay
+ * valid while steps that read them may run.  Synchronises the batch's
+ * stream; not capturable.  NEUROSIM_E_INVALID for a NULL pointer. */
+int neurosim_evsim_batch_set_frames(neurosim_evsim_batch *b, const float *const *frames_dev);
+
+/* Initialises every stream from one frame at t0_us (HOST array of n_streams
+ * DEVICE pointers to one [H_i][W_i] FP32 frame each): ref = L_prev = L, no
+ * events.  Enqueued on the batch's stream.  NEUROSIM_E_STATE if the batch
+ * was initialised already. */
+int neurosim_evsim_batch_init(neurosim_evsim_batch *b, const float *const *first_frames_dev);
+
+/* Enqueues one step over the registered buffers (emission, interval count,
+ * scan, sort and the device clock's advance: 5 kernels).  Capturable.  If a
+ * step overflows a capacity, it and every later step are dropped on the
+ * device (state, clock and pending intervals stay as after the last good
+ * step) and the next drain reports it.  NEUROSIM_E_STATE before init or
+ * set_frames. */
+int neurosim_evsim_batch_step(neurosim_evsim_batch *b);
+
+/* Synchronises; *n_events = records of the committed steps since the last
+ * drain, *n_segments = their intervals (steps * n_streams * T). */
+int neurosim_evsim_batch_pending(neurosim_evsim_batch *b, uint64_t *n_events, int64_t *n_segments);
+
+/* Synchronises and hands out the committed records: out (capacity records;
+ * DEVICE memory if out_is_device, else HOST) receives them in order step,
+ * stream, interval, then (t, y, x, p); seg_offsets (HOST, nullable,
+ * seg_capacity >= n_segments + 1) receives the n_segments + 1 offsets of
+ * the (step, stream, interval) segments in that order.  Clears the pending
+ * records.  If a step was dropped, delivers the committed records, clears
+ * the condition and returns NEUROSIM_E_OVERFLOW (records, keys or pending
+ * intervals; the message names which and the demand) or NEUROSIM_E_TIME;
+ * the caller re-runs the dropped steps' frames, on a larger batch if the
+ * capacity was the cause.  NEUROSIM_E_OVERFLOW with nothing copied if
+ * capacity < n_events or seg_capacity is too small. */
+int neurosim_evsim_batch_drain(neurosim_evsim_batch *b, void *out, uint64_t capacity,
+                               int32_t out_is_device, uint64_t *n_out, int64_t *seg_offsets,
+                               int64_t seg_capacity, int64_t *n_segments);
+
+/* Copies stream i's state after the last committed step to HOST arrays of
+ * W_i*H_i entries (ref, L_prev, t_last with 0xFFFFFFFF = none) and *tau_us
+ * (time of the last frame consumed).  Synchronises. */
+int neurosim_evsim_batch_get_state(neurosim_evsim_batch *b, int32_t stream, float *ref,
+                                   float *lprev, uint32_t *tlast, int64_t *tau_us);
+
+/* Copies stream i's per-pixel thresholds to HOST arrays of W_i*H_i floats. */
+int neurosim_evsim_batch_get_thresholds(neurosim_evsim_batch *b, int32_t stream, float *c_pos,
+                                        float *c_neg);
+
+/* Kernel launches enqueued by the batch so far (*launches) and committed
+ * steps (*steps, synchronises). */
+int neurosim_evsim_batch_counters(neurosim_evsim_batch *b, uint64_t *launches, uint64_t *steps);
+
+/* Frees the batch (synchronises its stream first). */
+void neurosim_evsim_batch_destroy(neurosim_evsim_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Autotuner: picks the emission tile (pixels_per_thread) and the frame
+ * prefetch depth for a workload by timing every variant on the caller's
+ * frames.  The paper has no autotuner (it fixes one thread per pixel).
+ *
+ * Times `repeats` (>= 1) steps of n_frames frames (DEVICE [T][H][W] FP32 at
+ * spacing dt_us) with each variant on a fresh simulator of params p (the
+ * params' pixels_per_thread / prefetch_frames are ignored) and keeps the one
+ * with the smallest median emission + sort time; all variants produce the
+ * same events.  If cache_path is not NULL, a result cached there for this
+ * GPU model, width, height and n_frames is returned without timing, and a
+ * new result is appended to it (one JSON object per line:
+ * {"gpu": ..., "width": W, "height": H, "frames": T, "pixels_per_thread": P,
+ *  "prefetch_frames": F, "ms": M}).  *ms_out (nullable) gets the winner's
+ * median time.  Returns NEUROSIM_E_INVALID / NEUROSIM_E_CUDA / NEUROSIM_E_NOMEM. */
+int neurosim_evsim_autotune(const neurosim_evsim_params *p, const float *frames_dev,
+                            int32_t n_frames, int32_t dt_us, int32_t repeats,
+                            const char *cache_path, int32_t *pixels_per_thread,
+                            int32_t *prefetch_frames, double *ms_out);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *neurosim_last_error(void);
 

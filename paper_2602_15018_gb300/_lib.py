@@ -25,6 +25,11 @@ EXPORTS = [
     "neurosim_evsim_destroy", "neurosim_last_error", "neurosim_abi_version",
     "neurosim_debug_log", "neurosim_evsim_set_profiling", "neurosim_evsim_get_stats",
     "neurosim_evsim_step_noalloc",
+    "neurosim_evsim_batch_default_params", "neurosim_evsim_batch_create",
+    "neurosim_evsim_batch_set_frames", "neurosim_evsim_batch_init", "neurosim_evsim_batch_step",
+    "neurosim_evsim_batch_pending", "neurosim_evsim_batch_drain", "neurosim_evsim_batch_get_state",
+    "neurosim_evsim_batch_get_thresholds", "neurosim_evsim_batch_counters",
+    "neurosim_evsim_batch_destroy", "neurosim_evsim_autotune",
 ]
 
 
@@ -45,6 +50,16 @@ class Params(C.Structure):
         ("event_capacity", C.c_uint64), ("max_frames_per_step", C.c_int32),
         ("max_pending_intervals", C.c_int32), ("pixels_per_thread", C.c_int32),
         ("prefetch_frames", C.c_int32), ("reserved", C.c_int32 * 6),
+    ]
+
+
+class BatchParams(C.Structure):
+    """Mirror of neurosim_evsim_batch_params."""
+    _fields_ = [
+        ("n_streams", C.c_int32), ("frames_per_step", C.c_int32), ("dt_us", C.c_int32),
+        ("max_pending_steps", C.c_int32), ("t0_us", C.c_int64), ("event_capacity", C.c_uint64),
+        ("pixels_per_thread", C.c_int32), ("prefetch_frames", C.c_int32),
+        ("reserved", C.c_int32 * 6),
     ]
 
 
@@ -107,6 +122,34 @@ def lib():
                 vp, i32, i32, i32, i64, i32, vp, vp, C.c_float, C.c_float, C.c_uint32,
                 C.c_float, i32, vp, vp, vp, vp, vp, vp, i32, i64, vp, u64, vp,
                 C.POINTER(u64), vp]
+            L.neurosim_evsim_batch_default_params.restype = None
+            L.neurosim_evsim_batch_default_params.argtypes = [C.POINTER(BatchParams)]
+            L.neurosim_evsim_batch_create.restype = C.c_int
+            L.neurosim_evsim_batch_create.argtypes = [C.POINTER(Params), C.POINTER(BatchParams), vp,
+                                                      C.POINTER(vp)]
+            L.neurosim_evsim_batch_set_frames.restype = C.c_int
+            L.neurosim_evsim_batch_set_frames.argtypes = [vp, C.POINTER(vp)]
+            L.neurosim_evsim_batch_init.restype = C.c_int
+            L.neurosim_evsim_batch_init.argtypes = [vp, C.POINTER(vp)]
+            L.neurosim_evsim_batch_step.restype = C.c_int
+            L.neurosim_evsim_batch_step.argtypes = [vp]
+            L.neurosim_evsim_batch_pending.restype = C.c_int
+            L.neurosim_evsim_batch_pending.argtypes = [vp, C.POINTER(u64), C.POINTER(i64)]
+            L.neurosim_evsim_batch_drain.restype = C.c_int
+            L.neurosim_evsim_batch_drain.argtypes = [vp, vp, u64, i32, C.POINTER(u64),
+                                                     C.POINTER(i64), i64, C.POINTER(i64)]
+            L.neurosim_evsim_batch_get_state.restype = C.c_int
+            L.neurosim_evsim_batch_get_state.argtypes = [vp, i32, f32p, f32p, u32p, C.POINTER(i64)]
+            L.neurosim_evsim_batch_get_thresholds.restype = C.c_int
+            L.neurosim_evsim_batch_get_thresholds.argtypes = [vp, i32, f32p, f32p]
+            L.neurosim_evsim_batch_counters.restype = C.c_int
+            L.neurosim_evsim_batch_counters.argtypes = [vp, C.POINTER(u64), C.POINTER(u64)]
+            L.neurosim_evsim_batch_destroy.restype = None
+            L.neurosim_evsim_batch_destroy.argtypes = [vp]
+            L.neurosim_evsim_autotune.restype = C.c_int
+            L.neurosim_evsim_autotune.argtypes = [C.POINTER(Params), vp, i32, i32, i32, C.c_char_p,
+                                                  C.POINTER(i32), C.POINTER(i32),
+                                                  C.POINTER(C.c_double)]
             _lib = L
     return _lib
 

@@ -428,6 +428,8 @@ int resolve(neurosim_evsim* h, Ctl* c)
 namespace nsim {
 // Sets the calling thread's last-error message (used by the other C-ABI units).
 int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+// Checks one sensor's parameters as neurosim_evsim_create does (batches).
+int validate_stream_params(const neurosim_evsim_params* p) { return validate(p); }
 }  // namespace nsim
 
 extern "C" {

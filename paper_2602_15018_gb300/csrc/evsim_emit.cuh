@@ -346,6 +346,7 @@ __global__ void __launch_bounds__(WARPS * 32) emit_kernel(const __grid_constant_
     const uint64_t pol_keep = policy_evict_last();
     const int gw = blockIdx.x * WARPS + wib;
     const int nw = gridDim.x * WARPS;
+    if (step_stopped(L)) return;
 
     for (int item = gw; item < L.n_items; item += nw) {
         const StreamDesc* sdp = stream_of_item(L, item);
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(WARPS * 32) emit_kernel(const __grid_constant_
         const int T = L.T;
         const int dt = L.dt;
         const int D0 = sdp->D0;
-        const int64_t ta0 = sdp->ta0;
+        const int64_t ta0 = step_ta0(L, *sdp);
         uint2* const chunk_col = L.chunks + sdp->chunk_base + tile;
         const int n_tiles = sdp->n_tiles;
         TileCtx c;

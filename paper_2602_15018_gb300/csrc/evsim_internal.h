@@ -29,6 +29,23 @@ struct Ctl {
     unsigned int pad;
 };
 
+constexpr uint32_t kErrPendingOverflow = 8u;  // pending interval offsets exhausted (device clock)
+constexpr uint32_t kErrTime = 16u;            // device clock left the 32-bit timestamp range
+
+// Device-side clock of a batch whose steps run from captured CUDA graphs:
+// everything that changes from one step to the next lives here, so that the
+// same launches can be replayed.  Advanced by advance_kernel after a step
+// that raised no error; a failed step sets `sticky`, and every later step
+// does nothing until the host drains and clears it.
+struct DevClock {
+    long long tau;                        // time of the last frame consumed (us)
+    long long pending_segs;               // interval offsets written since the last drain
+    unsigned long long committed_total;   // records of committed steps since the last drain
+    unsigned long long steps;             // committed steps
+    unsigned int parity;                  // state buffer holding the current state
+    unsigned int sticky;                  // kErr* bits of the failed step, 0 if none
+};
+
 // One sensor stream inside a step launch.
 struct StreamDesc {
     const float* frames;          // [T][npix] FP32 (device)
@@ -88,13 +105,19 @@ struct StepLaunch {
     Ctl* ctl;
     cudaStream_t stream;
     uint64_t wait_limit_ns;         // bound of every device-side wait
+    DevClock* clock;                // device clock (batches), or nullptr: times,
+                                    // parity and pending offsets come from the host
+    int64_t max_pending;            // capacity of seg_off_out in intervals (device clock)
+    int64_t tau_init;               // device clock: an init launch sets tau to this
     cudaEvent_t ev_begin;           // optional timing events (nullptr: none):
     cudaEvent_t ev_emitted;         //   before emission, after emission,
     cudaEvent_t ev_sorted;          //   after the interval sort
 };
 
-// Enqueues emission, segment count, segment scan and segment sort; adds the
-// number of kernels launched to *launches.
+// Enqueues emission, segment count, segment scan and segment sort (and, with
+// a device clock, the clock advance); adds the number of kernels launched to
+// *launches.  With a device clock, streams_dev holds two descriptor sets of
+// n_streams entries: set `parity` reads the state from its *_in buffers.
 cudaError_t launch_step(const StepLaunch& L, uint64_t* launches);
 
 // Emission launch geometry helpers (CTA = 64/ppt warps).

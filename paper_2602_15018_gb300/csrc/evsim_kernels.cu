@@ -76,31 +76,53 @@ __device__ __forceinline__ float model_log(float x)
     return __fmaf_rn(fe, 0x1.62e4p-1f, tail);                   // ln2 head (16 bits)
 }
 
+// Descriptor set of this launch: the host's s0, or the device array (with a
+// device clock, the set whose *_in buffers hold the current state).
+__device__ __forceinline__ const StreamDesc* stream_set(const StepLaunch& L)
+{
+    return L.clock ? L.streams_dev + (size_t)(L.clock->parity & 1u) * L.n_streams : L.streams_dev;
+}
+
 __device__ __forceinline__ const StreamDesc* stream_of_item(const StepLaunch& L, int item)
 {
-    if (L.n_streams == 1) return &L.s0;
+    if (L.streams_dev == nullptr) return &L.s0;
+    const StreamDesc* sd = stream_set(L);
     int lo = 0, hi = L.n_streams - 1;            // last stream with item_base <= item
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (L.streams_dev[mid].item_base <= item) lo = mid; else hi = mid - 1;
+        if (sd[mid].item_base <= item) lo = mid; else hi = mid - 1;
     }
-    return &L.streams_dev[lo];
+    return &sd[lo];
 }
 
 __device__ __forceinline__ const StreamDesc* stream_of_seg(const StepLaunch& L, int seg)
 {
-    if (L.n_streams == 1) return &L.s0;
+    if (L.streams_dev == nullptr) return &L.s0;
+    const StreamDesc* sd = stream_set(L);
     int lo = 0, hi = L.n_streams - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (L.streams_dev[mid].seg_base <= seg) lo = mid; else hi = mid - 1;
+        if (sd[mid].seg_base <= seg) lo = mid; else hi = mid - 1;
     }
-    return &L.streams_dev[lo];
+    return &sd[lo];
 }
 
-__device__ __forceinline__ int64_t interval_start(const StreamDesc& sd, int j, int dt)
+// Start time of the step's first interval: the host's value, or the device
+// clock (time of the last frame consumed).
+__device__ __forceinline__ int64_t step_ta0(const StepLaunch& L, const StreamDesc& sd)
 {
-    return sd.ta0 + (j == 0 ? 0 : (int64_t)sd.D0 + (int64_t)(j - 1) * dt);
+    return L.clock ? (int64_t)L.clock->tau : sd.ta0;
+}
+
+// Device clock: a failed earlier step stops every later one.
+__device__ __forceinline__ bool step_stopped(const StepLaunch& L)
+{
+    return L.clock != nullptr && L.clock->sticky != 0u;
+}
+
+__device__ __forceinline__ int64_t interval_start(int64_t ta0, const StreamDesc& sd, int j, int dt)
+{
+    return ta0 + (j == 0 ? 0 : (int64_t)sd.D0 + (int64_t)(j - 1) * dt);
 }
 
 #include "evsim_emit.cuh"
@@ -113,7 +135,7 @@ __global__ void seg_count_kernel(const __grid_constant__ StepLaunch L)
     const int warps = blockDim.x >> 5;
     const int seg = blockIdx.x * warps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (seg >= L.n_segs) return;
+    if (seg >= L.n_segs || step_stopped(L)) return;
     const StreamDesc* sdp = stream_of_seg(L, seg);
     const int j = seg - sdp->seg_base;
     const uint2* row = L.chunks + sdp->chunk_base + (int64_t)j * sdp->n_tiles;
@@ -131,7 +153,11 @@ __global__ void __launch_bounds__(1024) seg_scan_kernel(const __grid_constant__ 
     __shared__ unsigned long long s_w[32];
     __shared__ unsigned long long s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (step_stopped(L)) return;
     const unsigned long long base = L.ctl->run_total;
+    // device clock: the step's offsets follow the pending ones, if they fit
+    const int64_t pend0 = L.clock ? (int64_t)L.clock->pending_segs : 0;
+    const bool pend_ok = !L.clock || pend0 + L.n_segs <= L.max_pending;
     if (tid == 0) s_carry = 0ull;
     __syncthreads();
     for (int c0 = 0; c0 < L.n_segs; c0 += 1024) {
@@ -159,8 +185,12 @@ __global__ void __launch_bounds__(1024) seg_scan_kernel(const __grid_constant__ 
         if (seg < L.n_segs) {
             L.seg_rel[seg] = (int64_t)rel;
             L.seg_abs[seg] = (int64_t)(base + rel);
-            const StreamDesc* sdp = stream_of_seg(L, seg);
-            L.seg_off_out[sdp->out_seg_index + (seg - sdp->seg_base)] = (int64_t)(base + rel);
+            if (L.clock) {
+                if (pend_ok) L.seg_off_out[pend0 + seg] = (int64_t)(base + rel);
+            } else {
+                const StreamDesc* sdp = stream_of_seg(L, seg);
+                L.seg_off_out[sdp->out_seg_index + (seg - sdp->seg_base)] = (int64_t)(base + rel);
+            }
         }
         __syncthreads();
         if (tid == 1023) s_carry = rel + v;
@@ -172,6 +202,7 @@ __global__ void __launch_bounds__(1024) seg_scan_kernel(const __grid_constant__ 
         c->run_total = total;
         if (total > c->out_demand_max) c->out_demand_max = total;
         if (total > L.out_cap) c->err |= kErrOutOverflow;
+        if (!pend_ok) c->err |= kErrPendingOverflow;
         if (c->page_ctr > c->page_demand_max) c->page_demand_max = c->page_ctr;
         c->page_ctr = 0u;                      // pages are free again for the next step
     }
@@ -330,6 +361,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_kernel(const __grid_constan
     const int npass = (tb + kMaxDigitBits - 1) / kMaxDigitBits;
     const int bits = (tb + npass - 1) / npass;
     const int NB = 1 << bits;
+    if (step_stopped(L)) return;
 
     for (int seg = blockIdx.x; seg < L.n_segs; seg += gridDim.x) {
         const uint32_t N = L.seg_count[seg];
@@ -379,7 +411,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_kernel(const __grid_constan
         __syncthreads();
 
         const int tshift = sdp->pix_bits + 1;
-        const uint32_t ta = (uint32_t)interval_start(*sdp, j, L.dt);
+        const uint32_t ta = (uint32_t)interval_start(step_ta0(L, *sdp), *sdp, j, L.dt);
         const RecordSink rsink{L.out + abs0, ta, sdp->W, tshift, (1u << sdp->pix_bits) - 1u};
         const bool fit = (npass <= 2) ? (N <= cap) : (2u * N <= cap);
         KeyT* X = fit ? sbuf : reinterpret_cast<KeyT*>(L.temp) + L.seg_rel[seg];
@@ -453,14 +485,34 @@ __global__ void write_total_kernel(const Ctl* ctl, int64_t* dst)
     *dst = (int64_t)ctl->run_total;
 }
 
+// Device clock: commits a step that raised no error (state parity, time,
+// pending offsets, committed records), or discards it and stops later steps.
+// `add_tau` advances the clock by the step's span; an init launch (add_tau
+// < 0) sets it to tau_init.
+__global__ void advance_kernel(DevClock* clk, Ctl* ctl, int n_segs, long long add_tau, long long tau_init)
+{
+    if (clk->sticky != 0u) return;
+    unsigned int err = ctl->err;
+    const long long tau = add_tau < 0 ? tau_init : clk->tau + add_tau;
+    if (tau > 0xFFFFFFFEll) err |= kErrTime;
+    if (err != 0u) {
+        clk->sticky = err;
+        ctl->run_total = clk->committed_total;   // the step's records are dropped
+        return;
+    }
+    clk->parity ^= 1u;
+    clk->tau = tau;
+    clk->pending_segs += n_segs;
+    clk->committed_total = ctl->run_total;
+    clk->steps += 1ull;
+}
+
 template <int PPT, int PF>
 cudaError_t launch_emit_t(const StepLaunch& L, size_t smem)
 {
     constexpr int WARPS = 64 / PPT;
-    const void* fn = L.key64 ? (const void*)emit_kernel<PPT, WARPS, PF, uint64_t>
-                             : (const void*)emit_kernel<PPT, WARPS, PF, uint32_t>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    // (the dynamic shared-memory attribute was set by emit_occupancy at create
+    // time, so that launches stay capturable)
     if (L.key64)
         emit_kernel<PPT, WARPS, PF, uint64_t><<<L.grid_emit, WARPS * 32, smem, L.stream>>>(L);
     else
@@ -540,6 +592,12 @@ cudaError_t launch_step(const StepLaunch& L, uint64_t* launches)
         else
             sort_kernel<uint32_t><<<L.grid_sort, kSortThreads, L.sort_smem, L.stream>>>(L);
         *launches += 3;
+    }
+    if (L.clock) {
+        const bool init = L.n_segs == 0;   // an init launch consumes one frame: no intervals
+        advance_kernel<<<1, 1, 0, L.stream>>>(L.clock, L.ctl, L.n_segs,
+                                              init ? -1ll : (long long)L.T * L.dt, (long long)L.tau_init);
+        *launches += 1;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (L.ev_sorted && (e = cudaEventRecord(L.ev_sorted, L.stream)) != cudaSuccess) return e;

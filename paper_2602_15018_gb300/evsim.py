@@ -12,7 +12,30 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import Params, Stats, check, lib
+from ._lib import BatchParams, Params, Stats, check, lib
+
+
+def _params(width: int, height: int, c_pos: float = 0.2, c_neg: float = 0.2,
+            sigma_c: float = 0.0, c_min: float = 0.01, refractory_us: int = 0,
+            log_eps: float = 1e-3, input_is_log: bool = False, seed: int = 0,
+            c_pos_map=None, c_neg_map=None, keep=None) -> Params:
+    """neurosim_evsim_params of one sensor (host maps are kept alive in `keep`)."""
+    p = Params()
+    lib().neurosim_evsim_default_params(C.byref(p))
+    p.width, p.height = int(width), int(height)
+    p.c_pos, p.c_neg, p.sigma_c, p.c_min = c_pos, c_neg, sigma_c, c_min
+    p.refractory_us = int(refractory_us)
+    p.log_eps = log_eps
+    p.input_is_log = int(bool(input_is_log))
+    p.seed = int(seed)
+    if c_pos_map is not None:
+        cp = np.ascontiguousarray(c_pos_map, np.float32).reshape(-1)
+        cn = np.ascontiguousarray(c_neg_map, np.float32).reshape(-1)
+        if keep is not None:
+            keep += [cp, cn]
+        p.c_pos_map = cp.ctypes.data_as(C.POINTER(C.c_float))
+        p.c_neg_map = cn.ctypes.data_as(C.POINTER(C.c_float))
+    return p
 
 
 class EventSim:
@@ -187,3 +210,173 @@ def device_log(x: torch.Tensor) -> torch.Tensor:
     check(lib().neurosim_debug_log(C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.numel(),
                                    C.c_void_p(torch.cuda.current_stream().cuda_stream)))
     return y
+
+
+def _ptr_array(tensors):
+    arr = (C.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError("frames must be contiguous float32 CUDA tensors")
+        arr[i] = t.data_ptr()
+    return arr
+
+
+class EventSimBatch:
+    """Many independent sensors stepped together (C ABI "Batched sensors").
+
+    sensors: list of dicts with EventSim's sensor keywords (width, height,
+    c_pos, c_neg, sigma_c, c_min, refractory_us, log_eps, input_is_log,
+    seed, c_pos_map, c_neg_map).  init(first) takes one [H, W] frame per
+    sensor at t0_us; set_frames(bufs) registers one [T, H, W] buffer per
+    sensor that every step() reads (step() may be captured in a CUDA graph
+    on `stream`); drain() returns the committed records and the offsets of
+    the (step, sensor, interval) segments.
+    """
+
+    def __init__(self, sensors, frames_per_step: int, dt_us: int = 1000, t0_us: int = 0,
+                 event_capacity: int = 0, max_pending_steps: int = 0,
+                 pixels_per_thread: int = 0, prefetch_frames: int = 0,
+                 stream: torch.cuda.Stream | None = None):
+        L = lib()
+        keep = []
+        arr = (Params * len(sensors))()
+        for i, kw in enumerate(sensors):
+            arr[i] = _params(keep=keep, **kw)
+        self.dims = [(int(kw["height"]), int(kw["width"])) for kw in sensors]
+        bp = BatchParams()
+        L.neurosim_evsim_batch_default_params(C.byref(bp))
+        bp.n_streams = len(sensors)
+        bp.frames_per_step = int(frames_per_step)
+        bp.dt_us = int(dt_us)
+        bp.t0_us = int(t0_us)
+        bp.event_capacity = int(event_capacity)
+        bp.max_pending_steps = int(max_pending_steps)
+        bp.pixels_per_thread = int(pixels_per_thread)
+        bp.prefetch_frames = int(prefetch_frames)
+        self.T = int(frames_per_step)
+        self.n = len(sensors)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        check(L.neurosim_evsim_batch_create(arr, C.byref(bp), C.c_void_p(self.stream.cuda_stream),
+                                            C.byref(h)))
+        self._h = h
+        self._bufs = None
+
+    def init(self, first_frames) -> None:
+        self._first = list(first_frames)
+        check(lib().neurosim_evsim_batch_init(self._h, _ptr_array(self._first)))
+
+    def set_frames(self, buffers) -> None:
+        for (H, W), b in zip(self.dims, buffers):
+            if b.numel() != self.T * H * W:
+                raise ValueError("each buffer must hold frames_per_step frames of its sensor")
+        self._bufs = list(buffers)
+        check(lib().neurosim_evsim_batch_set_frames(self._h, _ptr_array(self._bufs)))
+
+    def step(self) -> None:
+        check(lib().neurosim_evsim_batch_step(self._h))
+
+    def pending(self):
+        n_ev, n_seg = C.c_uint64(0), C.c_int64(0)
+        check(lib().neurosim_evsim_batch_pending(self._h, C.byref(n_ev), C.byref(n_seg)))
+        return int(n_ev.value), int(n_seg.value)
+
+    def drain(self, to: str = "cpu", out: torch.Tensor | None = None, strict: bool = True):
+        """(events, seg_offsets): records of the committed steps in order
+        step, sensor, interval; seg_offsets has one entry per segment + 1.
+        With strict=False a dropped-step condition is returned as a third
+        item (the NEUROSIM status) instead of raised, after the records of
+        the committed steps."""
+        n_ev, n_seg = self.pending()
+        seg = np.zeros(n_seg + 1, np.int64)
+        n_out, ns = C.c_uint64(0), C.c_int64(0)
+        segp = seg.ctypes.data_as(C.POINTER(C.c_int64))
+        if to == "cuda":
+            if out is None:
+                out = torch.empty(max(n_ev, 1), dtype=torch.int64, device=self.stream.device)
+            rc = lib().neurosim_evsim_batch_drain(self._h, C.c_void_p(out.data_ptr()), out.numel(), 1,
+                                                  C.byref(n_out), segp, seg.size, C.byref(ns))
+            ev = out[: n_out.value]
+        else:
+            buf = np.empty(max(n_ev, 1), np.uint64)
+            rc = lib().neurosim_evsim_batch_drain(self._h, C.c_void_p(buf.ctypes.data), buf.size, 0,
+                                                  C.byref(n_out), segp, seg.size, C.byref(ns))
+            ev = buf[: n_out.value]
+        if strict:
+            check(rc)
+            return ev, seg
+        return ev, seg, rc
+
+    def split(self, events, seg):
+        """Per sensor: list over sensors of (events, offsets) of its intervals,
+        steps concatenated (offsets relative to the sensor's own events)."""
+        n_steps = (len(seg) - 1) // (self.n * self.T) if self.n * self.T else 0
+        res = []
+        for i in range(self.n):
+            parts, offs, base = [], [0], 0
+            for k in range(n_steps):
+                s0 = (k * self.n + i) * self.T
+                a, b = seg[s0], seg[s0 + self.T]
+                parts.append(events[a:b])
+                offs.extend(list(seg[s0 + 1: s0 + self.T + 1] - a + base))
+                base += b - a
+            ev = np.concatenate(parts) if parts else np.empty(0, np.uint64)
+            res.append((ev, np.asarray(offs, np.int64)))
+        return res
+
+    def get_state(self, i: int):
+        H, W = self.dims[i]
+        n = H * W
+        ref = np.empty(n, np.float32)
+        lp = np.empty(n, np.float32)
+        tl = np.empty(n, np.uint32)
+        tau = C.c_int64(0)
+        check(lib().neurosim_evsim_batch_get_state(
+            self._h, int(i), ref.ctypes.data_as(C.POINTER(C.c_float)),
+            lp.ctypes.data_as(C.POINTER(C.c_float)), tl.ctypes.data_as(C.POINTER(C.c_uint32)),
+            C.byref(tau)))
+        return dict(ref=ref, lprev=lp, tlast=tl, tau=int(tau.value))
+
+    def thresholds(self, i: int):
+        H, W = self.dims[i]
+        cp = np.empty(H * W, np.float32)
+        cn = np.empty(H * W, np.float32)
+        check(lib().neurosim_evsim_batch_get_thresholds(
+            self._h, int(i), cp.ctypes.data_as(C.POINTER(C.c_float)),
+            cn.ctypes.data_as(C.POINTER(C.c_float))))
+        return cp.reshape(H, W), cn.reshape(H, W)
+
+    def counters(self):
+        la, st = C.c_uint64(0), C.c_uint64(0)
+        check(lib().neurosim_evsim_batch_counters(self._h, C.byref(la), C.byref(st)))
+        return int(la.value), int(st.value)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().neurosim_evsim_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(frames: torch.Tensor, dt_us: int = 1000, repeats: int = 5, cache_path: str | None = None,
+             **sensor):
+    """Times every emission launch shape on `frames` [T, H, W] (FP32, CUDA) for
+    one sensor (EventSim's keywords) and returns (pixels_per_thread,
+    prefetch_frames, median_ms); `cache_path` is a JSON-lines cache keyed by
+    GPU model, width, height and T."""
+    H, W = frames.shape[-2], frames.shape[-1]
+    if not (frames.is_cuda and frames.dtype == torch.float32 and frames.is_contiguous()):
+        raise ValueError("frames must be a contiguous float32 CUDA tensor [T, H, W]")
+    keep = []
+    p = _params(W, H, keep=keep, **sensor)
+    ppt, pf, ms = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
+    T = frames.numel() // (H * W)
+    check(lib().neurosim_evsim_autotune(C.byref(p), C.c_void_p(frames.data_ptr()), T, int(dt_us),
+                                        int(repeats), cache_path.encode() if cache_path else None,
+                                        C.byref(ppt), C.byref(pf), C.byref(ms)))
+    return int(ppt.value), int(pf.value), float(ms.value)

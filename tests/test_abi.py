@@ -56,9 +56,10 @@ def test_abi_version_and_defaults(built):
 
 
 def test_struct_layout_matches_header(built):
-    """Offsets of every field of the two public structs, C compiler vs ctypes."""
+    """Offsets of every field of the public structs, C compiler vs ctypes."""
     from paper_2602_15018_gb300 import _lib
-    structs = {"neurosim_evsim_params": _lib.Params, "neurosim_evsim_stats": _lib.Stats}
+    structs = {"neurosim_evsim_params": _lib.Params, "neurosim_evsim_stats": _lib.Stats,
+               "neurosim_evsim_batch_params": _lib.BatchParams}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "neurosim_evsim.h"',
              "int main(void) {"]
     for cname, py in structs.items():
@@ -96,3 +97,31 @@ def test_no_gpu_fails_loudly(built):
     h = C.c_void_p()
     rc = L.neurosim_evsim_create(C.byref(p), None, C.byref(h))
     assert rc != 0 and not h.value
+
+
+def test_batch_defaults_and_no_gpu(built):
+    """Batch defaults; without a CUDA device batch creation and the autotuner
+    report an error instead of computing."""
+    import torch
+    from paper_2602_15018_gb300 import _lib
+    L = _lib.lib()
+    bp = _lib.BatchParams()
+    L.neurosim_evsim_batch_default_params(C.byref(bp))
+    assert bp.n_streams == 1 and bp.frames_per_step == 16 and bp.dt_us == 1000
+    assert bp.t0_us == 0 and bp.event_capacity == 0 and list(bp.reserved) == [0] * 6
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    p = _lib.Params()
+    L.neurosim_evsim_default_params(C.byref(p))
+    p.width, p.height = 8, 8
+    h = C.c_void_p()
+    assert L.neurosim_evsim_batch_create(C.byref(p), C.byref(bp), None, C.byref(h)) != 0
+    assert not h.value
+    # argument checks come first and need no device
+    bp.n_streams = 0
+    assert L.neurosim_evsim_batch_create(C.byref(p), C.byref(bp), None, C.byref(h)) == 1
+    assert b"n_streams" in L.neurosim_last_error()
+    ppt, pf = C.c_int32(0), C.c_int32(0)
+    rc = L.neurosim_evsim_autotune(C.byref(p), C.c_void_p(16), 1, 1000, 3, None, C.byref(ppt),
+                                   C.byref(pf), None)
+    assert rc == 1 and b"n_frames" in L.neurosim_last_error()
