@@ -187,13 +187,14 @@ int neurosim_evsim_get_stats(neurosim_evsim *h, neurosim_evsim_stats *out);
  * stream's events are exactly those of a single-stream simulator fed the
  * same frames.
  *
- * Every step consumes frames_per_step frames per stream from device buffers
- * registered with neurosim_evsim_batch_set_frames.  Everything that changes
- * from step to step (times, state buffer, pending intervals, record count)
- * lives in device memory, so neurosim_evsim_batch_step allocates nothing,
- * never synchronises, and may be captured into a CUDA graph on the batch's
- * stream and replayed; the caller refills the registered frame buffers
- * between replays.  Frame j of step k (k = 0, 1, ...) is at
+ * Every step consumes frames_per_step frames per stream from one of the
+ * frame-buffer sets ("slots") registered with neurosim_evsim_batch_set_frames.
+ * Everything that changes from step to step (times, state buffer, pending
+ * intervals, record count) lives in device memory, so
+ * neurosim_evsim_batch_step allocates nothing, never synchronises, and may
+ * be captured into a CUDA graph on the batch's stream (one graph per slot)
+ * and replayed; the caller refills a slot's buffers between the replays
+ * that read it.  Frame j of step k (k = 0, 1, ...) is at
  * t0_us + (1 + k * frames_per_step + j) * dt_us; frame t0_us is the one
  * given to neurosim_evsim_batch_init.
  * ---------------------------------------------------------------------- */
@@ -209,7 +210,10 @@ typedef struct {
                                     sum(W*H) * T * max_pending_steps / 16)        */
     int32_t pixels_per_thread;   /* emission tile: 0 (16), 8 or 16                */
     int32_t prefetch_frames;     /* frames in flight per lane: 0 (2), 2 or 3      */
-    int32_t reserved[6];         /* must be zero                                  */
+    int32_t frame_slots;         /* frame-buffer sets that can be registered
+                                    (0 = 2, at most 16): a renderer fills one
+                                    while the steps read another               */
+    int32_t reserved[5];         /* must be zero                                  */
 } neurosim_evsim_batch_params;
 
 /* Fills *p with defaults (n_streams 1, T 16, dt 1000 us). */
@@ -225,12 +229,14 @@ int neurosim_evsim_batch_create(const neurosim_evsim_params *streams,
                                 const neurosim_evsim_batch_params *bp, void *cuda_stream,
                                 neurosim_evsim_batch **out);
 
-/* Registers the frame buffers the steps read: frames_dev is a HOST array of
- * n_streams DEVICE pointers, stream i's buffer holding frames_per_step FP32
- * frames [T][H_i][W_i].  The buffers stay owned by the caller and must stay
- * valid while steps that read them may run.  Synchronises the batch's
- * stream; not capturable.  NEUROSIM_E_INVALID for a NULL pointer. */
-int neurosim_evsim_batch_set_frames(neurosim_evsim_batch *b, const float *const *frames_dev);
+/* Registers the frame buffers of slot `slot` (0 <= slot < frame_slots):
+ * frames_dev is a HOST array of n_streams DEVICE pointers, stream i's buffer
+ * holding frames_per_step FP32 frames [T][H_i][W_i].  The buffers stay owned
+ * by the caller and must stay valid while steps that read them may run.
+ * Synchronises the batch's stream; not capturable.  NEUROSIM_E_INVALID for
+ * a NULL pointer or a bad slot. */
+int neurosim_evsim_batch_set_frames(neurosim_evsim_batch *b, int32_t slot,
+                                    const float *const *frames_dev);
 
 /* Initialises every stream from one frame at t0_us (HOST array of n_streams
  * DEVICE pointers to one [H_i][W_i] FP32 frame each): ref = L_prev = L, no
@@ -238,13 +244,13 @@ int neurosim_evsim_batch_set_frames(neurosim_evsim_batch *b, const float *const 
  * was initialised already. */
 int neurosim_evsim_batch_init(neurosim_evsim_batch *b, const float *const *first_frames_dev);
 
-/* Enqueues one step over the registered buffers (emission, interval count,
- * scan, sort and the device clock's advance: 5 kernels).  Capturable.  If a
- * step overflows a capacity, it and every later step are dropped on the
- * device (state, clock and pending intervals stay as after the last good
- * step) and the next drain reports it.  NEUROSIM_E_STATE before init or
- * set_frames. */
-int neurosim_evsim_batch_step(neurosim_evsim_batch *b);
+/* Enqueues one step over the buffers registered in `slot` (emission,
+ * interval count, scan, sort and the device clock's advance: 5 kernels).
+ * Capturable.  If a step overflows a capacity, it and every later step are
+ * dropped on the device (state, clock and pending intervals stay as after
+ * the last good step) and the next drain reports it.  NEUROSIM_E_STATE
+ * before init or before the slot was registered. */
+int neurosim_evsim_batch_step(neurosim_evsim_batch *b, int32_t slot);
 
 /* Synchronises; *n_events = records of the committed steps since the last
  * drain, *n_segments = their intervals (steps * n_streams * T). */

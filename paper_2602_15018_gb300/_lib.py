@@ -59,7 +59,7 @@ class BatchParams(C.Structure):
         ("n_streams", C.c_int32), ("frames_per_step", C.c_int32), ("dt_us", C.c_int32),
         ("max_pending_steps", C.c_int32), ("t0_us", C.c_int64), ("event_capacity", C.c_uint64),
         ("pixels_per_thread", C.c_int32), ("prefetch_frames", C.c_int32),
-        ("reserved", C.c_int32 * 6),
+        ("frame_slots", C.c_int32), ("reserved", C.c_int32 * 5),
     ]
 
 
@@ -128,11 +128,11 @@ def lib():
             L.neurosim_evsim_batch_create.argtypes = [C.POINTER(Params), C.POINTER(BatchParams), vp,
                                                       C.POINTER(vp)]
             L.neurosim_evsim_batch_set_frames.restype = C.c_int
-            L.neurosim_evsim_batch_set_frames.argtypes = [vp, C.POINTER(vp)]
+            L.neurosim_evsim_batch_set_frames.argtypes = [vp, i32, C.POINTER(vp)]
             L.neurosim_evsim_batch_init.restype = C.c_int
             L.neurosim_evsim_batch_init.argtypes = [vp, C.POINTER(vp)]
             L.neurosim_evsim_batch_step.restype = C.c_int
-            L.neurosim_evsim_batch_step.argtypes = [vp]
+            L.neurosim_evsim_batch_step.argtypes = [vp, i32]
             L.neurosim_evsim_batch_pending.restype = C.c_int
             L.neurosim_evsim_batch_pending.argtypes = [vp, C.POINTER(u64), C.POINTER(i64)]
             L.neurosim_evsim_batch_drain.restype = C.c_int

@@ -71,7 +71,6 @@ struct BatchStream {
     float* cneg = nullptr;
     float cpos_u = 0.2f, cneg_u = 0.2f;
     neurosim_evsim_params p{};
-    const float* frames = nullptr;
 };
 
 }  // namespace
@@ -88,7 +87,8 @@ struct neurosim_evsim_batch {
     int64_t max_pending = 0;      // pending interval capacity
     std::vector<BatchStream> s;
 
-    StreamDesc* d_step = nullptr;   // [2][n] step descriptors (by state parity)
+    int slots = 2;
+    StreamDesc* d_step = nullptr;   // [slots][2][n] step descriptors (by slot and state parity)
     StreamDesc* d_init = nullptr;   // [2][n] init descriptors
     void* keys = nullptr;
     void* temp = nullptr;
@@ -104,7 +104,7 @@ struct neurosim_evsim_batch {
     Ctl* ctl = nullptr;
     DevClock* clock = nullptr;
 
-    bool frames_set = false;
+    std::vector<bool> slot_set;
     bool initialised = false;
     uint64_t launches = 0;
 };
@@ -184,11 +184,11 @@ int upload_descs(neurosim_evsim_batch* b, StreamDesc* dst, bool init, const floa
     return NEUROSIM_OK;
 }
 
-StepLaunch make_launch(const neurosim_evsim_batch* b, bool init)
+StepLaunch make_launch(const neurosim_evsim_batch* b, bool init, int slot)
 {
     StepLaunch L;
     memset(&L, 0, sizeof L);
-    L.streams_dev = init ? b->d_init : b->d_step;
+    L.streams_dev = init ? b->d_init : b->d_step + (size_t)slot * 2 * b->n;
     L.n_streams = b->n;
     L.n_items = b->n_items;
     L.n_segs = init ? 0 : (int32_t)b->n_segs;
@@ -274,7 +274,8 @@ int neurosim_evsim_batch_create(const neurosim_evsim_params* streams, const neur
         return fail(NEUROSIM_E_INVALID, "pixels_per_thread must be 0, 8 or 16");
     if (bp->prefetch_frames != 0 && bp->prefetch_frames != 2 && bp->prefetch_frames != 3)
         return fail(NEUROSIM_E_INVALID, "prefetch_frames must be 0, 2 or 3");
-    for (int i = 0; i < 6; ++i)
+    if (bp->frame_slots < 0 || bp->frame_slots > 16) return fail(NEUROSIM_E_INVALID, "frame_slots must be in [0, 16]");
+    for (int i = 0; i < 5; ++i)
         if (bp->reserved[i] != 0) return fail(NEUROSIM_E_INVALID, "reserved fields must be zero");
     for (int i = 0; i < bp->n_streams; ++i) {
         const int rc = validate_stream_params(&streams[i]);
@@ -290,6 +291,8 @@ int neurosim_evsim_batch_create(const neurosim_evsim_params* streams, const neur
     b->dt = bp->dt_us;
     b->ppt = bp->pixels_per_thread ? bp->pixels_per_thread : 16;
     b->pf = bp->prefetch_frames ? bp->prefetch_frames : 2;
+    b->slots = bp->frame_slots ? bp->frame_slots : 2;
+    b->slot_set.assign(b->slots, false);
     const int pend_steps = bp->max_pending_steps ? bp->max_pending_steps : 4;
     auto bail = [&](int code) {
         release(b);
@@ -373,7 +376,7 @@ int neurosim_evsim_batch_create(const neurosim_evsim_params* streams, const neur
     b->n_pages = (uint32_t)(key_count / kBatchPageKeys);
     int64_t chunk_entries = 0;
     for (const auto& st : b->s) chunk_entries += (int64_t)b->T * st.n_tiles;
-    if (dalloc(&b->d_step, (size_t)2 * b->n) || dalloc(&b->d_init, (size_t)2 * b->n) ||
+    if (dalloc(&b->d_step, (size_t)b->slots * 2 * b->n) || dalloc(&b->d_init, (size_t)2 * b->n) ||
         cudaMalloc(&b->keys, b->key_bytes) != cudaSuccess || cudaMalloc(&b->temp, b->key_bytes) != cudaSuccess ||
         dalloc(&b->chunks, (size_t)chunk_entries) || dalloc(&b->seg_count, (size_t)b->n_segs) ||
         dalloc(&b->seg_rel, (size_t)b->n_segs) || dalloc(&b->seg_abs, (size_t)b->n_segs) ||
@@ -388,17 +391,17 @@ int neurosim_evsim_batch_create(const neurosim_evsim_params* streams, const neur
     return NEUROSIM_OK;
 }
 
-int neurosim_evsim_batch_set_frames(neurosim_evsim_batch* b, const float* const* frames_dev)
+int neurosim_evsim_batch_set_frames(neurosim_evsim_batch* b, int32_t slot, const float* const* frames_dev)
 {
     if (!b || !frames_dev) return fail(NEUROSIM_E_INVALID, "batch and frames_dev must not be NULL");
+    if (slot < 0 || slot >= b->slots) return fail(NEUROSIM_E_INVALID, "slot %d not in [0, %d)", slot, b->slots);
     for (int i = 0; i < b->n; ++i)
         if (!frames_dev[i]) return fail(NEUROSIM_E_INVALID, "frames_dev[%d] is NULL", i);
     BatchGuard g(b->device);
     if (!g.ok) return fail(NEUROSIM_E_CUDA, "cannot select the batch's device");
-    const int rc = upload_descs(b, b->d_step, false, frames_dev);
+    const int rc = upload_descs(b, b->d_step + (size_t)slot * 2 * b->n, false, frames_dev);
     if (rc) return rc;
-    for (int i = 0; i < b->n; ++i) b->s[i].frames = frames_dev[i];
-    b->frames_set = true;
+    b->slot_set[slot] = true;
     return NEUROSIM_OK;
 }
 
@@ -412,20 +415,21 @@ int neurosim_evsim_batch_init(neurosim_evsim_batch* b, const float* const* first
     if (!g.ok) return fail(NEUROSIM_E_CUDA, "cannot select the batch's device");
     int rc = upload_descs(b, b->d_init, true, first_frames_dev);
     if (rc) return rc;
-    const StepLaunch L = make_launch(b, true);
+    const StepLaunch L = make_launch(b, true, 0);
     BCUDA(launch_step(L, &b->launches));
     b->initialised = true;
     return NEUROSIM_OK;
 }
 
-int neurosim_evsim_batch_step(neurosim_evsim_batch* b)
+int neurosim_evsim_batch_step(neurosim_evsim_batch* b, int32_t slot)
 {
     if (!b) return fail(NEUROSIM_E_INVALID, "batch is NULL");
-    if (!b->initialised || !b->frames_set)
-        return fail(NEUROSIM_E_STATE, "call neurosim_evsim_batch_init and _set_frames before stepping");
+    if (slot < 0 || slot >= b->slots) return fail(NEUROSIM_E_INVALID, "slot %d not in [0, %d)", slot, b->slots);
+    if (!b->initialised || !b->slot_set[slot])
+        return fail(NEUROSIM_E_STATE, "call neurosim_evsim_batch_init and register slot %d before stepping", slot);
     BatchGuard g(b->device);
     if (!g.ok) return fail(NEUROSIM_E_CUDA, "cannot select the batch's device");
-    const StepLaunch L = make_launch(b, false);
+    const StepLaunch L = make_launch(b, false, slot);
     BCUDA(launch_step(L, &b->launches));
     return NEUROSIM_OK;
 }

@@ -227,15 +227,16 @@ class EventSimBatch:
     sensors: list of dicts with EventSim's sensor keywords (width, height,
     c_pos, c_neg, sigma_c, c_min, refractory_us, log_eps, input_is_log,
     seed, c_pos_map, c_neg_map).  init(first) takes one [H, W] frame per
-    sensor at t0_us; set_frames(bufs) registers one [T, H, W] buffer per
-    sensor that every step() reads (step() may be captured in a CUDA graph
-    on `stream`); drain() returns the committed records and the offsets of
-    the (step, sensor, interval) segments.
+    sensor at t0_us; set_frames(bufs, slot) registers one [T, H, W] buffer
+    per sensor in a frame slot that step(slot) reads (step() may be captured
+    in a CUDA graph on `stream`, one graph per slot); drain() returns the
+    committed records and the offsets of the (step, sensor, interval)
+    segments.
     """
 
     def __init__(self, sensors, frames_per_step: int, dt_us: int = 1000, t0_us: int = 0,
                  event_capacity: int = 0, max_pending_steps: int = 0,
-                 pixels_per_thread: int = 0, prefetch_frames: int = 0,
+                 pixels_per_thread: int = 0, prefetch_frames: int = 0, frame_slots: int = 0,
                  stream: torch.cuda.Stream | None = None):
         L = lib()
         keep = []
@@ -253,6 +254,7 @@ class EventSimBatch:
         bp.max_pending_steps = int(max_pending_steps)
         bp.pixels_per_thread = int(pixels_per_thread)
         bp.prefetch_frames = int(prefetch_frames)
+        bp.frame_slots = int(frame_slots)
         self.T = int(frames_per_step)
         self.n = len(sensors)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -260,21 +262,21 @@ class EventSimBatch:
         check(L.neurosim_evsim_batch_create(arr, C.byref(bp), C.c_void_p(self.stream.cuda_stream),
                                             C.byref(h)))
         self._h = h
-        self._bufs = None
+        self._bufs = {}
 
     def init(self, first_frames) -> None:
         self._first = list(first_frames)
         check(lib().neurosim_evsim_batch_init(self._h, _ptr_array(self._first)))
 
-    def set_frames(self, buffers) -> None:
+    def set_frames(self, buffers, slot: int = 0) -> None:
         for (H, W), b in zip(self.dims, buffers):
             if b.numel() != self.T * H * W:
                 raise ValueError("each buffer must hold frames_per_step frames of its sensor")
-        self._bufs = list(buffers)
-        check(lib().neurosim_evsim_batch_set_frames(self._h, _ptr_array(self._bufs)))
+        self._bufs[slot] = list(buffers)
+        check(lib().neurosim_evsim_batch_set_frames(self._h, int(slot), _ptr_array(self._bufs[slot])))
 
-    def step(self) -> None:
-        check(lib().neurosim_evsim_batch_step(self._h))
+    def step(self, slot: int = 0) -> None:
+        check(lib().neurosim_evsim_batch_step(self._h, int(slot)))
 
     def pending(self):
         n_ev, n_seg = C.c_uint64(0), C.c_int64(0)

@@ -108,7 +108,8 @@ def test_batch_defaults_and_no_gpu(built):
     bp = _lib.BatchParams()
     L.neurosim_evsim_batch_default_params(C.byref(bp))
     assert bp.n_streams == 1 and bp.frames_per_step == 16 and bp.dt_us == 1000
-    assert bp.t0_us == 0 and bp.event_capacity == 0 and list(bp.reserved) == [0] * 6
+    assert bp.t0_us == 0 and bp.event_capacity == 0 and bp.frame_slots == 0
+    assert list(bp.reserved) == [0] * 5
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
     p = _lib.Params()

@@ -92,13 +92,16 @@ def test_batch_eager_matches_oracle_per_stream():
     batch = EventSimBatch(SENSORS, frames_per_step=T, dt_us=DT, t0_us=t0)
     orcs = _oracles(batch)
     first = _init(batch, orcs, frames, t0)
-    bufs = [torch.empty((T, s["height"], s["width"]), dtype=torch.float32, device="cuda") for s in SENSORS]
-    batch.set_frames(bufs)
+    # two frame slots, used alternately
+    bufs = [[torch.empty((T, s["height"], s["width"]), dtype=torch.float32, device="cuda") for s in SENSORS]
+            for _ in range(2)]
+    batch.set_frames(bufs[0], slot=0)
+    batch.set_frames(bufs[1], slot=1)
     for drain_after in ((0, 2), (2, 3), (3, 4)):     # two steps between the first drain
         for k in range(*drain_after):
             for i in range(len(SENSORS)):
-                bufs[i].copy_(frames[i][1 + k * T: 1 + (k + 1) * T])
-            batch.step()
+                bufs[k % 2][i].copy_(frames[i][1 + k * T: 1 + (k + 1) * T])
+            batch.step(slot=k % 2)
         ev, seg = batch.drain()
         _run_oracles(orcs, frames, drain_after[0], drain_after[1], T, t0)
         per = batch.split(ev, seg)
