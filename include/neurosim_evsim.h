@@ -314,6 +314,14 @@ const char *neurosim_last_error(void);
 /* Library ABI version (NEUROSIM_EVSIM_ABI_VERSION of the build). */
 int32_t neurosim_abi_version(void);
 
+/* Verification of the library's tensor-core GEMM core (used by the learned
+ * interpolator): C[M][N] (FP32, DEVICE, row-major) = sum_k A(m, k) B(n, k)
+ * with BF16 DEVICE operands; mode bit 0: A stored [K][M] (else [M][K]),
+ * bit 1: B stored [K][N] (else [N][K]).  16 <= N <= 256, N % 16 == 0,
+ * K % 8 == 0, M % 8 == 0 when A is stored [K][M].  Synchronises cuda_stream. */
+int neurosim_debug_umma_gemm(int32_t mode, int32_t M, int32_t N, int32_t K, const void *A,
+                             const void *B, float *C, void *cuda_stream);
+
 /* Evaluates the library's FP32 log (the one the event model uses) on n DEVICE
  * floats x_dev into y_dev on cuda_stream; for verification of the log. */
 int neurosim_debug_log(const float *x_dev, float *y_dev, int64_t n, void *cuda_stream);

@@ -29,7 +29,7 @@ EXPORTS = [
     "neurosim_evsim_batch_set_frames", "neurosim_evsim_batch_init", "neurosim_evsim_batch_step",
     "neurosim_evsim_batch_pending", "neurosim_evsim_batch_drain", "neurosim_evsim_batch_get_state",
     "neurosim_evsim_batch_get_thresholds", "neurosim_evsim_batch_counters",
-    "neurosim_evsim_batch_destroy", "neurosim_evsim_autotune",
+    "neurosim_evsim_batch_destroy", "neurosim_evsim_autotune", "neurosim_debug_umma_gemm",
 ]
 
 
@@ -150,6 +150,8 @@ def lib():
             L.neurosim_evsim_autotune.argtypes = [C.POINTER(Params), vp, i32, i32, i32, C.c_char_p,
                                                   C.POINTER(i32), C.POINTER(i32),
                                                   C.POINTER(C.c_double)]
+            L.neurosim_debug_umma_gemm.restype = C.c_int
+            L.neurosim_debug_umma_gemm.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp]
             _lib = L
     return _lib
 

@@ -1,0 +1,74 @@
+// Verification entry point of the tensor-core GEMM core (declared in
+// include/neurosim_evsim.h as neurosim_debug_umma_gemm): plain dense GEMMs
+// with every operand layout, compared against a host GEMM by the tests.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/neurosim_evsim.h"
+#include "evsim_internal.h"
+#include "umma_gemm.cuh"
+
+namespace {
+
+using namespace ugemm;
+
+template <int BN, class AG, class BG>
+int run(const AG& a, const BG& b, int M, int N, int K, float* C, unsigned int* err, cudaStream_t st)
+{
+    GemmArgs<AG, BG, StoreF32> g;
+    g.a = a;
+    g.b = b;
+    g.ep = StoreF32{C, N};
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.k_per_split = ((K + BK - 1) / BK) * BK;
+    g.err = err;
+    g.limit_ns = 2000000000ull;
+    // 64 KB of slack after the tiles: a descriptor that strides further than
+    // the layout intends still reads shared memory the CTA owns
+    if (launch_gemm<BN>(g, 1, st, 64 * 1024) != cudaSuccess) return NEUROSIM_E_CUDA;
+    return NEUROSIM_OK;
+}
+
+template <int BN>
+int dispatch(int mode, int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C,
+             unsigned int* err, cudaStream_t st)
+{
+    const bool amn = mode & 1, bmn = mode & 2;
+    const DenseK ak{A, M, K}, bk{B, N, K};
+    const DenseMN am{A, M, M}, bm{B, N, N};
+    if (!amn && !bmn) return run<BN>(ak, bk, M, N, K, C, err, st);
+    if (amn && !bmn) return run<BN>(am, bk, M, N, K, C, err, st);
+    if (!amn && bmn) return run<BN>(ak, bm, M, N, K, C, err, st);
+    return run<BN>(am, bm, M, N, K, C, err, st);
+}
+
+}  // namespace
+
+extern "C" int neurosim_debug_umma_gemm(int32_t mode, int32_t M, int32_t N, int32_t K, const void* A,
+                                        const void* B, float* C, void* cuda_stream)
+{
+    if (!A || !B || !C) return nsim::report_error(NEUROSIM_E_INVALID, "NULL operand");
+    if (mode < 0 || mode > 3) return nsim::report_error(NEUROSIM_E_INVALID, "mode must be in [0, 3]");
+    if (M < 1 || N < 16 || N > 256 || N % 16 || K < 8 || K % 8 || ((mode & 1) && M % 8) || ((mode & 2) && N % 8))
+        return nsim::report_error(NEUROSIM_E_INVALID,
+                                  "need M >= 1, 16 <= N <= 256 with N % 16 == 0, K % 8 == 0, MN-major rows % 8 == 0");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    unsigned int* err = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&err), sizeof(unsigned int), st) != cudaSuccess ||
+        cudaMemsetAsync(err, 0, sizeof(unsigned int), st) != cudaSuccess)
+        return nsim::report_error(NEUROSIM_E_CUDA, "cannot allocate the error word");
+    const auto* a = static_cast<const __nv_bfloat16*>(A);
+    const auto* b = static_cast<const __nv_bfloat16*>(B);
+    int rc = N <= 64 ? dispatch<64>(mode, M, N, K, a, b, C, err, st) : dispatch<256>(mode, M, N, K, a, b, C, err, st);
+    unsigned int h = 0;
+    if (cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        rc = rc ? rc : NEUROSIM_E_CUDA;
+    cudaFreeAsync(err, st);
+    if (rc) return nsim::report_error(rc, "GEMM launch failed");
+    if (h) return nsim::report_error(NEUROSIM_E_TIMEOUT, "a bounded MMA wait timed out");
+    return NEUROSIM_OK;
+}
