@@ -308,6 +308,64 @@ int neurosim_evsim_autotune(const neurosim_evsim_params *p, const float *frames_
                             const char *cache_path, int32_t *pixels_per_thread,
                             int32_t *prefetch_frames, double *ms_out);
 
+/* ------------------------------------------------------------------------
+ * Learned interpolator.  The paper has no counterpart (it renders every frame,
+ * Sec. 2); this is the project's way to run the renderer at a quarter of the
+ * event camera's rate: a 3-level convolutional U-Net predicts the three log
+ * frames between two log keyframes L0 (time tau) and L4 (tau + 4 dt):
+ *   L_j = L0 + (j / 4)(L4 - L0) + r_j(L0, L4),  j = 1, 2, 3,
+ * with BF16 weights and activations, FP32 accumulation on the tensor cores,
+ * and r = 0 for the untrained network (linear interpolation).  Layers:
+ * conv3x3 8->32, conv3x3/2 32->64, conv3x3/2 64->128, conv3x3 128->128,
+ * convT2x2/2 128->64 | skip, conv3x3 128->64, convT2x2/2 64->32 | skip,
+ * conv3x3 64->32, conv1x1 32->3; ReLU after every 3x3 convolution.
+ *
+ * Parameters (FP32, neurosim_interp_param_count() values): weights, then
+ * biases, layer by layer; 3x3 layers as [3][3][Cin][Cout], transposed layers
+ * as [Cin][2][2][Cout], the 1x1 layer as [32][16] (outputs 3..15 unused and
+ * zero), biases [Cout] (the last one 16 with 3..15 zero).
+ * ---------------------------------------------------------------------- */
+typedef struct neurosim_interp neurosim_interp;
+
+/* Number of FP32 parameters in the flat layout above. */
+int64_t neurosim_interp_param_count(void);
+
+/* Creates a network for up to max_batch images of max_height x max_width
+ * (both divisible by 4), with seeded He-normal weights; device work runs on
+ * cuda_stream. */
+int neurosim_interp_create(int32_t max_batch, int32_t max_height, int32_t max_width, uint64_t seed,
+                           void *cuda_stream, neurosim_interp **out);
+
+/* Predicts frames 1..3 between DEVICE log keyframes L0_dev and L4_dev
+ * ([batch][height][width] FP32) into out_dev ([3][batch][height][width]
+ * FP32).  Asynchronous on the network's stream. */
+int neurosim_interp_forward(neurosim_interp *h, const float *L0_dev, const float *L4_dev, int32_t batch,
+                            int32_t height, int32_t width, float *out_dev);
+
+/* One AdamW step (beta 0.9 / 0.999, eps 1e-8, decoupled weight decay on the
+ * weights) on DEVICE training clips [batch][5][height][width] of log frames
+ * at 1000 FPS: frames 0 and 4 are the keyframes, 1..3 the targets; loss =
+ * mean Charbonnier (eps 1e-3) over the three frames.  *loss_out (HOST,
+ * nullable; synchronises when given) receives the loss before the step. */
+int neurosim_interp_train_step(neurosim_interp *h, const float *clips_dev, int32_t batch, int32_t height,
+                               int32_t width, float lr, float weight_decay, float *loss_out);
+
+/* Loss and parameter gradients (HOST array of param_count floats, nullable)
+ * for clips as in train_step, without updating.  Synchronises. */
+int neurosim_interp_gradients(neurosim_interp *h, const float *clips_dev, int32_t batch, int32_t height,
+                              int32_t width, float *grads_host, float *loss_out);
+
+/* Copies the FP32 parameters to / from HOST memory (n = param_count);
+ * set_params also resets the optimiser state.  Synchronise. */
+int neurosim_interp_get_params(neurosim_interp *h, float *host, int64_t n);
+int neurosim_interp_set_params(neurosim_interp *h, const float *host, int64_t n);
+
+/* Kernels launched by the network so far. */
+int neurosim_interp_launches(neurosim_interp *h, uint64_t *launches);
+
+/* Frees the network (synchronises its stream first). */
+void neurosim_interp_destroy(neurosim_interp *h);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *neurosim_last_error(void);
 

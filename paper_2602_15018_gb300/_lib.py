@@ -30,6 +30,9 @@ EXPORTS = [
     "neurosim_evsim_batch_pending", "neurosim_evsim_batch_drain", "neurosim_evsim_batch_get_state",
     "neurosim_evsim_batch_get_thresholds", "neurosim_evsim_batch_counters",
     "neurosim_evsim_batch_destroy", "neurosim_evsim_autotune", "neurosim_debug_umma_gemm",
+    "neurosim_interp_param_count", "neurosim_interp_create", "neurosim_interp_forward",
+    "neurosim_interp_train_step", "neurosim_interp_gradients", "neurosim_interp_get_params",
+    "neurosim_interp_set_params", "neurosim_interp_launches", "neurosim_interp_destroy",
 ]
 
 
@@ -152,6 +155,25 @@ def lib():
                                                   C.POINTER(C.c_double)]
             L.neurosim_debug_umma_gemm.restype = C.c_int
             L.neurosim_debug_umma_gemm.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp]
+            L.neurosim_interp_param_count.restype = C.c_int64
+            L.neurosim_interp_param_count.argtypes = []
+            L.neurosim_interp_create.restype = C.c_int
+            L.neurosim_interp_create.argtypes = [i32, i32, i32, u64, vp, C.POINTER(vp)]
+            L.neurosim_interp_forward.restype = C.c_int
+            L.neurosim_interp_forward.argtypes = [vp, vp, vp, i32, i32, i32, vp]
+            L.neurosim_interp_train_step.restype = C.c_int
+            L.neurosim_interp_train_step.argtypes = [vp, vp, i32, i32, i32, C.c_float, C.c_float,
+                                                     C.POINTER(C.c_float)]
+            L.neurosim_interp_gradients.restype = C.c_int
+            L.neurosim_interp_gradients.argtypes = [vp, vp, i32, i32, i32, vp, C.POINTER(C.c_float)]
+            L.neurosim_interp_get_params.restype = C.c_int
+            L.neurosim_interp_get_params.argtypes = [vp, vp, i64]
+            L.neurosim_interp_set_params.restype = C.c_int
+            L.neurosim_interp_set_params.argtypes = [vp, vp, i64]
+            L.neurosim_interp_launches.restype = C.c_int
+            L.neurosim_interp_launches.argtypes = [vp, C.POINTER(u64)]
+            L.neurosim_interp_destroy.restype = None
+            L.neurosim_interp_destroy.argtypes = [vp]
             _lib = L
     return _lib
 

@@ -1,0 +1,321 @@
+// Operand gathers and epilogues that turn the U-Net layers of the learned
+// interpolator into tensor-core GEMMs (umma_gemm.cuh).  Activations are BF16
+// NHWC; a view selects `C` channels at offset `off` of rows of `stride`
+// channels, so that a concatenation is one buffer written by two layers.
+// Every gather moves 16-byte chunks of 8 channels (channel counts, offsets
+// and strides are multiples of 8).
+//
+//   forward   conv 3x3 (stride 1 or 2):  D[pixel][cout] = im2col(x) * W
+//             convT 2x2 stride 2:        D[in pixel][(a, b, cout)] = x * W
+//   backward  data of conv:  D[in pixel][cin]  = "transposed im2col"(dy) * W^T
+//             data of convT: D[in pixel][cin]  = space-to-depth(dy) * W^T
+//             weights:       D[(tap, cin)][cout] = sum over pixels (split over
+//                            the grid's y dimension, FP32 atomics)
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "umma_gemm.cuh"
+
+namespace interp {
+
+using bf16 = __nv_bfloat16;
+using ugemm::BK;
+using ugemm::kmajor_chunk;
+using ugemm::mnmajor_chunk;
+using ugemm::st_chunk;
+
+struct Act {            // BF16 NHWC view
+    const bf16* p;
+    int N, H, W;        // image size of the view
+    int stride, off;    // channels per pixel row, first channel of the view
+    __device__ __forceinline__ const bf16* at(int n, int y, int x, int c) const
+    {
+        return p + ((size_t)((size_t)n * H + y) * W + x) * stride + off + c;
+    }
+};
+
+__device__ __forceinline__ uint4 ld16(const bf16* p) { return *reinterpret_cast<const uint4*>(p); }
+
+// ---- K-major A gathers (rows = output pixels of the GEMM) ---------------------------
+// conv 3x3, zero padding 1, stride s: row (n, yo, xo), k = tap * C + c reads
+// x(n, s yo + dy - 1, s xo + dx - 1, c).
+struct Conv3K {
+    static constexpr bool MN = false;
+    Act x;
+    int C, Ho, Wo, s, M;
+    template <int R>
+    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    {
+        for (int i = tid; i < R * (BK / 8); i += 128) {
+            const int r = i / (BK / 8), kc = i % (BK / 8);
+            const int m = r0 + r, k = k0 + kc * 8;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (m < M && kc * 8 < kn) {
+                const int hw = Ho * Wo;
+                const int n = m / hw, rem = m - n * hw, yo = rem / Wo, xo = rem - (rem / Wo) * Wo;
+                const int tap = k / C, c = k - tap * C;
+                const int yi = yo * s + tap / 3 - 1, xi = xo * s + tap % 3 - 1;
+                if ((unsigned)yi < (unsigned)x.H && (unsigned)xi < (unsigned)x.W) v = ld16(x.at(n, yi, xi, c));
+            }
+            st_chunk(tile, kmajor_chunk(r, kc * 8), v);
+        }
+    }
+};
+
+// data gradient of a conv 3x3 of stride s: row (n, y, x) at the conv's input
+// size, k = tap * C + c reads dy(n, (y + 1 - dy) / s, (x + 1 - dx) / s, c)
+// where the division is exact (else zero).
+struct Conv3TK {
+    static constexpr bool MN = false;
+    Act g;              // gradient of the conv's output (size Ho x Wo)
+    int C, Hi, Wi, s, M;
+    template <int R>
+    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    {
+        for (int i = tid; i < R * (BK / 8); i += 128) {
+            const int r = i / (BK / 8), kc = i % (BK / 8);
+            const int m = r0 + r, k = k0 + kc * 8;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (m < M && kc * 8 < kn) {
+                const int hw = Hi * Wi;
+                const int n = m / hw, rem = m - n * hw, y = rem / Wi, xx = rem - (rem / Wi) * Wi;
+                const int tap = k / C, c = k - tap * C;
+                const int ty = y + 1 - tap / 3, tx = xx + 1 - tap % 3;
+                if (ty >= 0 && tx >= 0 && ty % s == 0 && tx % s == 0) {
+                    const int yo = ty / s, xo = tx / s;
+                    if (yo < g.H && xo < g.W) v = ld16(g.at(n, yo, xo, c));
+                }
+            }
+            st_chunk(tile, kmajor_chunk(r, kc * 8), v);
+        }
+    }
+};
+
+// 1x1: row = pixel, k = channel.
+struct PixK {
+    static constexpr bool MN = false;
+    Act x;
+    int M;
+    template <int R>
+    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    {
+        for (int i = tid; i < R * (BK / 8); i += 128) {
+            const int r = i / (BK / 8), kc = i % (BK / 8);
+            const int m = r0 + r;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (m < M && kc * 8 < kn) v = ld16(x.p + (size_t)m * x.stride + x.off + k0 + kc * 8);
+            st_chunk(tile, kmajor_chunk(r, kc * 8), v);
+        }
+    }
+};
+
+// data gradient of a convT 2x2 stride 2: row (n, y, x) at the low size,
+// k = (2a + b) * C + c reads g(n, 2y + a, 2x + b, c).
+struct S2DK {
+    static constexpr bool MN = false;
+    Act g;              // full-size gradient
+    int C, Hl, Wl, M;
+    template <int R>
+    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    {
+        for (int i = tid; i < R * (BK / 8); i += 128) {
+            const int r = i / (BK / 8), kc = i % (BK / 8);
+            const int m = r0 + r, k = k0 + kc * 8;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (m < M && kc * 8 < kn) {
+                const int hw = Hl * Wl;
+                const int n = m / hw, rem = m - n * hw, y = rem / Wl, xx = rem - (rem / Wl) * Wl;
+                const int ab = k / C, c = k - ab * C;
+                v = ld16(g.at(n, 2 * y + (ab >> 1), 2 * xx + (ab & 1), c));
+            }
+            st_chunk(tile, kmajor_chunk(r, kc * 8), v);
+        }
+    }
+};
+
+// ---- MN-major gathers (weight gradients: K = pixels) -------------------------------
+// rows (tap, c) of a conv 3x3 stride s at output pixel p: x(n, s yo + dy - 1, s xo + dx - 1, c).
+struct Im2colMN {
+    static constexpr bool MN = true;
+    Act x;
+    int C, Ho, Wo, s, rows, P;
+    template <int R>
+    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    {
+        for (int i = tid; i < (R / 8) * BK; i += 128) {
+            const int k = i / (R / 8), rc = i % (R / 8);
+            const int row = r0 + rc * 8, p = k0 + k;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (row < rows && k < kn && p < P) {
+                const int hw = Ho * Wo;
+                const int n = p / hw, rem = p - n * hw, yo = rem / Wo, xo = rem - (rem / Wo) * Wo;
+                const int tap = row / C, c = row - tap * C;
+                const int yi = yo * s + tap / 3 - 1, xi = xo * s + tap % 3 - 1;
+                if ((unsigned)yi < (unsigned)x.H && (unsigned)xi < (unsigned)x.W) v = ld16(x.at(n, yi, xi, c));
+            }
+            st_chunk(tile, mnmajor_chunk<R>(rc * 8, k), v);
+        }
+    }
+};
+
+// rows = channels at pixel p.
+struct PixMN {
+    static constexpr bool MN = true;
+    Act x;
+    int rows, P;
+    template <int R>
+    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    {
+        for (int i = tid; i < (R / 8) * BK; i += 128) {
+            const int k = i / (R / 8), rc = i % (R / 8);
+            const int row = r0 + rc * 8, p = k0 + k;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (row < rows && k < kn && p < P) v = ld16(x.p + (size_t)p * x.stride + x.off + row);
+            st_chunk(tile, mnmajor_chunk<R>(rc * 8, k), v);
+        }
+    }
+};
+
+// rows (2a + b, c) at low-size pixel p: g(n, 2y + a, 2x + b, c).
+struct S2DMN {
+    static constexpr bool MN = true;
+    Act g;
+    int C, Hl, Wl, rows, P;
+    template <int R>
+    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    {
+        for (int i = tid; i < (R / 8) * BK; i += 128) {
+            const int k = i / (R / 8), rc = i % (R / 8);
+            const int row = r0 + rc * 8, p = k0 + k;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (row < rows && k < kn && p < P) {
+                const int hw = Hl * Wl;
+                const int n = p / hw, rem = p - n * hw, y = rem / Wl, xx = rem - (rem / Wl) * Wl;
+                const int ab = row / C, c = row - ab * C;
+                v = ld16(g.at(n, 2 * y + (ab >> 1), 2 * xx + (ab & 1), c));
+            }
+            st_chunk(tile, mnmajor_chunk<R>(rc * 8, k), v);
+        }
+    }
+};
+
+// ---- epilogues --------------------------------------------------------------------
+__device__ __forceinline__ uint4 pack8(const float (&v)[8])
+{
+    uint4 o;
+    __nv_bfloat162 h;
+    h = __floats2bfloat162_rn(v[0], v[1]);
+    o.x = *reinterpret_cast<uint32_t*>(&h);
+    h = __floats2bfloat162_rn(v[2], v[3]);
+    o.y = *reinterpret_cast<uint32_t*>(&h);
+    h = __floats2bfloat162_rn(v[4], v[5]);
+    o.z = *reinterpret_cast<uint32_t*>(&h);
+    h = __floats2bfloat162_rn(v[6], v[7]);
+    o.w = *reinterpret_cast<uint32_t*>(&h);
+    return o;
+}
+
+__device__ __forceinline__ void unpack8(uint4 u, float (&v)[8])
+{
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[i]);
+        const float2 f = __bfloat1622float2(h);
+        v[2 * i] = f.x;
+        v[2 * i + 1] = f.y;
+    }
+}
+
+// out[row][off + col] = bf16(relu?(acc + bias[col]))
+struct EpiAct {
+    bf16* out;
+    int stride, off;
+    const float* bias;
+    int relu;
+    __device__ __forceinline__ void store(int row, int c0, const float (&v)[8], int) const
+    {
+        float o[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float t = v[i] + bias[c0 + i];
+            o[i] = relu ? fmaxf(t, 0.0f) : t;
+        }
+        *reinterpret_cast<uint4*>(out + (size_t)row * stride + off + c0) = pack8(o);
+    }
+};
+
+// convT 2x2 stride 2: column (2a + b) * Cout + o of input pixel (n, y, x)
+// goes to output pixel (n, 2y + a, 2x + b), channel off + o.
+struct EpiConvT {
+    bf16* out;
+    int stride, off;
+    const float* bias;
+    int Cout, Hl, Wl;
+    __device__ __forceinline__ void store(int row, int c0, const float (&v)[8], int) const
+    {
+        const int hw = Hl * Wl;
+        const int n = row / hw, rem = row - n * hw, y = rem / Wl, x = rem - (rem / Wl) * Wl;
+        const int ab = c0 / Cout, o = c0 - ab * Cout;
+        const size_t pix = ((size_t)n * 2 * Hl + 2 * y + (ab >> 1)) * (2 * Wl) + 2 * x + (ab & 1);
+        float t[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = v[i] + bias[o + i];
+        *reinterpret_cast<uint4*>(out + pix * stride + off + o) = pack8(t);
+    }
+};
+
+// Gradient of a layer input: out[row][off + col] = bf16((acc ? out : 0) + v *
+// mask), mask = act[row][aoff + col] > 0 for col >= mask_from (ReLU inputs),
+// else 1 (linear inputs).
+struct EpiGrad {
+    bf16* out;
+    int stride, off;
+    const bf16* act;
+    int astride, aoff, mask_from, accumulate;
+    __device__ __forceinline__ void store(int row, int c0, const float (&v)[8], int) const
+    {
+        bf16* dst = out + (size_t)row * stride + off + c0;
+        float o[8], a[8], old[8];
+        unpack8(ld16(act + (size_t)row * astride + aoff + c0), a);
+        if (accumulate) unpack8(ld16(dst), old);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float m = (c0 + i < mask_from || a[i] > 0.0f) ? 1.0f : 0.0f;
+            o[i] = v[i] * m + (accumulate ? old[i] : 0.0f);
+        }
+        *reinterpret_cast<uint4*>(dst) = pack8(o);
+    }
+};
+
+// Final 1x1 layer: L_j = L0 + (j / 4)(L4 - L0) + r_{j - 1} + b, j = 1..3 (FP32).
+struct EpiOut {
+    float* out;            // [3][P]
+    const float* L0;
+    const float* L4;
+    const float* bias;
+    int P;
+    __device__ __forceinline__ void store(int row, int c0, const float (&v)[8], int) const
+    {
+        if (c0 != 0) return;
+        const float a = L0[row], d = L4[row] - a;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) out[(size_t)j * P + row] = a + 0.25f * (float)(j + 1) * d + (v[j] + bias[j]);
+    }
+};
+
+// Weight gradient: dw[row][col] += acc (FP32 atomics over the K splits).
+struct EpiDW {
+    float* dw;
+    int ld;
+    __device__ __forceinline__ void store(int row, int c0, const float (&v)[8], int) const
+    {
+        float* d = dw + (size_t)row * ld + c0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) atomicAdd(d + i, v[i]);
+    }
+};
+
+}  // namespace interp

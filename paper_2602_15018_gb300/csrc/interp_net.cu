@@ -1,0 +1,685 @@
+// Learned temporal interpolator (C ABI in include/neurosim_evsim.h,
+// "Learned interpolator"): a 3-level convolutional U-Net that predicts the
+// three log-intensity frames between two keyframes 4 frame periods apart, so
+// that a renderer can run at a quarter of the event camera's frame rate.
+// Every convolution, transposed convolution and their data and weight
+// gradients run as BF16 tcgen05 GEMMs with FP32 accumulation in TMEM
+// (umma_gemm.cuh, interp_layers.cuh); loss, bias gradients, AdamW and weight
+// packing are small CUDA-core kernels.  The paper has no counterpart: it
+// renders every frame (Sec. 2); the network is this project's.
+//
+// Network (activations BF16 NHWC; concatenations share one buffer):
+//   x  = [L0, L4 - L0, 0 x 6]                                   P   x 8
+//   e1 = relu(conv3(x, W1) + b1)        -> cat1[:, 32:64]        P   x 32
+//   e2 = relu(conv3s2(e1, W2) + b2)     -> cat2[:, 64:128]       P/4 x 64
+//   e3 = relu(conv3s2(e2, W3) + b3)                              P/16 x 128
+//   e4 = relu(conv3(e3, W4) + b4)                                P/16 x 128
+//   u1 = convT2(e4, W5) + b5            -> cat2[:, 0:64]         P/4 x 64
+//   d1 = relu(conv3(cat2, W6) + b6)                              P/4 x 64
+//   u2 = convT2(d1, W7) + b7            -> cat1[:, 0:32]         P   x 32
+//   d2 = relu(conv3(cat1, W8) + b8)                              P   x 32
+//   L_j = L0 + j/4 (L4 - L0) + (d2 W9 + b9)_j,  j = 1..3          FP32
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/neurosim_evsim.h"
+#include "evsim_internal.h"
+#include "interp_layers.cuh"
+
+using namespace interp;
+
+namespace {
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return nsim::report_error(code, buf);
+}
+
+#define ICUDA(expr)                                                                    \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(NEUROSIM_E_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                           \
+    } while (0)
+
+// ---- parameters: one flat FP32 array, weights first, then biases ---------------------
+enum LayerKind { CONV, CONVT, FINAL };
+struct LayerDef {
+    LayerKind kind;
+    int cin, cout;
+};
+constexpr int kLayers = 9;
+constexpr LayerDef kDefs[kLayers] = {
+    {CONV, 8, 32},   {CONV, 32, 64},  {CONV, 64, 128}, {CONV, 128, 128}, {CONVT, 128, 64},
+    {CONV, 128, 64}, {CONVT, 64, 32}, {CONV, 64, 32},  {FINAL, 32, 16},
+};
+
+constexpr int64_t weight_count(const LayerDef& d)
+{
+    return d.kind == CONV ? 9ll * d.cin * d.cout : d.kind == CONVT ? 4ll * d.cin * d.cout : (int64_t)d.cin * d.cout;
+}
+
+struct ParamLayout {
+    int64_t w_off[kLayers], b_off[kLayers];
+    int64_t n_weights = 0, total = 0;
+    ParamLayout()
+    {
+        int64_t o = 0;
+        for (int l = 0; l < kLayers; ++l) {
+            w_off[l] = o;
+            o += weight_count(kDefs[l]);
+        }
+        n_weights = o;
+        for (int l = 0; l < kLayers; ++l) {
+            b_off[l] = o;
+            o += kDefs[l].cout;
+        }
+        total = o;
+    }
+};
+
+// ---- CUDA-core kernels -------------------------------------------------------------
+__global__ void pack_input_kernel(const float* L0, const float* L4, int64_t plane_stride, int HW, int P, bf16* x0,
+                                  float* l0c, float* l4c)
+{
+    // L0 / L4 of image n at L0 + n * plane_stride (keyframes inside a clip array)
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const int n = p / HW, q = p - n * HW;
+        const float a = L0[(size_t)n * plane_stride + q], b = L4[(size_t)n * plane_stride + q];
+        l0c[p] = a;
+        l4c[p] = b;
+        float v[8] = {a, b - a, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        *reinterpret_cast<uint4*>(x0 + (size_t)p * 8) = pack8(v);
+    }
+}
+
+// Charbonnier loss over out [3][P] against the targets (frames 1..3 of each
+// clip) and its gradient, written as BF16 [P][16] (columns 3..15 zero).
+__global__ void loss_kernel(const float* out, const float* clips, int HW, int P, float inv_count, bf16* gr,
+                            double* loss_sum)
+{
+    __shared__ double s_part[32];
+    double acc = 0.0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const int n = p / HW, q = p - n * HW;
+        float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float d = out[(size_t)j * P + p] - clips[((size_t)n * 5 + 1 + j) * HW + q];
+            const float s = sqrtf(d * d + 1e-6f);
+            acc += (double)s;
+            g[j] = d / s * inv_count;
+        }
+        uint4* dst = reinterpret_cast<uint4*>(gr + (size_t)p * 16);
+        dst[0] = pack8(g);
+        dst[1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+        atomicAdd(loss_sum, t);
+    }
+}
+
+// db[c] += sum over rows of g[row * stride + off + c], c < C (C divides 256).
+__global__ void bias_grad_kernel(const bf16* g, int rows, int stride, int off, int C, float* db)
+{
+    __shared__ float s[256];
+    const int c = threadIdx.x % C, grp = threadIdx.x / C, G = blockDim.x / C;
+    float acc = 0.0f;
+    for (int r = blockIdx.x * G + grp; r < rows; r += gridDim.x * G)
+        acc += __bfloat162float(g[(size_t)r * stride + off + c]);
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    if (grp == 0) {
+        for (int k = 1; k < G; ++k) acc += s[k * C + c];
+        atomicAdd(db + c, acc);
+    }
+}
+
+// AdamW on the flat parameters; decoupled weight decay on [0, n_weights).
+__global__ void adamw_kernel(float* w, const float* g, float* m, float* v, int64_t n, int64_t n_weights, float lr,
+                             float wd, float b1, float b2, float eps, float bc1, float bc2)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        float upd = (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        if (i < n_weights) upd += wd * w[i];
+        w[i] -= lr * upd;
+    }
+}
+
+// BF16 GEMM operands of one layer from its FP32 master weights:
+//   fwd [N_f][K_f]: conv [cout][tap * cin + c], convT [(ab) * cout + o][cin], final [j][cin]
+//   bwd [N_b][K_b]: conv [cin][tap * cout + o], convT [cin][ab * cout + o], final [cin][j]
+__global__ void pack_weights_kernel(const float* w, int kind, int cin, int cout, bf16* fwd, bf16* bwd)
+{
+    const int taps = kind == CONV ? 9 : kind == CONVT ? 4 : 1;
+    const int n = taps * cin * cout;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        // master index i = (tap * cin + c) * cout + o  (conv, final: tap = 0)
+        //                  c * (4 cout) + ab * cout + o  (convT)
+        int tap, c, o;
+        if (kind == CONVT) {
+            c = i / (4 * cout);
+            const int r = i - c * 4 * cout;
+            tap = r / cout;
+            o = r - tap * cout;
+        } else {
+            o = i % cout;
+            const int tc = i / cout;
+            tap = tc / cin;
+            c = tc - tap * cin;
+        }
+        const bf16 val = __float2bfloat16_rn(w[i]);
+        if (kind == CONVT) {
+            fwd[(size_t)(tap * cout + o) * cin + c] = val;
+            bwd[(size_t)c * (4 * cout) + tap * cout + o] = val;
+        } else {
+            fwd[(size_t)o * (taps * cin) + tap * cin + c] = val;
+            bwd[(size_t)c * (taps * cout) + tap * cout + o] = val;
+        }
+    }
+}
+
+// He-normal initial weights (fan-in), zero final layer and biases: the
+// untrained network is linear interpolation.  Normal draws: Irwin-Hall(12)
+// of SplitMix64 outputs, counter-based by parameter index.
+__device__ __forceinline__ uint64_t sm64(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1ull) * 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void init_weights_kernel(float* w, int64_t n, float scale, int64_t base, uint64_t seed, int kind, int cin,
+                                    int cout, int zero_pad_in)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t acc = 0;
+        for (int k = 0; k < 12; ++k) acc += (int64_t)(sm64(seed, (uint64_t)(base + i) * 12ull + k) >> 44);
+        float z = (float)(acc - 6ll * (1ll << 20)) * 0x1p-20f;
+        const int c = kind == CONVT ? (int)(i / (4 * cout)) : (int)((i / cout) % cin);
+        if (c >= zero_pad_in) z = 0.0f;
+        w[i] = z * scale;
+    }
+}
+
+unsigned grid_for(int64_t n, int threads = 256)
+{
+    int64_t b = (n + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 4096));
+}
+
+}  // namespace
+
+struct neurosim_interp {
+    cudaStream_t stream = nullptr;
+    int device = 0, sms = 0;
+    int64_t Pmax = 0;
+    ParamLayout lay;
+    float* params = nullptr;   // master FP32
+    float* grads = nullptr;
+    float* m = nullptr;
+    float* v = nullptr;
+    bf16* wf[kLayers] = {};    // forward GEMM operands
+    bf16* wb[kLayers] = {};    // backward-data GEMM operands
+    int64_t step = 0;
+    // activations (BF16 NHWC) and their gradients
+    bf16 *x0 = nullptr, *cat1 = nullptr, *cat2 = nullptr, *e3 = nullptr, *e4 = nullptr, *d1 = nullptr, *d2 = nullptr;
+    bf16 *gcat1 = nullptr, *gcat2 = nullptr, *ge3 = nullptr, *ge4 = nullptr, *gd1 = nullptr, *gd2 = nullptr,
+         *gr = nullptr;
+    float *l0 = nullptr, *l4 = nullptr, *out = nullptr;
+    double* loss = nullptr;
+    unsigned int* err = nullptr;
+    uint64_t launches = 0;
+};
+
+namespace {
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count)
+{
+    *p = nullptr;
+    return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+void release(neurosim_interp* h)
+{
+    void* ptrs[] = {h->params, h->grads, h->m, h->v, h->x0, h->cat1, h->cat2, h->e3, h->e4, h->d1, h->d2,
+                    h->gcat1, h->gcat2, h->ge3, h->ge4, h->gd1, h->gd2, h->gr, h->l0, h->l4, h->out, h->loss,
+                    h->err};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int l = 0; l < kLayers; ++l) {
+        if (h->wf[l]) cudaFree(h->wf[l]);
+        if (h->wb[l]) cudaFree(h->wb[l]);
+    }
+}
+
+// ---- GEMM dispatch -------------------------------------------------------------------
+template <int BN, class AG, class BG, class EP>
+cudaError_t gemm_bn(neurosim_interp* h, const AG& a, const BG& b, const EP& ep, int M, int N, int K, int splits,
+                    int k_per_split)
+{
+    ugemm::GemmArgs<AG, BG, EP> g;
+    g.a = a;
+    g.b = b;
+    g.ep = ep;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.k_per_split = k_per_split;
+    g.err = h->err;
+    g.limit_ns = 2000000000ull;
+    h->launches += 1;
+    return ugemm::launch_gemm<BN>(g, splits, h->stream);
+}
+
+// D[M x N] = A * B over K; `split_k` spreads K over CTAs (weight gradients).
+template <class AG, class BG, class EP>
+cudaError_t gemm(neurosim_interp* h, const AG& a, const BG& b, const EP& ep, int M, int N, int K, bool split_k)
+{
+    int splits = 1, kps = ((K + ugemm::BK - 1) / ugemm::BK) * ugemm::BK;
+    if (split_k) {
+        const int mt = (M + ugemm::BM - 1) / ugemm::BM;
+        const int want = std::max(1, (4 * h->sms + mt - 1) / mt);
+        const int kt = (K + ugemm::BK - 1) / ugemm::BK;
+        const int per = std::max(1, (kt + want - 1) / want);
+        kps = per * ugemm::BK;
+        splits = (K + kps - 1) / kps;
+    }
+    if (N <= 16) return gemm_bn<16>(h, a, b, ep, M, N, K, splits, kps);
+    if (N <= 32) return gemm_bn<32>(h, a, b, ep, M, N, K, splits, kps);
+    if (N <= 64) return gemm_bn<64>(h, a, b, ep, M, N, K, splits, kps);
+    if (N <= 128) return gemm_bn<128>(h, a, b, ep, M, N, K, splits, kps);
+    return gemm_bn<256>(h, a, b, ep, M, N, K, splits, kps);
+}
+
+struct Shape {
+    int N, H, W;        // batch and full size
+    int P, P2, P4;      // pixels at full, half and quarter size
+};
+
+Act act(const bf16* p, int N, int H, int W, int stride, int off) { return Act{p, N, H, W, stride, off}; }
+
+const float* bias_of(const neurosim_interp* h, int l) { return h->params + h->lay.b_off[l]; }
+
+int pack_all(neurosim_interp* h)
+{
+    for (int l = 0; l < kLayers; ++l) {
+        const LayerDef& d = kDefs[l];
+        pack_weights_kernel<<<grid_for(weight_count(d)), 256, 0, h->stream>>>(h->params + h->lay.w_off[l], d.kind,
+                                                                            d.cin, d.cout, h->wf[l], h->wb[l]);
+        h->launches += 1;
+    }
+    ICUDA(cudaGetLastError());
+    return NEUROSIM_OK;
+}
+
+// Forward pass; L0 / L4 planes of image n at L0 + n * plane_stride.
+int forward(neurosim_interp* h, const Shape& s, const float* L0, const float* L4, int64_t plane_stride)
+{
+    const int N = s.N, H = s.H, W = s.W, H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
+    pack_input_kernel<<<grid_for(s.P), 256, 0, h->stream>>>(L0, L4, plane_stride, H * W, s.P, h->x0, h->l0, h->l4);
+    h->launches += 1;
+    ICUDA(cudaGetLastError());
+    // e1 -> cat1[:, 32:64]
+    ICUDA(gemm(h, Conv3K{act(h->x0, N, H, W, 8, 0), 8, H, W, 1, s.P}, ugemm::DenseK{h->wf[0], 32, 72},
+               EpiAct{h->cat1, 64, 32, bias_of(h, 0), 1}, s.P, 32, 72, false));
+    // e2 -> cat2[:, 64:128]
+    ICUDA(gemm(h, Conv3K{act(h->cat1, N, H, W, 64, 32), 32, H2, W2, 2, s.P2}, ugemm::DenseK{h->wf[1], 64, 288},
+               EpiAct{h->cat2, 128, 64, bias_of(h, 1), 1}, s.P2, 64, 288, false));
+    // e3
+    ICUDA(gemm(h, Conv3K{act(h->cat2, N, H2, W2, 128, 64), 64, H4, W4, 2, s.P4}, ugemm::DenseK{h->wf[2], 128, 576},
+               EpiAct{h->e3, 128, 0, bias_of(h, 2), 1}, s.P4, 128, 576, false));
+    // e4
+    ICUDA(gemm(h, Conv3K{act(h->e3, N, H4, W4, 128, 0), 128, H4, W4, 1, s.P4}, ugemm::DenseK{h->wf[3], 128, 1152},
+               EpiAct{h->e4, 128, 0, bias_of(h, 3), 1}, s.P4, 128, 1152, false));
+    // u1 -> cat2[:, 0:64]
+    ICUDA(gemm(h, PixK{act(h->e4, N, H4, W4, 128, 0), s.P4}, ugemm::DenseK{h->wf[4], 256, 128},
+               EpiConvT{h->cat2, 128, 0, bias_of(h, 4), 64, H4, W4}, s.P4, 256, 128, false));
+    // d1
+    ICUDA(gemm(h, Conv3K{act(h->cat2, N, H2, W2, 128, 0), 128, H2, W2, 1, s.P2}, ugemm::DenseK{h->wf[5], 64, 1152},
+               EpiAct{h->d1, 64, 0, bias_of(h, 5), 1}, s.P2, 64, 1152, false));
+    // u2 -> cat1[:, 0:32]
+    ICUDA(gemm(h, PixK{act(h->d1, N, H2, W2, 64, 0), s.P2}, ugemm::DenseK{h->wf[6], 128, 64},
+               EpiConvT{h->cat1, 64, 0, bias_of(h, 6), 32, H2, W2}, s.P2, 128, 64, false));
+    // d2
+    ICUDA(gemm(h, Conv3K{act(h->cat1, N, H, W, 64, 0), 64, H, W, 1, s.P}, ugemm::DenseK{h->wf[7], 32, 576},
+               EpiAct{h->d2, 32, 0, bias_of(h, 7), 1}, s.P, 32, 576, false));
+    // frames
+    ICUDA(gemm(h, PixK{act(h->d2, N, H, W, 32, 0), s.P}, ugemm::DenseK{h->wf[8], 16, 32},
+               EpiOut{h->out, h->l0, h->l4, bias_of(h, 8), s.P}, s.P, 16, 32, false));
+    return NEUROSIM_OK;
+}
+
+int bias_grad(neurosim_interp* h, const bf16* g, int rows, int stride, int off, int C, int layer)
+{
+    const int G = 256 / C;
+    const unsigned blocks = (unsigned)std::max(1, std::min(4 * h->sms, (rows + G * 64 - 1) / (G * 64)));
+    bias_grad_kernel<<<blocks, 256, 0, h->stream>>>(g, rows, stride, off, C, h->grads + h->lay.b_off[layer]);
+    h->launches += 1;
+    ICUDA(cudaGetLastError());
+    return NEUROSIM_OK;
+}
+
+// Backward pass after forward() and the loss kernel (gradient of the three
+// outputs in h->gr); accumulates every parameter gradient into h->grads.
+int backward(neurosim_interp* h, const Shape& s)
+{
+    const int N = s.N, H = s.H, W = s.W, H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
+    float* G = h->grads;
+    const ParamLayout& L = h->lay;
+    int rc;
+    ICUDA(cudaMemsetAsync(G, 0, (size_t)L.total * sizeof(float), h->stream));
+    // ---- final 1x1: W9, b9, d(d2)
+    ICUDA(gemm(h, PixMN{act(h->d2, N, H, W, 32, 0), 32, s.P}, PixMN{act(h->gr, N, H, W, 16, 0), 16, s.P},
+               EpiDW{G + L.w_off[8], 16}, 32, 16, s.P, true));
+    if ((rc = bias_grad(h, h->gr, s.P, 16, 0, 16, 8))) return rc;
+    ICUDA(gemm(h, PixK{act(h->gr, N, H, W, 16, 0), s.P}, ugemm::DenseK{h->wb[8], 32, 16},
+               EpiGrad{h->gd2, 32, 0, h->d2, 32, 0, 0, 0}, s.P, 32, 16, false));
+    // ---- conv8 (cat1 -> d2): W8, b8, d(cat1) (u2 linear, e1 masked)
+    ICUDA(gemm(h, Im2colMN{act(h->cat1, N, H, W, 64, 0), 64, H, W, 1, 576, s.P}, PixMN{act(h->gd2, N, H, W, 32, 0), 32, s.P},
+               EpiDW{G + L.w_off[7], 32}, 576, 32, s.P, true));
+    if ((rc = bias_grad(h, h->gd2, s.P, 32, 0, 32, 7))) return rc;
+    ICUDA(gemm(h, Conv3TK{act(h->gd2, N, H, W, 32, 0), 32, H, W, 1, s.P}, ugemm::DenseK{h->wb[7], 64, 288},
+               EpiGrad{h->gcat1, 64, 0, h->cat1, 64, 0, 32, 0}, s.P, 64, 288, false));
+    // ---- convT2 (d1 -> u2): W7, b7, d(d1)
+    ICUDA(gemm(h, PixMN{act(h->d1, N, H2, W2, 64, 0), 64, s.P2}, S2DMN{act(h->gcat1, N, H, W, 64, 0), 32, H2, W2, 128, s.P2},
+               EpiDW{G + L.w_off[6], 128}, 64, 128, s.P2, true));
+    if ((rc = bias_grad(h, h->gcat1, s.P, 64, 0, 32, 6))) return rc;
+    ICUDA(gemm(h, S2DK{act(h->gcat1, N, H, W, 64, 0), 32, H2, W2, s.P2}, ugemm::DenseK{h->wb[6], 64, 128},
+               EpiGrad{h->gd1, 64, 0, h->d1, 64, 0, 0, 0}, s.P2, 64, 128, false));
+    // ---- conv6 (cat2 -> d1): W6, b6, d(cat2) (u1 linear, e2 masked)
+    ICUDA(gemm(h, Im2colMN{act(h->cat2, N, H2, W2, 128, 0), 128, H2, W2, 1, 1152, s.P2},
+               PixMN{act(h->gd1, N, H2, W2, 64, 0), 64, s.P2}, EpiDW{G + L.w_off[5], 64}, 1152, 64, s.P2, true));
+    if ((rc = bias_grad(h, h->gd1, s.P2, 64, 0, 64, 5))) return rc;
+    ICUDA(gemm(h, Conv3TK{act(h->gd1, N, H2, W2, 64, 0), 64, H2, W2, 1, s.P2}, ugemm::DenseK{h->wb[5], 128, 576},
+               EpiGrad{h->gcat2, 128, 0, h->cat2, 128, 0, 64, 0}, s.P2, 128, 576, false));
+    // ---- convT1 (e4 -> u1): W5, b5, d(e4)
+    ICUDA(gemm(h, PixMN{act(h->e4, N, H4, W4, 128, 0), 128, s.P4},
+               S2DMN{act(h->gcat2, N, H2, W2, 128, 0), 64, H4, W4, 256, s.P4}, EpiDW{G + L.w_off[4], 256}, 128, 256,
+               s.P4, true));
+    if ((rc = bias_grad(h, h->gcat2, s.P2, 128, 0, 64, 4))) return rc;
+    ICUDA(gemm(h, S2DK{act(h->gcat2, N, H2, W2, 128, 0), 64, H4, W4, s.P4}, ugemm::DenseK{h->wb[4], 128, 256},
+               EpiGrad{h->ge4, 128, 0, h->e4, 128, 0, 0, 0}, s.P4, 128, 256, false));
+    // ---- conv4 (e3 -> e4): W4, b4, d(e3)
+    ICUDA(gemm(h, Im2colMN{act(h->e3, N, H4, W4, 128, 0), 128, H4, W4, 1, 1152, s.P4},
+               PixMN{act(h->ge4, N, H4, W4, 128, 0), 128, s.P4}, EpiDW{G + L.w_off[3], 128}, 1152, 128, s.P4, true));
+    if ((rc = bias_grad(h, h->ge4, s.P4, 128, 0, 128, 3))) return rc;
+    ICUDA(gemm(h, Conv3TK{act(h->ge4, N, H4, W4, 128, 0), 128, H4, W4, 1, s.P4}, ugemm::DenseK{h->wb[3], 128, 1152},
+               EpiGrad{h->ge3, 128, 0, h->e3, 128, 0, 0, 0}, s.P4, 128, 1152, false));
+    // ---- conv3 (e2 -> e3, stride 2): W3, b3, d(e2) added into d(cat2)[:, 64:128]
+    ICUDA(gemm(h, Im2colMN{act(h->cat2, N, H2, W2, 128, 64), 64, H4, W4, 2, 576, s.P4},
+               PixMN{act(h->ge3, N, H4, W4, 128, 0), 128, s.P4}, EpiDW{G + L.w_off[2], 128}, 576, 128, s.P4, true));
+    if ((rc = bias_grad(h, h->ge3, s.P4, 128, 0, 128, 2))) return rc;
+    ICUDA(gemm(h, Conv3TK{act(h->ge3, N, H4, W4, 128, 0), 128, H2, W2, 2, s.P2}, ugemm::DenseK{h->wb[2], 64, 1152},
+               EpiGrad{h->gcat2, 128, 64, h->cat2, 128, 64, 0, 1}, s.P2, 64, 1152, false));
+    // ---- conv2 (e1 -> e2, stride 2): W2, b2, d(e1) added into d(cat1)[:, 32:64]
+    ICUDA(gemm(h, Im2colMN{act(h->cat1, N, H, W, 64, 32), 32, H2, W2, 2, 288, s.P2},
+               PixMN{act(h->gcat2, N, H2, W2, 128, 64), 64, s.P2}, EpiDW{G + L.w_off[1], 64}, 288, 64, s.P2, true));
+    if ((rc = bias_grad(h, h->gcat2, s.P2, 128, 64, 64, 1))) return rc;
+    ICUDA(gemm(h, Conv3TK{act(h->gcat2, N, H2, W2, 128, 64), 64, H, W, 2, s.P}, ugemm::DenseK{h->wb[1], 32, 576},
+               EpiGrad{h->gcat1, 64, 32, h->cat1, 64, 32, 0, 1}, s.P, 32, 576, false));
+    // ---- conv1 (x -> e1): W1, b1
+    ICUDA(gemm(h, Im2colMN{act(h->x0, N, H, W, 8, 0), 8, H, W, 1, 72, s.P}, PixMN{act(h->gcat1, N, H, W, 64, 32), 32, s.P},
+               EpiDW{G + L.w_off[0], 32}, 72, 32, s.P, true));
+    if ((rc = bias_grad(h, h->gcat1, s.P, 64, 32, 32, 0))) return rc;
+    return NEUROSIM_OK;
+}
+
+int check_shape(const neurosim_interp* h, int batch, int height, int width, Shape* s)
+{
+    if (batch < 1 || height < 4 || width < 4 || height % 4 || width % 4)
+        return fail(NEUROSIM_E_INVALID, "batch >= 1 and height, width >= 4 and divisible by 4 required");
+    const int64_t P = (int64_t)batch * height * width;
+    if (P > h->Pmax) return fail(NEUROSIM_E_INVALID, "batch * height * width %lld exceeds the capacity %lld", (long long)P,
+                                 (long long)h->Pmax);
+    s->N = batch;
+    s->H = height;
+    s->W = width;
+    s->P = (int)P;
+    s->P2 = (int)(P / 4);
+    s->P4 = (int)(P / 16);
+    return NEUROSIM_OK;
+}
+
+int finish(neurosim_interp* h)
+{
+    unsigned int e = 0;
+    ICUDA(cudaMemcpyAsync(&e, h->err, sizeof e, cudaMemcpyDeviceToHost, h->stream));
+    ICUDA(cudaStreamSynchronize(h->stream));
+    if (e) {
+        cudaMemsetAsync(h->err, 0, sizeof(unsigned int), h->stream);
+        return fail(NEUROSIM_E_TIMEOUT, "a bounded tensor-core wait timed out");
+    }
+    return NEUROSIM_OK;
+}
+
+int loss_and_backward(neurosim_interp* h, const Shape& s, const float* clips, float* loss_out)
+{
+    const int HW = s.H * s.W;
+    int rc = forward(h, s, clips, clips + 4 * (int64_t)HW, 5ll * HW);
+    if (rc) return rc;
+    ICUDA(cudaMemsetAsync(h->loss, 0, sizeof(double), h->stream));
+    loss_kernel<<<grid_for(s.P), 256, 0, h->stream>>>(h->out, clips, HW, s.P, 1.0f / (3.0f * (float)s.P), h->gr, h->loss);
+    h->launches += 1;
+    ICUDA(cudaGetLastError());
+    rc = backward(h, s);
+    if (rc) return rc;
+    if (loss_out) {
+        double l = 0.0;
+        ICUDA(cudaMemcpyAsync(&l, h->loss, sizeof l, cudaMemcpyDeviceToHost, h->stream));
+        rc = finish(h);
+        if (rc) return rc;
+        *loss_out = (float)(l / (3.0 * (double)s.P));
+    }
+    return NEUROSIM_OK;
+}
+
+struct IGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit IGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~IGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int64_t neurosim_interp_param_count(void) { return ParamLayout().total; }
+
+int neurosim_interp_create(int32_t max_batch, int32_t max_height, int32_t max_width, uint64_t seed, void* cuda_stream,
+                           neurosim_interp** out)
+{
+    if (!out) return fail(NEUROSIM_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (max_batch < 1 || max_height < 4 || max_width < 4 || max_height % 4 || max_width % 4)
+        return fail(NEUROSIM_E_INVALID, "max_batch >= 1 and max_height, max_width >= 4 and divisible by 4 required");
+    const int64_t P = (int64_t)max_batch * max_height * max_width;
+    if (P > (1ll << 30) / 64) return fail(NEUROSIM_E_INVALID, "max_batch * max_height * max_width too large");
+    neurosim_interp* h = new (std::nothrow) neurosim_interp();
+    if (!h) return fail(NEUROSIM_E_NOMEM, "host allocation failed");
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->Pmax = P;
+    auto bail = [&](int code) {
+        release(h);
+        delete h;
+        return code;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+        return bail(fail(NEUROSIM_E_CUDA, "no CUDA device"));
+    const ParamLayout& L = h->lay;
+    bool ok = dalloc(&h->params, L.total) == cudaSuccess && dalloc(&h->grads, L.total) == cudaSuccess &&
+              dalloc(&h->m, L.total) == cudaSuccess && dalloc(&h->v, L.total) == cudaSuccess;
+    for (int l = 0; l < kLayers && ok; ++l)
+        ok = dalloc(&h->wf[l], weight_count(kDefs[l])) == cudaSuccess &&
+             dalloc(&h->wb[l], weight_count(kDefs[l])) == cudaSuccess;
+    const size_t p = (size_t)P, p2 = p / 4, p4 = p / 16;
+    ok = ok && dalloc(&h->x0, p * 8) == cudaSuccess && dalloc(&h->cat1, p * 64) == cudaSuccess &&
+         dalloc(&h->cat2, p2 * 128) == cudaSuccess && dalloc(&h->e3, p4 * 128) == cudaSuccess &&
+         dalloc(&h->e4, p4 * 128) == cudaSuccess && dalloc(&h->d1, p2 * 64) == cudaSuccess &&
+         dalloc(&h->d2, p * 32) == cudaSuccess && dalloc(&h->gcat1, p * 64) == cudaSuccess &&
+         dalloc(&h->gcat2, p2 * 128) == cudaSuccess && dalloc(&h->ge3, p4 * 128) == cudaSuccess &&
+         dalloc(&h->ge4, p4 * 128) == cudaSuccess && dalloc(&h->gd1, p2 * 64) == cudaSuccess &&
+         dalloc(&h->gd2, p * 32) == cudaSuccess && dalloc(&h->gr, p * 16) == cudaSuccess &&
+         dalloc(&h->l0, p) == cudaSuccess && dalloc(&h->l4, p) == cudaSuccess && dalloc(&h->out, 3 * p) == cudaSuccess &&
+         dalloc(&h->loss, 1) == cudaSuccess && dalloc(&h->err, 1) == cudaSuccess;
+    if (!ok) return bail(fail(NEUROSIM_E_NOMEM, "device allocation of the interpolator failed"));
+    if (cudaMemsetAsync(h->params, 0, (size_t)L.total * 4, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->m, 0, (size_t)L.total * 4, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->v, 0, (size_t)L.total * 4, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->err, 0, 4, h->stream) != cudaSuccess)
+        return bail(fail(NEUROSIM_E_CUDA, "cudaMemsetAsync failed"));
+    for (int l = 0; l < kLayers - 1; ++l) {
+        const LayerDef& d = kDefs[l];
+        const int fan_in = d.kind == CONV ? 9 * d.cin : d.cin;
+        init_weights_kernel<<<grid_for(weight_count(d)), 256, 0, h->stream>>>(
+            h->params + L.w_off[l], weight_count(d), std::sqrt(2.0f / (float)fan_in), L.w_off[l], seed, d.kind, d.cin,
+            d.cout, l == 0 ? 2 : d.cin);
+    }
+    if (cudaGetLastError() != cudaSuccess || pack_all(h) || cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return bail(fail(NEUROSIM_E_CUDA, "initialising the weights failed"));
+    *out = h;
+    return NEUROSIM_OK;
+}
+
+int neurosim_interp_forward(neurosim_interp* h, const float* L0_dev, const float* L4_dev, int32_t batch,
+                            int32_t height, int32_t width, float* out_dev)
+{
+    if (!h || !L0_dev || !L4_dev || !out_dev) return fail(NEUROSIM_E_INVALID, "NULL argument");
+    Shape s;
+    int rc = check_shape(h, batch, height, width, &s);
+    if (rc) return rc;
+    IGuard g(h->device);
+    if (!g.ok) return fail(NEUROSIM_E_CUDA, "cannot select the device");
+    rc = forward(h, s, L0_dev, L4_dev, (int64_t)height * width);
+    if (rc) return rc;
+    ICUDA(cudaMemcpyAsync(out_dev, h->out, (size_t)3 * s.P * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    return NEUROSIM_OK;
+}
+
+int neurosim_interp_gradients(neurosim_interp* h, const float* clips_dev, int32_t batch, int32_t height, int32_t width,
+                              float* grads_host, float* loss_out)
+{
+    if (!h || !clips_dev) return fail(NEUROSIM_E_INVALID, "NULL argument");
+    Shape s;
+    int rc = check_shape(h, batch, height, width, &s);
+    if (rc) return rc;
+    IGuard g(h->device);
+    if (!g.ok) return fail(NEUROSIM_E_CUDA, "cannot select the device");
+    float l = 0.0f;
+    rc = loss_and_backward(h, s, clips_dev, &l);
+    if (rc) return rc;
+    if (loss_out) *loss_out = l;
+    if (grads_host) {
+        ICUDA(cudaMemcpyAsync(grads_host, h->grads, (size_t)h->lay.total * 4, cudaMemcpyDeviceToHost, h->stream));
+        ICUDA(cudaStreamSynchronize(h->stream));
+    }
+    return NEUROSIM_OK;
+}
+
+int neurosim_interp_train_step(neurosim_interp* h, const float* clips_dev, int32_t batch, int32_t height,
+                               int32_t width, float lr, float weight_decay, float* loss_out)
+{
+    if (!h || !clips_dev) return fail(NEUROSIM_E_INVALID, "NULL argument");
+    if (!(lr >= 0.0f && lr < 1.0f) || !(weight_decay >= 0.0f && weight_decay < 1.0f))
+        return fail(NEUROSIM_E_INVALID, "lr and weight_decay must be in [0, 1)");
+    Shape s;
+    int rc = check_shape(h, batch, height, width, &s);
+    if (rc) return rc;
+    IGuard g(h->device);
+    if (!g.ok) return fail(NEUROSIM_E_CUDA, "cannot select the device");
+    rc = loss_and_backward(h, s, clips_dev, loss_out);
+    if (rc) return rc;
+    h->step += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const float bc1 = (float)(1.0 - std::pow(b1, (double)h->step)), bc2 = (float)(1.0 - std::pow(b2, (double)h->step));
+    adamw_kernel<<<grid_for(h->lay.total), 256, 0, h->stream>>>(h->params, h->grads, h->m, h->v, h->lay.total,
+                                                                h->lay.n_weights, lr, weight_decay, (float)b1,
+                                                                (float)b2, 1e-8f, bc1, bc2);
+    h->launches += 1;
+    ICUDA(cudaGetLastError());
+    rc = pack_all(h);
+    if (rc) return rc;
+    if (loss_out) return finish(h);
+    return NEUROSIM_OK;
+}
+
+int neurosim_interp_get_params(neurosim_interp* h, float* host, int64_t n)
+{
+    if (!h || !host) return fail(NEUROSIM_E_INVALID, "NULL argument");
+    if (n != h->lay.total) return fail(NEUROSIM_E_INVALID, "n must be %lld", (long long)h->lay.total);
+    IGuard g(h->device);
+    ICUDA(cudaMemcpyAsync(host, h->params, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
+    ICUDA(cudaStreamSynchronize(h->stream));
+    return NEUROSIM_OK;
+}
+
+int neurosim_interp_set_params(neurosim_interp* h, const float* host, int64_t n)
+{
+    if (!h || !host) return fail(NEUROSIM_E_INVALID, "NULL argument");
+    if (n != h->lay.total) return fail(NEUROSIM_E_INVALID, "n must be %lld", (long long)h->lay.total);
+    IGuard g(h->device);
+    ICUDA(cudaMemcpyAsync(h->params, host, (size_t)n * 4, cudaMemcpyHostToDevice, h->stream));
+    ICUDA(cudaMemsetAsync(h->m, 0, (size_t)n * 4, h->stream));
+    ICUDA(cudaMemsetAsync(h->v, 0, (size_t)n * 4, h->stream));
+    h->step = 0;
+    int rc = pack_all(h);
+    if (rc) return rc;
+    ICUDA(cudaStreamSynchronize(h->stream));
+    return NEUROSIM_OK;
+}
+
+int neurosim_interp_launches(neurosim_interp* h, uint64_t* launches)
+{
+    if (!h || !launches) return fail(NEUROSIM_E_INVALID, "NULL argument");
+    *launches = h->launches;
+    return NEUROSIM_OK;
+}
+
+void neurosim_interp_destroy(neurosim_interp* h)
+{
+    if (!h) return;
+    {
+        IGuard g(h->device);
+        cudaStreamSynchronize(h->stream);
+        release(h);
+    }
+    delete h;
+}
+
+}  // extern "C"

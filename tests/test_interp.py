@@ -1,0 +1,155 @@
+"""The learned interpolator on the tensor cores against its FP64 oracle.
+
+The oracle rounds to BF16 exactly what the GPU stores in BF16 (weights and
+activations), so the two differ by FP32 accumulation order and by the BF16
+rounding of gradients the GPU keeps between layers; the tolerances below are
+derived from that: outputs within 1 % of the residual scale, gradients within
+a few BF16 ulps (2^-8) relative in norm.  Shapes: batch 2, 16 x 24 (several
+128-row tiles at full size, ragged tails at the quarter size).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import interp_oracle as io
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _params(seed):
+    p = io.init_params(seed)
+    rng = np.random.default_rng(seed + 7)
+    p["W9"] = rng.standard_normal((32, 3)) * 0.2
+    for k, n in io.BIAS.items():
+        p[k] = rng.standard_normal(n) * 0.05
+    return p
+
+
+def _clips(seed, N, H, W):
+    """Smooth log-intensity clips [N, 5, H, W]: moving sinusoid patterns."""
+    rng = np.random.default_rng(seed)
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    out = np.zeros((N, 5, H, W))
+    for n in range(N):
+        for _ in range(3):
+            fx, fy = rng.uniform(0.05, 0.3, 2)
+            vx, vy = rng.uniform(-1.5, 1.5, 2)
+            ph, a = rng.uniform(0, 6.28), rng.uniform(0.2, 0.6)
+            for f in range(5):
+                out[n, f] += a * np.sin(fx * (x - vx * f) + fy * (y - vy * f) + ph)
+        out[n] += rng.uniform(-3.0, -1.0)
+    return out
+
+
+def _net(p, N=2, H=16, W=24):
+    from paper_2602_15018_gb300 import Interpolator
+    from paper_2602_15018_gb300.interp import from_dict
+    net = Interpolator(N, H, W, seed=1)
+    net.set_params(from_dict({k: np.asarray(v, np.float32) for k, v in p.items()}))
+    return net
+
+
+def test_param_roundtrip_and_untrained_is_linear():
+    from paper_2602_15018_gb300 import Interpolator
+    from paper_2602_15018_gb300.interp import to_dict
+    net = Interpolator(2, 16, 24, seed=3)
+    p = to_dict(net.get_params())
+    assert np.all(p["W9"] == 0) and np.all(p["b9"] == 0) and np.all(p["W1"][:, :, 2:, :] == 0)
+    assert 0.5 < np.std(p["W4"]) * np.sqrt(9 * 128 / 2.0) < 1.5        # He-normal scale
+    c = torch.from_numpy(_clips(0, 2, 16, 24)).float().cuda()
+    out = net.forward(c[:, 0].contiguous(), c[:, 4].contiguous())
+    L0, L4 = c[:, 0], c[:, 4]
+    for j in range(3):
+        assert torch.allclose(out[j], L0 + (j + 1) / 4 * (L4 - L0), atol=1e-6)
+    net.close()
+
+
+def test_forward_matches_oracle():
+    p = _params(11)
+    clips = _clips(1, 2, 16, 24)
+    net = _net(p)
+    c = torch.from_numpy(clips).float().cuda()
+    out = net.forward(c[:, 0].contiguous(), c[:, 4].contiguous()).cpu().numpy()
+    ref, _ = io.forward(p, clips[:, 0].astype(np.float32), clips[:, 4].astype(np.float32), quantize=True)
+    base = np.stack([clips[:, 0] + (j + 1) / 4 * (clips[:, 4] - clips[:, 0]) for j in range(3)])
+    r_ref = ref - base
+    scale = np.abs(r_ref).max()
+    assert scale > 0.05
+    assert np.abs(out - ref).max() <= 0.01 * scale + 1e-4, np.abs(out - ref).max()
+    net.close()
+
+
+def test_gradients_match_oracle():
+    p = _params(12)
+    clips = _clips(2, 2, 16, 24).astype(np.float32)
+    net = _net(p)
+    loss, g = net.gradients(torch.from_numpy(clips).cuda())
+    from paper_2602_15018_gb300.interp import to_dict
+    gd = to_dict(g)
+    ref_loss, ref_g, _ = io.loss_and_grads(p, clips[:, 0], clips[:, 4], np.moveaxis(clips[:, 1:4], 1, 0),
+                                           quantize=True)
+    assert abs(loss - ref_loss) <= 1e-3 * ref_loss
+    for k in list(io.SHAPES) + list(io.BIAS):
+        a, b = np.asarray(gd[k], np.float64).reshape(-1), ref_g[k].reshape(-1)
+        nb = np.linalg.norm(b)
+        if nb == 0:
+            assert np.linalg.norm(a) == 0, k
+            continue
+        rel = np.linalg.norm(a - b) / nb
+        assert rel < 0.03, (k, rel)
+    net.close()
+
+
+def test_train_step_applies_adamw():
+    from paper_2602_15018_gb300.interp import to_dict
+    p = _params(13)
+    clips = torch.from_numpy(_clips(3, 2, 16, 24)).float().cuda()
+    net = _net(p)
+    p0 = net.get_params().astype(np.float64)
+    _, g = net.gradients(clips)
+    net.set_params(p0.astype(np.float32))            # resets the optimiser state
+    lr, wd = 1e-3, 1e-4
+    net.train_step(clips, lr, wd)
+    p1 = net.get_params().astype(np.float64)
+    st = io.adamw_init(to_dict(p0))
+    want = io.adamw_step(to_dict(p0), to_dict(g.astype(np.float64)), st, lr, wd=wd)
+    got = to_dict(p1)
+    for k in want:
+        assert np.allclose(got[k], want[k], atol=2e-6, rtol=1e-5), k
+    net.close()
+
+
+def test_training_beats_linear_interpolation():
+    """A few hundred steps on moving patterns: the trained network predicts the
+    intermediate frames of held-out clips better than linear interpolation
+    (the untrained network), by at least 10 % in mean absolute log error, and
+    the training loss falls."""
+    from paper_2602_15018_gb300 import Interpolator
+    N, H, W = 8, 32, 32
+    net = Interpolator(N, H, W, seed=5)
+    held = torch.from_numpy(_clips(999, N, H, W)).float().cuda()
+
+    def err(model):
+        out = model.forward(held[:, 0].contiguous(), held[:, 4].contiguous())
+        return (out - held[:, 1:4].permute(1, 0, 2, 3)).abs().mean().item()
+
+    e0 = err(net)
+    losses = []
+    for it in range(300):
+        clips = torch.from_numpy(_clips(it, N, H, W)).float().cuda()
+        loss = net.train_step(clips, 2e-3 * (0.5 + 0.5 * np.cos(np.pi * it / 300)), 1e-4,
+                              want_loss=(it < 10 or it >= 290))
+        if loss is not None:
+            losses.append(loss)
+    e1 = err(net)
+    assert np.mean(losses[-10:]) < 0.9 * np.mean(losses[:10]), losses
+    assert e1 < 0.9 * e0, (e0, e1)
+    net.close()
