@@ -366,6 +366,15 @@ int neurosim_interp_launches(neurosim_interp *h, uint64_t *launches);
 /* Frees the network (synchronises its stream first). */
 void neurosim_interp_destroy(neurosim_interp *h);
 
+/* Scores HOST event records `pred` against `ref` (any order): events match
+ * one to one inside the same pixel and polarity, greedily in time order,
+ * when their times differ by at most tol_us.  counts = {matched, n_pred,
+ * n_ref, sum over (pixel, polarity) of |n_pred - n_ref|}; scores =
+ * {precision, recall, F1, count error = counts[3] / n_ref}.  The paper defines
+ * no score; this is the one the learned interpolator is judged by. */
+int neurosim_event_f1(const uint64_t *pred, int64_t n_pred, const uint64_t *ref, int64_t n_ref,
+                      int64_t tol_us, int64_t *counts, double *scores);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *neurosim_last_error(void);
 

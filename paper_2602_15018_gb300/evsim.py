@@ -382,3 +382,19 @@ def autotune(frames: torch.Tensor, dt_us: int = 1000, repeats: int = 5, cache_pa
                                         int(repeats), cache_path.encode() if cache_path else None,
                                         C.byref(ppt), C.byref(pf), C.byref(ms)))
     return int(ppt.value), int(pf.value), float(ms.value)
+
+
+def event_f1(pred, ref, tol_us: int = 1000) -> dict:
+    """Event F1 and count error of `pred` against `ref` (uint64 records, any
+    order), scored by the library (C ABI neurosim_event_f1)."""
+    a = np.ascontiguousarray(np.asarray(pred).view(np.uint64) if np.asarray(pred).dtype == np.int64
+                             else np.asarray(pred, np.uint64))
+    b = np.ascontiguousarray(np.asarray(ref).view(np.uint64) if np.asarray(ref).dtype == np.int64
+                             else np.asarray(ref, np.uint64))
+    counts = (C.c_int64 * 4)()
+    scores = (C.c_double * 4)()
+    check(lib().neurosim_event_f1(C.c_void_p(a.ctypes.data), a.size, C.c_void_p(b.ctypes.data), b.size,
+                                  int(tol_us), counts, scores))
+    return dict(matched=int(counts[0]), n_pred=int(counts[1]), n_ref=int(counts[2]),
+                count_abs_err=int(counts[3]), precision=float(scores[0]), recall=float(scores[1]),
+                f1=float(scores[2]), count_err=float(scores[3]))
