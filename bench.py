@@ -88,6 +88,9 @@ WORKLOADS = {
     "c1": dict(dims=C1, sim=CONFIG1_SIM, render=render_config1,
                name="plain 240x180 FP32, 200 frames @1000 FPS, 8 translating sinusoids, "
                     "C+-0.2, no noise, no refractory"),
+    "learned": dict(dims=None, sim=None, render=None,
+                    name="learned: HD 1280x720 texture clip, keyframes at 250 FPS, U-Net predicts 3 log frames "
+                         "per interval, exact event emission at 1000 FPS; C+0.2 C-0.25 sigma0.03 refractory 100us"),
     "batch": dict(dims=None, sim=None, render=None,
                   name="batched: 256 sensors (346x260 / 640x480 / 1280x720 by index mod 3), "
                        "16 frames @1000 FPS per step, texture scenes, C+- ~ U[0.15,0.35], "
@@ -480,6 +483,127 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+UNET_FLOP_PER_PX = 2 * (9 * 8 * 32 + 9 * 32 * 64 // 4 + 9 * 64 * 128 // 16 + 9 * 128 * 128 // 16
+                        + 128 * 256 // 16 + 9 * 128 * 64 // 4 + 64 * 128 // 4 + 9 * 64 * 32 + 32 * 16)
+
+
+def measured_bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def run_learned(args):
+    """Learned path at HD: train the interpolator on 1000 FPS clips, score its
+    events against the plain 1000 FPS path, and time both pipelines."""
+    from paper_2602_15018_gb300 import EventSim, Interpolator, log_intensity
+    from paper_2602_15018_gb300 import learned
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    W, H = HD["W"], HD["H"]
+    K = args.keys
+    T = 4 * (K - 1) + 1
+    npix = W * H
+    net = Interpolator(8, H, W, seed=args.seed)
+    t_tr = time.time()
+    losses = learned.train(net, args.train_steps, batch=16, size=256, lr=2e-3, speed=(150.0, 600.0),
+                           seed=10000 + 7919 * rank, report=max(1, args.train_steps // 8))
+    torch.cuda.synchronize()
+    train_s = time.time() - t_tr
+    score = learned.evaluate(net, W, H, K, scene_seed=args.seed + rank, **CONFIG2_SIM)
+
+    sc = scenes.TextureScene(W, H, seed=args.seed + 100 + rank)
+    st = torch.cuda.current_stream()
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def plain_once():
+        a, b, c = ev(), ev(), ev()
+        a.record(st)
+        fr = scenes.render_frames(sc, T, device=dev, chunk=32)
+        b.record(st)
+        n = len(learned.events_of(fr, False, **CONFIG2_SIM))
+        c.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), b.elapsed_time(c), n
+
+    def learned_once():
+        a, b, c, d = ev(), ev(), ev(), ev()
+        a.record(st)
+        keys = sc.render(np.arange(0, T, 4), device=dev).contiguous()
+        b.record(st)
+        seq = learned.interpolate_sequence(net, log_intensity(keys))
+        c.record(st)
+        n = len(learned.events_of(seq, True, **CONFIG2_SIM))
+        d.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), b.elapsed_time(c), c.elapsed_time(d), n
+
+    def unet_only():
+        L0 = torch.randn((8, H, W), device=dev) * 0.3 - 2.0
+        L4 = L0 + torch.randn((8, H, W), device=dev) * 0.05
+        out = torch.empty((3, 8, H, W), device=dev)
+        a, b = ev(), ev()
+        a.record(st)
+        net.forward(L0, L4, out)
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    for _ in range(args.warmup):
+        plain_once()
+        learned_once()
+        unet_only()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    tw0 = time.time()
+    pl = [plain_once() for _ in range(args.steps)]
+    le = [learned_once() for _ in range(args.steps)]
+    un = [unet_only() for _ in range(args.steps)]
+    tw1 = time.time()
+    clocks.stop()
+    med = lambda xs: float(statistics.median(xs))
+    r_all, e_plain = med([x[0] for x in pl]), med([x[1] for x in pl])
+    r_keys, u_ms, e_learn = med([x[0] for x in le]), med([x[1] for x in le]), med([x[2] for x in le])
+    unet_ms = med(un)
+    px = T * npix
+    value = px / ((u_ms + e_learn) / 1e3) / 1e6
+    tflops = 8 * npix * UNET_FLOP_PER_PX / (unet_ms / 1e3) / 1e12
+    peak, peak_src = measured_bf16_peak()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "Mpixel-frames/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(u_ms + e_learn, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (U-Net), f32 (events)",
+            "data": "synthetic (seeded procedural scenes rendered on the device)",
+            "config": {"workload": WORKLOADS["learned"]["name"], "width": W, "height": H, "keyframes": K,
+                       "frames": T, "dt_us": DT, "parallelism": f"replicas x{ws}",
+                       "l2": "frames and activations far larger than L2; no flush"},
+            "f1": round(score["learned"]["f1"], 4), "f1_linear": round(score["linear"]["f1"], 4),
+            "count_err": round(score["learned"]["count_err"], 4),
+            "count_err_linear": round(score["linear"]["count_err"], 4),
+            "plain_value": round(px / (e_plain / 1e3) / 1e6, 1),
+            "ms": {"render_all": round(r_all, 3), "events_plain": round(e_plain, 3), "render_keys": round(r_keys, 3),
+                   "unet_all_intervals": round(u_ms, 3), "events_learned": round(e_learn, 3)},
+            "e2e_speedup_vs_plain": round((r_all + e_plain) / (r_keys + u_ms + e_learn), 3),
+            "train": {"steps": args.train_steps, "seconds": round(train_s, 1), "crops": "16 x 256x256",
+                      "loss": [[int(i), round(float(l), 6)] for i, l in losses]},
+            "gpu_launches": None,
+            "roofline": {"bound": "tensor", "achieved": round(tflops, 1), "peak": peak, "unit": "TFLOP/s",
+                         "frac": round(tflops / peak, 4), "traffic": None,
+                         "kernel": "U-Net forward, 8 HD intervals (9 tcgen05 GEMMs)", "peak_source": peak_src},
+            "e2e": None, "cpu_baseline": None,
+            "clocks": clocks.summary(tw0, tw1),
+        }
+        print(json.dumps(line), flush=True)
+    net.close()
+
+
 def _oracle_sample_frames(args, dev):
     wl = WORKLOADS[args.workload]
     n = min(args.cpu_frames, wl["dims"]["T"])
@@ -570,17 +694,21 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-frames", type=int, default=480)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--keys", type=int, default=126, help="learned workload: keyframes per clip")
+    ap.add_argument("--train-steps", type=int, default=1500, help="learned workload: training steps")
     ap.add_argument("--frames", type=int, default=0,
                     help="frames per step (default: the workload's); for small profiling cases")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
-        if args.workload == "batch":
+        if args.workload in ("batch", "learned"):
             ap.error("the reference arm runs the plain workloads only")
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

@@ -389,6 +389,13 @@ int32_t neurosim_abi_version(void);
 int neurosim_debug_umma_gemm(int32_t mode, int32_t M, int32_t N, int32_t K, const void *A,
                              const void *B, float *C, void *cuda_stream);
 
+/* The event model's log intensity of n DEVICE floats (Sec. 2 contrast model,
+ * reading: L = log(clamp(I, 0, 1e6) + log_eps) with the library's FP32 log):
+ * L_dev[i] = the L the emission kernel computes for I_dev[i].  Feeding these
+ * frames with input_is_log = 1 gives the same events as the raw frames with
+ * input_is_log = 0.  Asynchronous on cuda_stream. */
+int neurosim_log_intensity(const float *I_dev, float *L_dev, int64_t n, float log_eps, void *cuda_stream);
+
 /* Evaluates the library's FP32 log (the one the event model uses) on n DEVICE
  * floats x_dev into y_dev on cuda_stream; for verification of the log. */
 int neurosim_debug_log(const float *x_dev, float *y_dev, int64_t n, void *cuda_stream);

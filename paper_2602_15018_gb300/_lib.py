@@ -33,7 +33,7 @@ EXPORTS = [
     "neurosim_interp_param_count", "neurosim_interp_create", "neurosim_interp_forward",
     "neurosim_interp_train_step", "neurosim_interp_gradients", "neurosim_interp_get_params",
     "neurosim_interp_set_params", "neurosim_interp_launches", "neurosim_interp_destroy",
-    "neurosim_event_f1",
+    "neurosim_event_f1", "neurosim_log_intensity",
 ]
 
 
@@ -175,6 +175,8 @@ def lib():
             L.neurosim_interp_launches.argtypes = [vp, C.POINTER(u64)]
             L.neurosim_interp_destroy.restype = None
             L.neurosim_interp_destroy.argtypes = [vp]
+            L.neurosim_log_intensity.restype = C.c_int
+            L.neurosim_log_intensity.argtypes = [vp, vp, i64, C.c_float, vp]
             L.neurosim_event_f1.restype = C.c_int
             L.neurosim_event_f1.argtypes = [vp, i64, vp, i64, i64, C.POINTER(i64), C.POINTER(C.c_double)]
             _lib = L

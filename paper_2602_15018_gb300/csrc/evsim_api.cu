@@ -711,6 +711,15 @@ const char* neurosim_last_error(void) { return g_err.c_str(); }
 
 int32_t neurosim_abi_version(void) { return NEUROSIM_EVSIM_ABI_VERSION; }
 
+int neurosim_log_intensity(const float* I_dev, float* L_dev, int64_t n, float log_eps, void* cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!I_dev || !L_dev))) return fail(NEUROSIM_E_INVALID, "bad arguments");
+    if (!(log_eps >= 1e-8f && log_eps <= 1.0f)) return fail(NEUROSIM_E_INVALID, "log_eps must be in [1e-8, 1]");
+    if (n == 0) return NEUROSIM_OK;
+    CUDA_TRY(launch_log_intensity(I_dev, L_dev, n, log_eps, static_cast<cudaStream_t>(cuda_stream)));
+    return NEUROSIM_OK;
+}
+
 int neurosim_debug_log(const float* x_dev, float* y_dev, int64_t n, void* cuda_stream)
 {
     if (n < 0 || (n > 0 && (!x_dev || !y_dev))) return fail(NEUROSIM_E_INVALID, "bad arguments");

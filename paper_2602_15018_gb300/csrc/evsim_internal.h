@@ -131,6 +131,9 @@ cudaError_t launch_threshold_maps(float* cpos, float* cneg, int64_t npix, float 
                                   float c_neg, float sigma, float c_min, uint64_t seed,
                                   cudaStream_t stream);
 
+// L = log(clamp(I, 0, 1e6) + eps) with the library's log (the event model's L).
+cudaError_t launch_log_intensity(const float* I, float* L, int64_t n, float eps, cudaStream_t stream);
+
 // Debug/verification: y = library log(x).
 cudaError_t launch_debug_log(const float* x, float* y, int64_t n, cudaStream_t stream);
 

@@ -472,6 +472,14 @@ __global__ void threshold_kernel(float* cpos, float* cneg, int64_t npix, float c
     }
 }
 
+// The event model's log intensity of raw frames: L = log(clamp(I, 0, 1e6) + eps)
+// with the library's log (the same function the emission kernel applies).
+__global__ void log_intensity_kernel(const float* I, float* L, int64_t n, float eps)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        L[i] = model_L(I[i], eps, 0);
+}
+
 __global__ void debug_log_kernel(const float* x, float* y, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -612,6 +620,16 @@ cudaError_t launch_threshold_maps(float* cpos, float* cneg, int64_t npix, float 
     if (blocks > 65535) blocks = 65535;
     threshold_kernel<<<(unsigned)blocks, threads, 0, stream>>>(cpos, cneg, npix, c_pos, c_neg, sigma,
                                                                 c_min, seed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_log_intensity(const float* I, float* L, int64_t n, float eps, cudaStream_t stream)
+{
+    const int threads = 256;
+    int64_t blocks = (n + threads - 1) / threads;
+    if (blocks > 65535) blocks = 65535;
+    if (blocks < 1) blocks = 1;
+    log_intensity_kernel<<<(unsigned)blocks, threads, 0, stream>>>(I, L, n, eps);
     return cudaGetLastError();
 }
 

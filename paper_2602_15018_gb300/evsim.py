@@ -212,6 +212,18 @@ def device_log(x: torch.Tensor) -> torch.Tensor:
     return y
 
 
+def log_intensity(frames: torch.Tensor, log_eps: float = 1e-3, out: torch.Tensor | None = None) -> torch.Tensor:
+    """The event model's log intensity of raw frames (library kernel): feeding
+    the result with input_is_log=True gives the events of the raw frames."""
+    if not (frames.is_cuda and frames.dtype == torch.float32 and frames.is_contiguous()):
+        raise ValueError("frames must be a contiguous float32 CUDA tensor")
+    if out is None:
+        out = torch.empty_like(frames)
+    check(lib().neurosim_log_intensity(C.c_void_p(frames.data_ptr()), C.c_void_p(out.data_ptr()), frames.numel(),
+                                       float(log_eps), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return out
+
+
 def _ptr_array(tensors):
     arr = (C.c_void_p * len(tensors))()
     for i, t in enumerate(tensors):
