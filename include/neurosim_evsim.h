@@ -366,6 +366,27 @@ int neurosim_interp_launches(neurosim_interp *h, uint64_t *launches);
 /* Frees the network (synchronises its stream first). */
 void neurosim_interp_destroy(neurosim_interp *h);
 
+/* Time surface (RL appendix of the paper, Observation Space paragraph:
+ * S(x, y, p) <- S(x, y, p) exp(-dt / tau) + 1 at every event of that cell).
+ * S_dev: DEVICE FP32 [2][height][width] (p = 0 OFF, 1 ON) holding the surface
+ * evaluated at *t_ref_us (HOST in/out; start with S = 0).  Moves S to
+ * t_query_us >= *t_ref_us and adds the DEVICE records events_dev[0..n), all
+ * with t <= t_query_us:  S <- S exp(-(t_q - t_ref)/tau) + sum exp(-(t_q - t_i)/tau)
+ * (the per-event recursion evaluated at t_q, up to FP32 rounding), then
+ * sets *t_ref_us = t_query_us.  Synchronises cuda_stream.  NEUROSIM_E_INVALID
+ * for an event outside the sensor or after t_query_us, NEUROSIM_E_TIME for
+ * t_query_us < *t_ref_us. */
+int neurosim_time_surface(float *S_dev, int32_t width, int32_t height, int64_t *t_ref_us,
+                          const uint64_t *events_dev, int64_t n, int64_t t_query_us, float tau_us,
+                          void *cuda_stream);
+
+/* Polarity event frames: counts_dev (DEVICE int32 [n_windows][2][height][width],
+ * accumulated into) gets one count per event of window
+ * (t - t_start_us) / window_us in [0, n_windows).  Synchronises cuda_stream. */
+int neurosim_event_frames(int32_t *counts_dev, int32_t width, int32_t height, const uint64_t *events_dev,
+                          int64_t n, int64_t t_start_us, int64_t window_us, int32_t n_windows,
+                          void *cuda_stream);
+
 /* Scores HOST event records `pred` against `ref` (any order): events match
  * one to one inside the same pixel and polarity, greedily in time order,
  * when their times differ by at most tol_us.  counts = {matched, n_pred,

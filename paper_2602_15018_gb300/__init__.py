@@ -3,8 +3,9 @@
 The compute path is the CUDA library libneurosim_evsim.so (C ABI in
 include/neurosim_evsim.h); this package only binds it.
 """
-from .evsim import EventSim, EventSimBatch, autotune, device_log, event_f1, log_intensity  # noqa: F401
+from .evsim import (EventSim, EventSimBatch, TimeSurface, autotune, device_log, event_f1,  # noqa: F401
+                    event_frames, log_intensity)
 from .interp import Interpolator  # noqa: F401
 from ._lib import NeurosimError, lib  # noqa: F401
 
-__all__ = ["EventSim", "EventSimBatch", "Interpolator", "autotune", "device_log", "event_f1", "log_intensity", "NeurosimError", "lib"]
+__all__ = ["EventSim", "EventSimBatch", "Interpolator", "autotune", "device_log", "event_f1", "log_intensity", "TimeSurface", "event_frames", "NeurosimError", "lib"]

@@ -33,7 +33,7 @@ EXPORTS = [
     "neurosim_interp_param_count", "neurosim_interp_create", "neurosim_interp_forward",
     "neurosim_interp_train_step", "neurosim_interp_gradients", "neurosim_interp_get_params",
     "neurosim_interp_set_params", "neurosim_interp_launches", "neurosim_interp_destroy",
-    "neurosim_event_f1", "neurosim_log_intensity",
+    "neurosim_event_f1", "neurosim_log_intensity", "neurosim_time_surface", "neurosim_event_frames",
 ]
 
 
@@ -175,6 +175,10 @@ def lib():
             L.neurosim_interp_launches.argtypes = [vp, C.POINTER(u64)]
             L.neurosim_interp_destroy.restype = None
             L.neurosim_interp_destroy.argtypes = [vp]
+            L.neurosim_time_surface.restype = C.c_int
+            L.neurosim_time_surface.argtypes = [vp, i32, i32, C.POINTER(i64), vp, i64, i64, C.c_float, vp]
+            L.neurosim_event_frames.restype = C.c_int
+            L.neurosim_event_frames.argtypes = [vp, i32, i32, vp, i64, i64, i64, i32, vp]
             L.neurosim_log_intensity.restype = C.c_int
             L.neurosim_log_intensity.argtypes = [vp, vp, i64, C.c_float, vp]
             L.neurosim_event_f1.restype = C.c_int

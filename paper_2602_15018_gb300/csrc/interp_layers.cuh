@@ -39,26 +39,56 @@ struct Act {            // BF16 NHWC view
 __device__ __forceinline__ uint4 ld16(const bf16* p) { return *reinterpret_cast<const uint4*>(p); }
 
 // ---- K-major A gathers (rows = output pixels of the GEMM) ---------------------------
+// Thread t always fills chunk column kc = t % 8 of rows t / 8 + 16 j: its
+// rows' pixel coordinates are decoded once per tile (prep) and each K tile
+// only adds the tap offset.  Channel counts are powers of two (cshift).
+__host__ __device__ constexpr int kRowsPerThread(int R) { return R / 16; }
+
 // conv 3x3, zero padding 1, stride s: row (n, yo, xo), k = tap * C + c reads
 // x(n, s yo + dy - 1, s xo + dx - 1, c).
 struct Conv3K {
     static constexpr bool MN = false;
     Act x;
     int C, Ho, Wo, s, M;
+    int cshift;
     template <int R>
-    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    struct Rows {
+        int nH[kRowsPerThread(R)];     // n * H of the input, or -1 for rows past M
+        int ys[kRowsPerThread(R)];     // s yo - 1
+        int xs[kRowsPerThread(R)];     // s xo - 1
+    };
+    template <int R>
+    __device__ __forceinline__ void prep(Rows<R>& rw, int r0, int tid) const
     {
-        for (int i = tid; i < R * (BK / 8); i += 128) {
-            const int r = i / (BK / 8), kc = i % (BK / 8);
-            const int m = r0 + r, k = k0 + kc * 8;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (m < M && kc * 8 < kn) {
-                const int hw = Ho * Wo;
-                const int n = m / hw, rem = m - n * hw, yo = rem / Wo, xo = rem - (rem / Wo) * Wo;
-                const int tap = k / C, c = k - tap * C;
-                const int yi = yo * s + tap / 3 - 1, xi = xo * s + tap % 3 - 1;
-                if ((unsigned)yi < (unsigned)x.H && (unsigned)xi < (unsigned)x.W) v = ld16(x.at(n, yi, xi, c));
+        const int hw = Ho * Wo;
+#pragma unroll
+        for (int j = 0; j < kRowsPerThread(R); ++j) {
+            const int m = r0 + (tid >> 3) + 16 * j;
+            if (m < M) {
+                const int n = m / hw, rem = m - n * hw, yo = rem / Wo, xo = rem - yo * Wo;
+                rw.nH[j] = n * x.H;
+                rw.ys[j] = yo * s - 1;
+                rw.xs[j] = xo * s - 1;
+            } else {
+                rw.nH[j] = -1;
+                rw.ys[j] = rw.xs[j] = 0;
             }
+        }
+    }
+    template <int R>
+    __device__ __forceinline__ void gather(unsigned char* tile, const Rows<R>& rw, int, int k0, int kn, int tid) const
+    {
+        const int kc = tid & 7, k = k0 + kc * 8;
+        const int tap = k >> cshift, c = k & (C - 1);
+        const int dy = tap / 3, dx = tap - 3 * dy;
+        const bool kok = kc * 8 < kn;
+#pragma unroll
+        for (int j = 0; j < kRowsPerThread(R); ++j) {
+            const int r = (tid >> 3) + 16 * j;
+            const int yi = rw.ys[j] + dy, xi = rw.xs[j] + dx;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (kok && rw.nH[j] >= 0 && (unsigned)yi < (unsigned)x.H && (unsigned)xi < (unsigned)x.W)
+                v = ld16(x.p + ((size_t)(rw.nH[j] + yi) * x.W + xi) * x.stride + x.off + c);
             st_chunk(tile, kmajor_chunk(r, kc * 8), v);
         }
     }
@@ -71,22 +101,47 @@ struct Conv3TK {
     static constexpr bool MN = false;
     Act g;              // gradient of the conv's output (size Ho x Wo)
     int C, Hi, Wi, s, M;
+    int cshift;
     template <int R>
-    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    struct Rows {
+        int nH[kRowsPerThread(R)];     // n * Ho, or -1 for rows past M
+        int y1[kRowsPerThread(R)];     // y + 1
+        int x1[kRowsPerThread(R)];     // x + 1
+    };
+    template <int R>
+    __device__ __forceinline__ void prep(Rows<R>& rw, int r0, int tid) const
     {
-        for (int i = tid; i < R * (BK / 8); i += 128) {
-            const int r = i / (BK / 8), kc = i % (BK / 8);
-            const int m = r0 + r, k = k0 + kc * 8;
+        const int hw = Hi * Wi;
+#pragma unroll
+        for (int j = 0; j < kRowsPerThread(R); ++j) {
+            const int m = r0 + (tid >> 3) + 16 * j;
+            if (m < M) {
+                const int n = m / hw, rem = m - n * hw, y = rem / Wi, xx = rem - y * Wi;
+                rw.nH[j] = n * g.H;
+                rw.y1[j] = y + 1;
+                rw.x1[j] = xx + 1;
+            } else {
+                rw.nH[j] = -1;
+                rw.y1[j] = rw.x1[j] = 0;
+            }
+        }
+    }
+    template <int R>
+    __device__ __forceinline__ void gather(unsigned char* tile, const Rows<R>& rw, int, int k0, int kn, int tid) const
+    {
+        const int kc = tid & 7, k = k0 + kc * 8;
+        const int tap = k >> cshift, c = k & (C - 1);
+        const int dy = tap / 3, dx = tap - 3 * dy;
+        const bool kok = kc * 8 < kn;
+        const int smask = s - 1, sshift = s == 2 ? 1 : 0;
+#pragma unroll
+        for (int j = 0; j < kRowsPerThread(R); ++j) {
+            const int r = (tid >> 3) + 16 * j;
+            const int ty = rw.y1[j] - dy, tx = rw.x1[j] - dx;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (m < M && kc * 8 < kn) {
-                const int hw = Hi * Wi;
-                const int n = m / hw, rem = m - n * hw, y = rem / Wi, xx = rem - (rem / Wi) * Wi;
-                const int tap = k / C, c = k - tap * C;
-                const int ty = y + 1 - tap / 3, tx = xx + 1 - tap % 3;
-                if (ty >= 0 && tx >= 0 && ty % s == 0 && tx % s == 0) {
-                    const int yo = ty / s, xo = tx / s;
-                    if (yo < g.H && xo < g.W) v = ld16(g.at(n, yo, xo, c));
-                }
+            if (kok && rw.nH[j] >= 0 && ty >= 0 && tx >= 0 && !(ty & smask) && !(tx & smask)) {
+                const int yo = ty >> sshift, xo = tx >> sshift;
+                if (yo < g.H && xo < g.W) v = ld16(g.p + ((size_t)(rw.nH[j] + yo) * g.W + xo) * g.stride + g.off + c);
             }
             st_chunk(tile, kmajor_chunk(r, kc * 8), v);
         }
@@ -98,14 +153,17 @@ struct PixK {
     static constexpr bool MN = false;
     Act x;
     int M;
+    UGEMM_NO_ROWS
     template <int R>
-    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    __device__ __forceinline__ void gather(unsigned char* tile, const Rows<R>&, int r0, int k0, int kn, int tid) const
     {
-        for (int i = tid; i < R * (BK / 8); i += 128) {
-            const int r = i / (BK / 8), kc = i % (BK / 8);
-            const int m = r0 + r;
+        const int kc = tid & 7;
+        const bool kok = kc * 8 < kn;
+#pragma unroll
+        for (int j = 0; j < kRowsPerThread(R); ++j) {
+            const int r = (tid >> 3) + 16 * j, m = r0 + r;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (m < M && kc * 8 < kn) v = ld16(x.p + (size_t)m * x.stride + x.off + k0 + kc * 8);
+            if (kok && m < M) v = ld16(x.p + (size_t)m * x.stride + x.off + k0 + kc * 8);
             st_chunk(tile, kmajor_chunk(r, kc * 8), v);
         }
     }
@@ -117,19 +175,38 @@ struct S2DK {
     static constexpr bool MN = false;
     Act g;              // full-size gradient
     int C, Hl, Wl, M;
+    int cshift;
     template <int R>
-    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    struct Rows {
+        int pix[kRowsPerThread(R)];    // full-size pixel index of (n, 2y, 2x), or -1 past M
+    };
+    template <int R>
+    __device__ __forceinline__ void prep(Rows<R>& rw, int r0, int tid) const
     {
-        for (int i = tid; i < R * (BK / 8); i += 128) {
-            const int r = i / (BK / 8), kc = i % (BK / 8);
-            const int m = r0 + r, k = k0 + kc * 8;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (m < M && kc * 8 < kn) {
-                const int hw = Hl * Wl;
-                const int n = m / hw, rem = m - n * hw, y = rem / Wl, xx = rem - (rem / Wl) * Wl;
-                const int ab = k / C, c = k - ab * C;
-                v = ld16(g.at(n, 2 * y + (ab >> 1), 2 * xx + (ab & 1), c));
+        const int hw = Hl * Wl;
+#pragma unroll
+        for (int j = 0; j < kRowsPerThread(R); ++j) {
+            const int m = r0 + (tid >> 3) + 16 * j;
+            if (m < M) {
+                const int n = m / hw, rem = m - n * hw, y = rem / Wl, xx = rem - y * Wl;
+                rw.pix[j] = (n * g.H + 2 * y) * g.W + 2 * xx;
+            } else {
+                rw.pix[j] = -1;
             }
+        }
+    }
+    template <int R>
+    __device__ __forceinline__ void gather(unsigned char* tile, const Rows<R>& rw, int, int k0, int kn, int tid) const
+    {
+        const int kc = tid & 7, k = k0 + kc * 8;
+        const int ab = k >> cshift, c = k & (C - 1);
+        const int dpix = (ab >> 1) * g.W + (ab & 1);
+        const bool kok = kc * 8 < kn;
+#pragma unroll
+        for (int j = 0; j < kRowsPerThread(R); ++j) {
+            const int r = (tid >> 3) + 16 * j;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (kok && rw.pix[j] >= 0) v = ld16(g.p + (size_t)(rw.pix[j] + dpix) * g.stride + g.off + c);
             st_chunk(tile, kmajor_chunk(r, kc * 8), v);
         }
     }
@@ -139,10 +216,11 @@ struct S2DK {
 // rows (tap, c) of a conv 3x3 stride s at output pixel p: x(n, s yo + dy - 1, s xo + dx - 1, c).
 struct Im2colMN {
     static constexpr bool MN = true;
+    UGEMM_NO_ROWS
     Act x;
     int C, Ho, Wo, s, rows, P;
     template <int R>
-    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    __device__ __forceinline__ void gather(unsigned char* tile, const Rows<R>&, int r0, int k0, int kn, int tid) const
     {
         for (int i = tid; i < (R / 8) * BK; i += 128) {
             const int k = i / (R / 8), rc = i % (R / 8);
@@ -163,10 +241,11 @@ struct Im2colMN {
 // rows = channels at pixel p.
 struct PixMN {
     static constexpr bool MN = true;
+    UGEMM_NO_ROWS
     Act x;
     int rows, P;
     template <int R>
-    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    __device__ __forceinline__ void gather(unsigned char* tile, const Rows<R>&, int r0, int k0, int kn, int tid) const
     {
         for (int i = tid; i < (R / 8) * BK; i += 128) {
             const int k = i / (R / 8), rc = i % (R / 8);
@@ -181,10 +260,11 @@ struct PixMN {
 // rows (2a + b, c) at low-size pixel p: g(n, 2y + a, 2x + b, c).
 struct S2DMN {
     static constexpr bool MN = true;
+    UGEMM_NO_ROWS
     Act g;
     int C, Hl, Wl, rows, P;
     template <int R>
-    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    __device__ __forceinline__ void gather(unsigned char* tile, const Rows<R>&, int r0, int k0, int kn, int tid) const
     {
         for (int i = tid; i < (R / 8) * BK; i += 128) {
             const int k = i / (R / 8), rc = i % (R / 8);

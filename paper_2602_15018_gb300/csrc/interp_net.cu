@@ -325,6 +325,16 @@ struct Shape {
 
 Act act(const bf16* p, int N, int H, int W, int stride, int off) { return Act{p, N, H, W, stride, off}; }
 
+int log2i(int c)
+{
+    int k = 0;
+    while ((1 << k) < c) ++k;
+    return k;
+}
+Conv3K conv3k(Act x, int C, int Ho, int Wo, int s, int M) { return Conv3K{x, C, Ho, Wo, s, M, log2i(C)}; }
+Conv3TK conv3tk(Act g, int C, int Hi, int Wi, int s, int M) { return Conv3TK{g, C, Hi, Wi, s, M, log2i(C)}; }
+S2DK s2dk(Act g, int C, int Hl, int Wl, int M) { return S2DK{g, C, Hl, Wl, M, log2i(C)}; }
+
 const float* bias_of(const neurosim_interp* h, int l) { return h->params + h->lay.b_off[l]; }
 
 int pack_all(neurosim_interp* h)
@@ -347,28 +357,28 @@ int forward(neurosim_interp* h, const Shape& s, const float* L0, const float* L4
     h->launches += 1;
     ICUDA(cudaGetLastError());
     // e1 -> cat1[:, 32:64]
-    ICUDA(gemm(h, Conv3K{act(h->x0, N, H, W, 8, 0), 8, H, W, 1, s.P}, ugemm::DenseK{h->wf[0], 32, 72},
+    ICUDA(gemm(h, conv3k(act(h->x0, N, H, W, 8, 0), 8, H, W, 1, s.P), ugemm::DenseK{h->wf[0], 32, 72},
                EpiAct{h->cat1, 64, 32, bias_of(h, 0), 1}, s.P, 32, 72, false));
     // e2 -> cat2[:, 64:128]
-    ICUDA(gemm(h, Conv3K{act(h->cat1, N, H, W, 64, 32), 32, H2, W2, 2, s.P2}, ugemm::DenseK{h->wf[1], 64, 288},
+    ICUDA(gemm(h, conv3k(act(h->cat1, N, H, W, 64, 32), 32, H2, W2, 2, s.P2), ugemm::DenseK{h->wf[1], 64, 288},
                EpiAct{h->cat2, 128, 64, bias_of(h, 1), 1}, s.P2, 64, 288, false));
     // e3
-    ICUDA(gemm(h, Conv3K{act(h->cat2, N, H2, W2, 128, 64), 64, H4, W4, 2, s.P4}, ugemm::DenseK{h->wf[2], 128, 576},
+    ICUDA(gemm(h, conv3k(act(h->cat2, N, H2, W2, 128, 64), 64, H4, W4, 2, s.P4), ugemm::DenseK{h->wf[2], 128, 576},
                EpiAct{h->e3, 128, 0, bias_of(h, 2), 1}, s.P4, 128, 576, false));
     // e4
-    ICUDA(gemm(h, Conv3K{act(h->e3, N, H4, W4, 128, 0), 128, H4, W4, 1, s.P4}, ugemm::DenseK{h->wf[3], 128, 1152},
+    ICUDA(gemm(h, conv3k(act(h->e3, N, H4, W4, 128, 0), 128, H4, W4, 1, s.P4), ugemm::DenseK{h->wf[3], 128, 1152},
                EpiAct{h->e4, 128, 0, bias_of(h, 3), 1}, s.P4, 128, 1152, false));
     // u1 -> cat2[:, 0:64]
     ICUDA(gemm(h, PixK{act(h->e4, N, H4, W4, 128, 0), s.P4}, ugemm::DenseK{h->wf[4], 256, 128},
                EpiConvT{h->cat2, 128, 0, bias_of(h, 4), 64, H4, W4}, s.P4, 256, 128, false));
     // d1
-    ICUDA(gemm(h, Conv3K{act(h->cat2, N, H2, W2, 128, 0), 128, H2, W2, 1, s.P2}, ugemm::DenseK{h->wf[5], 64, 1152},
+    ICUDA(gemm(h, conv3k(act(h->cat2, N, H2, W2, 128, 0), 128, H2, W2, 1, s.P2), ugemm::DenseK{h->wf[5], 64, 1152},
                EpiAct{h->d1, 64, 0, bias_of(h, 5), 1}, s.P2, 64, 1152, false));
     // u2 -> cat1[:, 0:32]
     ICUDA(gemm(h, PixK{act(h->d1, N, H2, W2, 64, 0), s.P2}, ugemm::DenseK{h->wf[6], 128, 64},
                EpiConvT{h->cat1, 64, 0, bias_of(h, 6), 32, H2, W2}, s.P2, 128, 64, false));
     // d2
-    ICUDA(gemm(h, Conv3K{act(h->cat1, N, H, W, 64, 0), 64, H, W, 1, s.P}, ugemm::DenseK{h->wf[7], 32, 576},
+    ICUDA(gemm(h, conv3k(act(h->cat1, N, H, W, 64, 0), 64, H, W, 1, s.P), ugemm::DenseK{h->wf[7], 32, 576},
                EpiAct{h->d2, 32, 0, bias_of(h, 7), 1}, s.P, 32, 576, false));
     // frames
     ICUDA(gemm(h, PixK{act(h->d2, N, H, W, 32, 0), s.P}, ugemm::DenseK{h->wf[8], 16, 32},
@@ -405,44 +415,44 @@ int backward(neurosim_interp* h, const Shape& s)
     ICUDA(gemm(h, Im2colMN{act(h->cat1, N, H, W, 64, 0), 64, H, W, 1, 576, s.P}, PixMN{act(h->gd2, N, H, W, 32, 0), 32, s.P},
                EpiDW{G + L.w_off[7], 32}, 576, 32, s.P, true));
     if ((rc = bias_grad(h, h->gd2, s.P, 32, 0, 32, 7))) return rc;
-    ICUDA(gemm(h, Conv3TK{act(h->gd2, N, H, W, 32, 0), 32, H, W, 1, s.P}, ugemm::DenseK{h->wb[7], 64, 288},
+    ICUDA(gemm(h, conv3tk(act(h->gd2, N, H, W, 32, 0), 32, H, W, 1, s.P), ugemm::DenseK{h->wb[7], 64, 288},
                EpiGrad{h->gcat1, 64, 0, h->cat1, 64, 0, 32, 0}, s.P, 64, 288, false));
     // ---- convT2 (d1 -> u2): W7, b7, d(d1)
     ICUDA(gemm(h, PixMN{act(h->d1, N, H2, W2, 64, 0), 64, s.P2}, S2DMN{act(h->gcat1, N, H, W, 64, 0), 32, H2, W2, 128, s.P2},
                EpiDW{G + L.w_off[6], 128}, 64, 128, s.P2, true));
     if ((rc = bias_grad(h, h->gcat1, s.P, 64, 0, 32, 6))) return rc;
-    ICUDA(gemm(h, S2DK{act(h->gcat1, N, H, W, 64, 0), 32, H2, W2, s.P2}, ugemm::DenseK{h->wb[6], 64, 128},
+    ICUDA(gemm(h, s2dk(act(h->gcat1, N, H, W, 64, 0), 32, H2, W2, s.P2), ugemm::DenseK{h->wb[6], 64, 128},
                EpiGrad{h->gd1, 64, 0, h->d1, 64, 0, 0, 0}, s.P2, 64, 128, false));
     // ---- conv6 (cat2 -> d1): W6, b6, d(cat2) (u1 linear, e2 masked)
     ICUDA(gemm(h, Im2colMN{act(h->cat2, N, H2, W2, 128, 0), 128, H2, W2, 1, 1152, s.P2},
                PixMN{act(h->gd1, N, H2, W2, 64, 0), 64, s.P2}, EpiDW{G + L.w_off[5], 64}, 1152, 64, s.P2, true));
     if ((rc = bias_grad(h, h->gd1, s.P2, 64, 0, 64, 5))) return rc;
-    ICUDA(gemm(h, Conv3TK{act(h->gd1, N, H2, W2, 64, 0), 64, H2, W2, 1, s.P2}, ugemm::DenseK{h->wb[5], 128, 576},
+    ICUDA(gemm(h, conv3tk(act(h->gd1, N, H2, W2, 64, 0), 64, H2, W2, 1, s.P2), ugemm::DenseK{h->wb[5], 128, 576},
                EpiGrad{h->gcat2, 128, 0, h->cat2, 128, 0, 64, 0}, s.P2, 128, 576, false));
     // ---- convT1 (e4 -> u1): W5, b5, d(e4)
     ICUDA(gemm(h, PixMN{act(h->e4, N, H4, W4, 128, 0), 128, s.P4},
                S2DMN{act(h->gcat2, N, H2, W2, 128, 0), 64, H4, W4, 256, s.P4}, EpiDW{G + L.w_off[4], 256}, 128, 256,
                s.P4, true));
     if ((rc = bias_grad(h, h->gcat2, s.P2, 128, 0, 64, 4))) return rc;
-    ICUDA(gemm(h, S2DK{act(h->gcat2, N, H2, W2, 128, 0), 64, H4, W4, s.P4}, ugemm::DenseK{h->wb[4], 128, 256},
+    ICUDA(gemm(h, s2dk(act(h->gcat2, N, H2, W2, 128, 0), 64, H4, W4, s.P4), ugemm::DenseK{h->wb[4], 128, 256},
                EpiGrad{h->ge4, 128, 0, h->e4, 128, 0, 0, 0}, s.P4, 128, 256, false));
     // ---- conv4 (e3 -> e4): W4, b4, d(e3)
     ICUDA(gemm(h, Im2colMN{act(h->e3, N, H4, W4, 128, 0), 128, H4, W4, 1, 1152, s.P4},
                PixMN{act(h->ge4, N, H4, W4, 128, 0), 128, s.P4}, EpiDW{G + L.w_off[3], 128}, 1152, 128, s.P4, true));
     if ((rc = bias_grad(h, h->ge4, s.P4, 128, 0, 128, 3))) return rc;
-    ICUDA(gemm(h, Conv3TK{act(h->ge4, N, H4, W4, 128, 0), 128, H4, W4, 1, s.P4}, ugemm::DenseK{h->wb[3], 128, 1152},
+    ICUDA(gemm(h, conv3tk(act(h->ge4, N, H4, W4, 128, 0), 128, H4, W4, 1, s.P4), ugemm::DenseK{h->wb[3], 128, 1152},
                EpiGrad{h->ge3, 128, 0, h->e3, 128, 0, 0, 0}, s.P4, 128, 1152, false));
     // ---- conv3 (e2 -> e3, stride 2): W3, b3, d(e2) added into d(cat2)[:, 64:128]
     ICUDA(gemm(h, Im2colMN{act(h->cat2, N, H2, W2, 128, 64), 64, H4, W4, 2, 576, s.P4},
                PixMN{act(h->ge3, N, H4, W4, 128, 0), 128, s.P4}, EpiDW{G + L.w_off[2], 128}, 576, 128, s.P4, true));
     if ((rc = bias_grad(h, h->ge3, s.P4, 128, 0, 128, 2))) return rc;
-    ICUDA(gemm(h, Conv3TK{act(h->ge3, N, H4, W4, 128, 0), 128, H2, W2, 2, s.P2}, ugemm::DenseK{h->wb[2], 64, 1152},
+    ICUDA(gemm(h, conv3tk(act(h->ge3, N, H4, W4, 128, 0), 128, H2, W2, 2, s.P2), ugemm::DenseK{h->wb[2], 64, 1152},
                EpiGrad{h->gcat2, 128, 64, h->cat2, 128, 64, 0, 1}, s.P2, 64, 1152, false));
     // ---- conv2 (e1 -> e2, stride 2): W2, b2, d(e1) added into d(cat1)[:, 32:64]
     ICUDA(gemm(h, Im2colMN{act(h->cat1, N, H, W, 64, 32), 32, H2, W2, 2, 288, s.P2},
                PixMN{act(h->gcat2, N, H2, W2, 128, 64), 64, s.P2}, EpiDW{G + L.w_off[1], 64}, 288, 64, s.P2, true));
     if ((rc = bias_grad(h, h->gcat2, s.P2, 128, 64, 64, 1))) return rc;
-    ICUDA(gemm(h, Conv3TK{act(h->gcat2, N, H2, W2, 128, 64), 64, H, W, 2, s.P}, ugemm::DenseK{h->wb[1], 32, 576},
+    ICUDA(gemm(h, conv3tk(act(h->gcat2, N, H2, W2, 128, 64), 64, H, W, 2, s.P), ugemm::DenseK{h->wb[1], 32, 576},
                EpiGrad{h->gcat1, 64, 32, h->cat1, 64, 32, 0, 1}, s.P, 32, 576, false));
     // ---- conv1 (x -> e1): W1, b1
     ICUDA(gemm(h, Im2colMN{act(h->x0, N, H, W, 8, 0), 8, H, W, 1, 72, s.P}, PixMN{act(h->gcat1, N, H, W, 64, 32), 32, s.P},

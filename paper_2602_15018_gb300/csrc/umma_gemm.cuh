@@ -107,6 +107,12 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
     const uint32_t tmem = *tslot;
     constexpr uint32_t idesc = umma::idesc_bf16_f32(BM, BN, AG::MN, BG::MN);
 
+    // per-thread row coordinates of this tile, computed once
+    typename AG::template Rows<BM> ra;
+    typename BG::template Rows<BN> rb;
+    g.a.template prep<BM>(ra, m0, tid);
+    g.b.template prep<BN>(rb, 0, tid);
+
     bool ok = true;
     for (int kt = 0; kt < n_kt; ++kt) {
         const int st = kt & 1;
@@ -118,8 +124,8 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
             ok = false;
             break;
         }
-        g.a.template gather<BM>(sA + st * A_BYTES, m0, kb + kt * BK, min(BK, ke - kb - kt * BK), tid);
-        g.b.template gather<BN>(sB + st * B_BYTES, 0, kb + kt * BK, min(BK, ke - kb - kt * BK), tid);
+        g.a.template gather<BM>(sA + st * A_BYTES, ra, m0, kb + kt * BK, min(BK, ke - kb - kt * BK), tid);
+        g.b.template gather<BN>(sB + st * B_BYTES, rb, 0, kb + kt * BK, min(BK, ke - kb - kt * BK), tid);
         umma::fence_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -164,13 +170,21 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
 }
 
 // ---- dense operands (row-major, leading dimension ld) ------------------------------
+// Gathers without per-row state declare an empty row cache.
+#define UGEMM_NO_ROWS                                                      \
+    template <int R>                                                       \
+    struct Rows {};                                                        \
+    template <int R>                                                       \
+    __device__ __forceinline__ void prep(Rows<R>&, int, int) const {}
+
 // K-major: row r of the operand is src[r * ld + k].
 struct DenseK {
     static constexpr bool MN = false;
+    UGEMM_NO_ROWS
     const __nv_bfloat16* src;
     int rows, ld;
     template <int R>
-    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    __device__ __forceinline__ void gather(unsigned char* tile, const Rows<R>&, int r0, int k0, int kn, int tid) const
     {
         // R rows x BK: chunks (r, kc)
         for (int i = tid; i < R * (BK / 8); i += 128) {
@@ -186,10 +200,11 @@ struct DenseK {
 // MN-major: element (r, k) of the operand is src[k * ld + r].
 struct DenseMN {
     static constexpr bool MN = true;
+    UGEMM_NO_ROWS
     const __nv_bfloat16* src;
     int rows, ld;
     template <int R>
-    __device__ __forceinline__ void gather(unsigned char* tile, int r0, int k0, int kn, int tid) const
+    __device__ __forceinline__ void gather(unsigned char* tile, const Rows<R>&, int r0, int k0, int kn, int tid) const
     {
         // R rows x BK: chunks (rc, k) of 8 rows
         for (int i = tid; i < (R / 8) * BK; i += 128) {

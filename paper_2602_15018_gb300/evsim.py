@@ -410,3 +410,36 @@ def event_f1(pred, ref, tol_us: int = 1000) -> dict:
     return dict(matched=int(counts[0]), n_pred=int(counts[1]), n_ref=int(counts[2]),
                 count_abs_err=int(counts[3]), precision=float(scores[0]), recall=float(scores[1]),
                 f1=float(scores[2]), count_err=float(scores[3]))
+
+
+class TimeSurface:
+    """Time surface of one sensor on the device (C ABI neurosim_time_surface):
+    S[2, H, W] evaluated at `t_ref`; update(events, t_query) decays it to
+    t_query and adds the events (int64 CUDA tensor of records, t <= t_query)."""
+
+    def __init__(self, width: int, height: int, tau_us: float = 10_000.0, device="cuda"):
+        self.W, self.H, self.tau = int(width), int(height), float(tau_us)
+        self.S = torch.zeros((2, self.H, self.W), dtype=torch.float32, device=device)
+        self.t_ref = 0
+
+    def update(self, events: torch.Tensor, t_query_us: int) -> torch.Tensor:
+        if events.numel() and not (events.is_cuda and events.dtype == torch.int64 and events.is_contiguous()):
+            raise ValueError("events must be a contiguous int64 CUDA tensor of records")
+        t = C.c_int64(self.t_ref)
+        check(lib().neurosim_time_surface(C.c_void_p(self.S.data_ptr()), self.W, self.H, C.byref(t),
+                                          C.c_void_p(events.data_ptr() if events.numel() else 0), events.numel(),
+                                          int(t_query_us), self.tau,
+                                          C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        self.t_ref = int(t.value)
+        return self.S
+
+
+def event_frames(events: torch.Tensor, width: int, height: int, t_start_us: int, window_us: int,
+                 n_windows: int) -> torch.Tensor:
+    """Per-window polarity counts int32 [n_windows, 2, H, W] of records (int64 CUDA tensor)."""
+    out = torch.zeros((n_windows, 2, height, width), dtype=torch.int32, device=events.device)
+    check(lib().neurosim_event_frames(C.c_void_p(out.data_ptr()), int(width), int(height),
+                                      C.c_void_p(events.data_ptr() if events.numel() else 0), events.numel(),
+                                      int(t_start_us), int(window_us), int(n_windows),
+                                      C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return out
