@@ -509,7 +509,7 @@ def run_learned(args):
     npix = W * H
     net = Interpolator(8, H, W, seed=args.seed)
     t_tr = time.time()
-    losses = learned.train(net, args.train_steps, batch=16, size=256, lr=2e-3, speed=(150.0, 600.0),
+    losses = learned.train(net, args.train_steps, batch=16, size=256, lr=3e-3, speed=(150.0, 600.0),
                            seed=10000 + 7919 * rank, report=max(1, args.train_steps // 8))
     torch.cuda.synchronize()
     train_s = time.time() - t_tr
@@ -695,7 +695,7 @@ def main():
     ap.add_argument("--cpu-frames", type=int, default=480)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--keys", type=int, default=126, help="learned workload: keyframes per clip")
-    ap.add_argument("--train-steps", type=int, default=1500, help="learned workload: training steps")
+    ap.add_argument("--train-steps", type=int, default=4000, help="learned workload: training steps")
     ap.add_argument("--frames", type=int, default=0,
                     help="frames per step (default: the workload's); for small profiling cases")
     args = ap.parse_args()

@@ -8,6 +8,7 @@
 #include "../../include/neurosim_evsim.h"
 #include "evsim_internal.h"
 #include "umma_gemm.cuh"
+#include "umma_tma.cuh"
 
 namespace {
 
@@ -45,13 +46,43 @@ int dispatch(int mode, int M, int N, int K, const __nv_bfloat16* A, const __nv_b
     return run<BN>(am, bm, M, N, K, C, err, st);
 }
 
+// Row-major FP32 output for the TMA kernel.
+struct StoreRow {
+    float* dst;
+    int ld;
+    __device__ __forceinline__ void store(int r, int c, const float (&v)[8], int) const
+    {
+        float4* p = reinterpret_cast<float4*>(dst + (size_t)r * ld + c);
+        p[0] = make_float4(v[0], v[1], v[2], v[3]);
+        p[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+};
+
+template <int BN>
+int run_tma(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, unsigned int* err,
+            cudaStream_t st)
+{
+    utma::TmaArgs<utma::DenseA, StoreRow> g;
+    if (!utma::encode_kmajor(&g.ta, A, M, K, utma::BM) || !utma::encode_kmajor(&g.tb, B, N, K, BN))
+        return NEUROSIM_E_CUDA;
+    g.a = utma::DenseA{M, K};
+    g.ep = StoreRow{C, N};
+    g.N = N;
+    g.err = err;
+    g.limit_ns = 2000000000ull;
+    if (utma::launch_tma_gemm<BN>(g, (M + utma::BM - 1) / utma::BM, st) != cudaSuccess) return NEUROSIM_E_CUDA;
+    return NEUROSIM_OK;
+}
+
 }  // namespace
 
 extern "C" int neurosim_debug_umma_gemm(int32_t mode, int32_t M, int32_t N, int32_t K, const void* A,
                                         const void* B, float* C, void* cuda_stream)
 {
     if (!A || !B || !C) return nsim::report_error(NEUROSIM_E_INVALID, "NULL operand");
-    if (mode < 0 || mode > 3) return nsim::report_error(NEUROSIM_E_INVALID, "mode must be in [0, 3]");
+    if (mode < 0 || mode > 4) return nsim::report_error(NEUROSIM_E_INVALID, "mode must be in [0, 4]");
+    if (mode == 4 && (reinterpret_cast<uintptr_t>(A) & 15u || reinterpret_cast<uintptr_t>(B) & 15u))
+        return nsim::report_error(NEUROSIM_E_INVALID, "TMA operands must be 16-byte aligned");
     if (M < 1 || N < 16 || N > 256 || N % 16 || K < 8 || K % 8 || ((mode & 1) && M % 8) || ((mode & 2) && N % 8))
         return nsim::report_error(NEUROSIM_E_INVALID,
                                   "need M >= 1, 16 <= N <= 256 with N % 16 == 0, K % 8 == 0, MN-major rows % 8 == 0");
@@ -62,7 +93,9 @@ extern "C" int neurosim_debug_umma_gemm(int32_t mode, int32_t M, int32_t N, int3
         return nsim::report_error(NEUROSIM_E_CUDA, "cannot allocate the error word");
     const auto* a = static_cast<const __nv_bfloat16*>(A);
     const auto* b = static_cast<const __nv_bfloat16*>(B);
-    int rc = N <= 64 ? dispatch<64>(mode, M, N, K, a, b, C, err, st) : dispatch<256>(mode, M, N, K, a, b, C, err, st);
+    int rc = mode == 4 ? (N <= 64 ? run_tma<64>(M, N, K, a, b, C, err, st) : run_tma<256>(M, N, K, a, b, C, err, st))
+             : N <= 64 ? dispatch<64>(mode, M, N, K, a, b, C, err, st)
+                       : dispatch<256>(mode, M, N, K, a, b, C, err, st);
     unsigned int h = 0;
     if (cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)

@@ -33,6 +33,7 @@
 #include "../../include/neurosim_evsim.h"
 #include "evsim_internal.h"
 #include "interp_layers.cuh"
+#include "umma_tma.cuh"
 
 using namespace interp;
 
@@ -318,6 +319,58 @@ cudaError_t gemm(neurosim_interp* h, const AG& a, const BG& b, const EP& ep, int
     return gemm_bn<256>(h, a, b, ep, M, N, K, splits, kps);
 }
 
+// ---- TMA path for 3x3 stride-1 convolutions over >= 64 channels ---------------------
+// Output tile TW x TH pixels (TW * TH = 128) chosen to waste the fewest rows.
+void pick_tile(int W, int H, int* TW, int* TH)
+{
+    int best = -1;
+    for (int tw = 128; tw >= 8; tw >>= 1) {
+        const int th = 128 / tw;
+        const long long tiles = (long long)((W + tw - 1) / tw) * ((H + th - 1) / th);
+        const long long waste = tiles * 128 - (long long)W * H;
+        if (best < 0 || waste < best) {
+            best = (int)waste;
+            *TW = tw;
+            *TH = th;
+        }
+    }
+}
+
+template <int BN, class EP>
+cudaError_t conv_tma_bn(neurosim_interp* h, const bf16* buf, int cstride, int off, int C, int flip, int N, int H,
+                        int W, const bf16* wpacked, int n_out, const EP& ep)
+{
+    int TW = 128, TH = 1;
+    pick_tile(W, H, &TW, &TH);
+    utma::TmaArgs<utma::ConvTapA, EP> g;
+    const cuuint64_t dims[4] = {(cuuint64_t)cstride, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t strides[3] = {(cuuint64_t)cstride * 2u, (cuuint64_t)W * cstride * 2u,
+                                   (cuuint64_t)H * W * cstride * 2u};
+    const cuuint32_t box[4] = {(cuuint32_t)utma::BK, (cuuint32_t)TW, (cuuint32_t)TH, 1u};
+    if (!utma::encode_tiled(&g.ta, 4, buf, dims, strides, box) ||
+        !utma::encode_kmajor(&g.tb, wpacked, n_out, 9 * C, BN))
+        return cudaErrorInvalidValue;
+    const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH;
+    g.a = utma::ConvTapA{C, off, flip, W, H, N, TW, TH, tx, ty};
+    g.ep = ep;
+    g.N = n_out;
+    g.err = h->err;
+    g.limit_ns = 2000000000ull;
+    h->launches += 1;
+    return utma::launch_tma_gemm<BN>(g, N * tx * ty, h->stream);
+}
+
+// out = conv3x3 (stride 1) of the view [off, off + C) of `buf`; flip = 1 for
+// the data gradient (taps mirrored).  C must be a multiple of 64.
+template <class EP>
+cudaError_t conv_tma(neurosim_interp* h, const bf16* buf, int cstride, int off, int C, int flip, int N, int H, int W,
+                     const bf16* wpacked, int n_out, const EP& ep)
+{
+    if (n_out <= 32) return conv_tma_bn<32>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+    if (n_out <= 64) return conv_tma_bn<64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+    return conv_tma_bn<128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+}
+
 struct Shape {
     int N, H, W;        // batch and full size
     int P, P2, P4;      // pixels at full, half and quarter size
@@ -366,20 +419,17 @@ int forward(neurosim_interp* h, const Shape& s, const float* L0, const float* L4
     ICUDA(gemm(h, conv3k(act(h->cat2, N, H2, W2, 128, 64), 64, H4, W4, 2, s.P4), ugemm::DenseK{h->wf[2], 128, 576},
                EpiAct{h->e3, 128, 0, bias_of(h, 2), 1}, s.P4, 128, 576, false));
     // e4
-    ICUDA(gemm(h, conv3k(act(h->e3, N, H4, W4, 128, 0), 128, H4, W4, 1, s.P4), ugemm::DenseK{h->wf[3], 128, 1152},
-               EpiAct{h->e4, 128, 0, bias_of(h, 3), 1}, s.P4, 128, 1152, false));
+    ICUDA(conv_tma(h, h->e3, 128, 0, 128, 0, N, H4, W4, h->wf[3], 128, EpiAct{h->e4, 128, 0, bias_of(h, 3), 1}));
     // u1 -> cat2[:, 0:64]
     ICUDA(gemm(h, PixK{act(h->e4, N, H4, W4, 128, 0), s.P4}, ugemm::DenseK{h->wf[4], 256, 128},
                EpiConvT{h->cat2, 128, 0, bias_of(h, 4), 64, H4, W4}, s.P4, 256, 128, false));
     // d1
-    ICUDA(gemm(h, conv3k(act(h->cat2, N, H2, W2, 128, 0), 128, H2, W2, 1, s.P2), ugemm::DenseK{h->wf[5], 64, 1152},
-               EpiAct{h->d1, 64, 0, bias_of(h, 5), 1}, s.P2, 64, 1152, false));
+    ICUDA(conv_tma(h, h->cat2, 128, 0, 128, 0, N, H2, W2, h->wf[5], 64, EpiAct{h->d1, 64, 0, bias_of(h, 5), 1}));
     // u2 -> cat1[:, 0:32]
     ICUDA(gemm(h, PixK{act(h->d1, N, H2, W2, 64, 0), s.P2}, ugemm::DenseK{h->wf[6], 128, 64},
                EpiConvT{h->cat1, 64, 0, bias_of(h, 6), 32, H2, W2}, s.P2, 128, 64, false));
     // d2
-    ICUDA(gemm(h, conv3k(act(h->cat1, N, H, W, 64, 0), 64, H, W, 1, s.P), ugemm::DenseK{h->wf[7], 32, 576},
-               EpiAct{h->d2, 32, 0, bias_of(h, 7), 1}, s.P, 32, 576, false));
+    ICUDA(conv_tma(h, h->cat1, 64, 0, 64, 0, N, H, W, h->wf[7], 32, EpiAct{h->d2, 32, 0, bias_of(h, 7), 1}));
     // frames
     ICUDA(gemm(h, PixK{act(h->d2, N, H, W, 32, 0), s.P}, ugemm::DenseK{h->wf[8], 16, 32},
                EpiOut{h->out, h->l0, h->l4, bias_of(h, 8), s.P}, s.P, 16, 32, false));
@@ -427,8 +477,7 @@ int backward(neurosim_interp* h, const Shape& s)
     ICUDA(gemm(h, Im2colMN{act(h->cat2, N, H2, W2, 128, 0), 128, H2, W2, 1, 1152, s.P2},
                PixMN{act(h->gd1, N, H2, W2, 64, 0), 64, s.P2}, EpiDW{G + L.w_off[5], 64}, 1152, 64, s.P2, true));
     if ((rc = bias_grad(h, h->gd1, s.P2, 64, 0, 64, 5))) return rc;
-    ICUDA(gemm(h, conv3tk(act(h->gd1, N, H2, W2, 64, 0), 64, H2, W2, 1, s.P2), ugemm::DenseK{h->wb[5], 128, 576},
-               EpiGrad{h->gcat2, 128, 0, h->cat2, 128, 0, 64, 0}, s.P2, 128, 576, false));
+    ICUDA(conv_tma(h, h->gd1, 64, 0, 64, 1, N, H2, W2, h->wb[5], 128, EpiGrad{h->gcat2, 128, 0, h->cat2, 128, 0, 64, 0}));
     // ---- convT1 (e4 -> u1): W5, b5, d(e4)
     ICUDA(gemm(h, PixMN{act(h->e4, N, H4, W4, 128, 0), 128, s.P4},
                S2DMN{act(h->gcat2, N, H2, W2, 128, 0), 64, H4, W4, 256, s.P4}, EpiDW{G + L.w_off[4], 256}, 128, 256,
@@ -440,8 +489,7 @@ int backward(neurosim_interp* h, const Shape& s)
     ICUDA(gemm(h, Im2colMN{act(h->e3, N, H4, W4, 128, 0), 128, H4, W4, 1, 1152, s.P4},
                PixMN{act(h->ge4, N, H4, W4, 128, 0), 128, s.P4}, EpiDW{G + L.w_off[3], 128}, 1152, 128, s.P4, true));
     if ((rc = bias_grad(h, h->ge4, s.P4, 128, 0, 128, 3))) return rc;
-    ICUDA(gemm(h, conv3tk(act(h->ge4, N, H4, W4, 128, 0), 128, H4, W4, 1, s.P4), ugemm::DenseK{h->wb[3], 128, 1152},
-               EpiGrad{h->ge3, 128, 0, h->e3, 128, 0, 0, 0}, s.P4, 128, 1152, false));
+    ICUDA(conv_tma(h, h->ge4, 128, 0, 128, 1, N, H4, W4, h->wb[3], 128, EpiGrad{h->ge3, 128, 0, h->e3, 128, 0, 0, 0}));
     // ---- conv3 (e2 -> e3, stride 2): W3, b3, d(e2) added into d(cat2)[:, 64:128]
     ICUDA(gemm(h, Im2colMN{act(h->cat2, N, H2, W2, 128, 64), 64, H4, W4, 2, 576, s.P4},
                PixMN{act(h->ge3, N, H4, W4, 128, 0), 128, s.P4}, EpiDW{G + L.w_off[2], 128}, 576, 128, s.P4, true));

@@ -1,0 +1,262 @@
+// Tensor-core GEMM with TMA-loaded operands: D[M x N] = A[M x K] * B[K x N]
+// where every K tile of A and B is one tensor-map box copied by the Tensor
+// Memory Accelerator into 128-byte-swizzled shared memory, in a 4-stage
+// pipeline with warp roles: one thread issues the TMA loads, one thread the
+// tcgen05 MMAs, and all four warps drain TMEM in the epilogue.
+//
+// A comes from an "A loader" that maps (tile, K tile) to box coordinates and
+// TMEM lane to output row: a dense row-major matrix, or the tap boxes of a
+// 3 x 3 stride-1 convolution over BF16 NHWC activations (one box of 64
+// channels x TW x TH pixels per tap and channel chunk; zero fill outside the
+// image is the convolution's padding).  B is a packed K-major weight matrix.
+#pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "umma.cuh"
+
+namespace utma {
+
+constexpr int BM = 128;
+constexpr int BK = 64;           // one 128-byte swizzle row of BF16
+constexpr int STAGES = 4;
+constexpr uint32_t kErrTimeout = 1u;
+
+// ---- host: tensor maps (driver entry point looked up through the runtime) -------------
+// BF16 tiled map with 128-byte swizzle and zero fill outside the tensor;
+// strides_bytes has rank - 1 entries (dimension 0 is contiguous).
+inline bool encode_tiled(CUtensorMap* map, int rank, const void* base, const cuuint64_t* dims,
+                         const cuuint64_t* strides_bytes, const cuuint32_t* box)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return false;
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    const cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), dims, strides_bytes,
+              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Packed K-major BF16 matrix [rows][K] as a 2-D map, box (64, box_rows).
+inline bool encode_kmajor(CUtensorMap* map, const void* base, int rows, int K, int box_rows)
+{
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * 2u};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    return encode_tiled(map, 2, base, dims, strides, box);
+}
+
+// ---- device helpers --------------------------------------------------------------------
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(umma::smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        :: "r"(umma::smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1),
+           "r"(umma::smem_u32(mbar)) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        :: "r"(umma::smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+           "r"(umma::smem_u32(mbar)) : "memory");
+}
+
+// K-major operand in the 128-byte swizzle layout written by TMA: rows of
+// 128 B (64 BF16 of K), 8-row atoms of 1024 B; k-step s (K = 16) starts
+// 32 B further inside the row.  Layout type 2 = SWIZZLE_128B.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr, int s)
+{
+    uint64_t d = umma::smem_desc(saddr + (uint32_t)s * 32u, 16u, 1024u);
+    d |= (uint64_t)2u << 61;
+    return d;
+}
+
+// ---- A loaders ---------------------------------------------------------------------------
+// Dense row-major A [M][K]: 2-D map (K, M), box (64, 128).
+struct DenseA {
+    int M, K;
+    __device__ __forceinline__ int n_kt() const { return (K + BK - 1) / BK; }
+    __device__ __forceinline__ void load(void* dst, const CUtensorMap* map, int tile, int kt, uint64_t* mbar) const
+    {
+        tma_load_2d(dst, map, kt * BK, tile * BM, mbar);
+    }
+    __device__ __forceinline__ int row_of(int tile, int r) const
+    {
+        const int m = tile * BM + r;
+        return m < M ? m : -1;
+    }
+};
+
+// 3 x 3 stride-1 convolution over NHWC activations (4-D map: channels of
+// the buffer, W, H, N; box 64 x TW x TH x 1).  Output tile = TW x TH pixels of
+// one image; K tile = (tap, 64-channel chunk) of the view [off, off + C).
+// flip = 0: out(y, x) reads in(y + dy - 1, x + dx - 1)          (forward)
+// flip = 1: out(y, x) reads g(y + 1 - dy, x + 1 - dx)           (data gradient)
+struct ConvTapA {
+    int C, off, flip;
+    int W, H, N;          // image size (input = output size at stride 1)
+    int TW, TH, tiles_x, tiles_y;
+    __device__ __forceinline__ int n_kt() const { return 9 * (C / BK); }
+    __device__ __forceinline__ void origin(int tile, int& n, int& x0, int& y0) const
+    {
+        const int per = tiles_x * tiles_y;
+        n = tile / per;
+        const int rem = tile - n * per;
+        const int ty = rem / tiles_x;
+        y0 = ty * TH;
+        x0 = (rem - ty * tiles_x) * TW;
+    }
+    __device__ __forceinline__ void load(void* dst, const CUtensorMap* map, int tile, int kt, uint64_t* mbar) const
+    {
+        int n, x0, y0;
+        origin(tile, n, x0, y0);
+        const int cc = C / BK;
+        const int tap = kt / cc, c = off + (kt - tap * cc) * BK;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        tma_load_4d(dst, map, c, flip ? x0 - dx : x0 + dx, flip ? y0 - dy : y0 + dy, n, mbar);
+    }
+    __device__ __forceinline__ int row_of(int tile, int r) const
+    {
+        int n, x0, y0;
+        origin(tile, n, x0, y0);
+        const int ty = r / TW, x = x0 + (r - ty * TW), y = y0 + ty;
+        return (x < W && y < H) ? (n * H + y) * W + x : -1;
+    }
+};
+
+template <class AL, class EP>
+struct TmaArgs {
+    CUtensorMap ta;       // A map
+    CUtensorMap tb;       // B map: packed weights (K, N), box (64, BN)
+    AL a;
+    EP ep;
+    int N;                // real columns (<= BN)
+    unsigned int* err;
+    uint64_t limit_ns;
+};
+
+template <int BN>
+__host__ __device__ constexpr size_t tma_smem_bytes()
+{
+    return 1024 + (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 256;
+}
+
+template <int BN, class AL, class EP>
+__global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ TmaArgs<AL, EP> g)
+{
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "tcgen05 N for M = 128");
+    constexpr uint32_t TCOLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+    extern __shared__ unsigned char smem_raw[];
+    // 1024-byte alignment of the swizzled tiles
+    unsigned char* smem = smem_raw + ((1024u - (umma::smem_u32(smem_raw) & 1023u)) & 1023u);
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + STAGES * A_BYTES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = empty + STAGES;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tile = blockIdx.x;
+    const int n_kt = g.a.n_kt();
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            umma::mbar_init(&full[s], 1);
+            umma::mbar_init(&empty[s], 1);
+        }
+        umma::mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) umma::tmem_alloc(tslot, TCOLS);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(BM, BN, false, false);
+
+    __shared__ unsigned int s_fail;
+    if (tid == 0) s_fail = 0u;
+    __syncthreads();
+    if (tid == 0) {
+        // producer: TMA loads of A and B, one stage ahead of the tensor core
+        for (int kt = 0; kt < n_kt; ++kt) {
+            const int s = kt % STAGES;
+            if (kt >= STAGES &&
+                !umma::mbar_wait(&empty[s], (uint32_t)((kt / STAGES - 1) & 1), g.limit_ns)) {
+                atomicOr(&s_fail, 1u);
+                break;
+            }
+            mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+            g.a.load(sA + s * A_BYTES, &g.ta, tile, kt, &full[s]);
+            tma_load_2d(sB + s * B_BYTES, &g.tb, kt * BK, 0, &full[s]);
+        }
+    } else if (tid == 32) {
+        // MMA issuer
+        for (int kt = 0; kt < n_kt; ++kt) {
+            const int s = kt % STAGES;
+            if (!umma::mbar_wait(&full[s], (uint32_t)((kt / STAGES) & 1), g.limit_ns)) {
+                atomicOr(&s_fail, 1u);
+                break;
+            }
+            umma::fence_after_sync();
+            const uint32_t a0 = umma::smem_u32(sA + s * A_BYTES), b0 = umma::smem_u32(sB + s * B_BYTES);
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k)
+                umma::mma_bf16(tmem, desc_sw128(a0, k), desc_sw128(b0, k), idesc, (kt > 0 || k > 0) ? 1u : 0u);
+            umma::mma_commit(&empty[s]);
+        }
+        umma::mma_commit(done);
+    }
+    bool ok = umma::mbar_wait(done, 0u, g.limit_ns);
+    umma::fence_after_sync();
+    ok = __syncthreads_and(ok && s_fail == 0u);
+    if (ok) {
+        const int r = warp * 32 + (tid & 31);
+        const int row = g.a.row_of(tile, r);
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 8) {
+            float v[8];
+            umma::tmem_ld8(lane_addr + (uint32_t)c, v);
+            if (row >= 0 && c < g.N) g.ep.store(row, c, v, 0);
+        }
+    } else if (tid == 0) {
+        atomicOr(g.err, kErrTimeout);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, TCOLS);
+}
+
+template <int BN, class AL, class EP>
+cudaError_t launch_tma_gemm(const TmaArgs<AL, EP>& g, int tiles, cudaStream_t stream)
+{
+    const size_t smem = tma_smem_bytes<BN>();
+    cudaError_t e = cudaFuncSetAttribute(tma_gemm_kernel<BN, AL, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    tma_gemm_kernel<BN, AL, EP><<<tiles, 128, smem, stream>>>(g);
+    return cudaGetLastError();
+}
+
+}  // namespace utma

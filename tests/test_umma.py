@@ -30,7 +30,7 @@ def _gemm(mode, A, B, M, N, K):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 64, 64), (304, 256, 200), (77, 48, 136)])
-@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
 def test_gemm_layouts(mode, M, N, K):
     g = torch.Generator().manual_seed(M * 1000 + N * 10 + K + mode)
     A = torch.randn(M, K, generator=g).to(torch.bfloat16).float()
