@@ -413,6 +413,31 @@ __global__ void __launch_bounds__(kSortThreads) sort_kernel(const __grid_constan
         const int tshift = sdp->pix_bits + 1;
         const uint32_t ta = (uint32_t)interval_start(step_ta0(L, *sdp), *sdp, j, L.dt);
         const RecordSink rsink{L.out + abs0, ta, sdp->W, tshift, (1u << sdp->pix_bits) - 1u};
+        if (2u * N <= cap) {
+            // the interval fits twice in shared memory: copy its chunks (tile
+            // order) into one array, then sort between two shared arrays
+            KeyT* X = sbuf;
+            KeyT* Y = sbuf + N;
+            const KeyT* keys = reinterpret_cast<const KeyT*>(L.keys);
+            for (int c = tid; c < nt; c += THREADS) {
+                const KeyT* src = keys + coff[c];
+                KeyT* dst = X + cpre[c];
+                const uint32_t cnt = cpre[c + 1] - cpre[c];
+                for (uint32_t i = 0; i < cnt; ++i) dst[i] = src[i];
+            }
+            __syncthreads();
+            KeyT* cur = X;
+            KeyT* nxt = Y;
+            for (int p = 0; p < npass - 1; ++p) {
+                radix_pass<THREADS, KeyT>(ArraySrc<KeyT>{cur}, KeySink<KeyT>{nxt}, N, tshift + p * bits, NB, hist,
+                                          binbase);
+                KeyT* t = cur;
+                cur = nxt;
+                nxt = t;
+            }
+            radix_pass<THREADS, KeyT>(ArraySrc<KeyT>{cur}, rsink, N, tshift + (npass - 1) * bits, NB, hist, binbase);
+            continue;
+        }
         const bool fit = (npass <= 2) ? (N <= cap) : (2u * N <= cap);
         KeyT* X = fit ? sbuf : reinterpret_cast<KeyT*>(L.temp) + L.seg_rel[seg];
         KeyT* Y = fit ? sbuf + N : reinterpret_cast<KeyT*>(L.out + abs0);
@@ -562,13 +587,14 @@ cudaError_t emit_occupancy(int ppt, int pf, int key64, int* blocks_per_sm)
 
 cudaError_t sort_configure(int* smem_bytes)
 {
-    // two sort CTAs per SM: ~113 KB of shared memory each
+    // two sort CTAs per SM: 110 KB of shared memory each (with the 1 KB the
+    // runtime reserves per CTA, two fit in the 228 KB of an SM)
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    int want = 113 * 1024;
+    int want = 110 * 1024;
     if (want > optin) want = optin;
     e = cudaFuncSetAttribute(sort_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
     if (e != cudaSuccess) return e;
