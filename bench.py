@@ -91,6 +91,11 @@ WORKLOADS = {
     "learned": dict(dims=None, sim=None, render=None,
                     name="learned: HD 1280x720 texture clip, keyframes at 250 FPS, U-Net predicts 3 log frames "
                          "per interval, exact event emission at 1000 FPS; C+0.2 C-0.25 sigma0.03 refractory 100us"),
+    "batched_learned": dict(dims=None, sim=None, render=None,
+                            name="batched + learned: 1024 sensors at 320x240 and 64 at 1280x720, keyframes at "
+                                 "250 FPS, U-Net predicts 3 log frames per interval, one batched event step of 4 "
+                                 "frames per interval; texture scenes up to 600 px/s, C+0.2 C-0.25 sigma0.03 "
+                                 "refractory 100us"),
     "batch": dict(dims=None, sim=None, render=None,
                   name="batched: 256 sensors (346x260 / 640x480 / 1280x720 by index mod 3), "
                        "16 frames @1000 FPS per step, texture scenes, C+- ~ U[0.15,0.35], "
@@ -604,6 +609,176 @@ def run_learned(args):
     net.close()
 
 
+def run_batched_learned(args):
+    """Batched + learned: every interval, the interpolator predicts 3 log frames
+    for each of 1088 sensors from their keyframes, and one batched event step
+    consumes them; scored (F1) and timed against the plain batched path on
+    the rendered 1000 FPS frames."""
+    from paper_2602_15018_gb300 import EventSimBatch, Interpolator, event_f1, log_intensity
+    from paper_2602_15018_gb300 import learned
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    groups = [((320, 240), args.bl_small, 64), ((1280, 720), args.bl_big, 8)]    # (size, sensors, U-Net chunk)
+    sim = dict(c_pos=0.2, c_neg=0.25, sigma_c=0.03, c_min=0.01, refractory_us=100, input_is_log=True)
+    sensors = []
+    for gi, ((W, H), n, _) in enumerate(groups):
+        for i in range(n):
+            sensors.append(dict(width=W, height=H, seed=rank * 100003 + gi * 10007 + i, **sim))
+    net = Interpolator(8, 720, 1280, seed=args.seed)
+    t_tr = time.time()
+    learned.train(net, args.train_steps, batch=16, size=256, lr=3e-3, speed=(150.0, 600.0), seed=10000 + 7919 * rank)
+    torch.cuda.synchronize()
+    train_s = time.time() - t_tr
+
+    # log frames at 1000 FPS, t = 0..4 ms, per group: [5][n][H][W]; keys are frames 0 and 4
+    t_r = time.time()
+    logs = []
+    for gi, ((W, H), n, _) in enumerate(groups):
+        L = torch.empty((5, n, H, W), dtype=torch.float32, device=dev)
+        for i in range(n):
+            sc = scenes.TextureScene(W, H, seed=args.seed * 7 + gi * 100003 + i + 1000 * rank, speed=(150.0, 600.0))
+            fr = sc.render(np.arange(5), device=dev).contiguous()
+            L[:, i] = log_intensity(fr)
+        logs.append(L)
+    torch.cuda.synchronize()
+    render_s = time.time() - t_r
+    npix = sum(n * W * H for (W, H), n, _ in groups)
+
+    # interval buffers [4][n][H][W]: planes 0..2 predicted, plane 3 the next key;
+    # slot 0 interpolates key A (t 0) -> B (t 4), slot 1 B -> A (ping-pong)
+    bufs = [[torch.empty((4, n, H, W), dtype=torch.float32, device=dev) for (W, H), n, _ in groups]
+            for _ in range(2)]
+
+    def predict(slot, model=None):
+        model = model or net
+        for gi, ((W, H), n, ch) in enumerate(groups):
+            a, b = (logs[gi][0], logs[gi][4]) if slot == 0 else (logs[gi][4], logs[gi][0])
+            buf = bufs[slot][gi]
+            for c0 in range(0, n, ch):
+                c1 = min(n, c0 + ch)
+                tmp = model.forward(a[c0:c1].contiguous(), b[c0:c1].contiguous())
+                buf[0:3, c0:c1] = tmp
+            buf[3] = b
+
+    def make_batch(plain):
+        bt = EventSimBatch(sensors, frames_per_step=4, dt_us=DT, t0_us=0, max_pending_steps=4)
+        bt.init([logs[gi][0, i] .contiguous() for gi, (_, n, _) in enumerate(groups) for i in range(n)])
+        for slot in range(2):
+            frames, strides = [], []
+            for gi, ((W, H), n, _) in enumerate(groups):
+                src = (plain_fwd[gi] if slot == 0 else plain_rev[gi]) if plain else bufs[slot][gi]
+                for i in range(n):
+                    frames.append(src[0, i])
+                    strides.append(n * W * H)
+            bt.set_frames_strided(frames, strides, slot=slot)
+        return bt
+
+    plain_fwd = [L[1:5].contiguous() for L in logs]                      # t 1..4 ms
+    plain_rev = [torch.flip(L[0:4], dims=[0]).contiguous() for L in logs]  # t 3..0 ms
+
+    # ---- score: 4 intervals of the plain, learned and linear (untrained) pipelines
+    n_score = 4
+    lin_net = Interpolator(8, 720, 1280, seed=0)
+    per_pipe = []
+    for plain, model in ((True, None), (False, net), (False, lin_net)):
+        bt = make_batch(plain)
+        for k in range(n_score):
+            if not plain:
+                predict(k % 2, model)
+            bt.step(slot=k % 2)
+        ev, seg = bt.drain()
+        per_pipe.append(bt.split(ev, seg))
+        bt.close()
+    lin_net.close()
+
+    def f1_of(pred):
+        c = np.zeros(3, np.int64)
+        for (ev_p, _), (ev_l, _) in zip(per_pipe[0], pred):
+            r = event_f1(ev_l, ev_p, 1000)
+            c += [r["matched"], r["n_pred"], r["n_ref"]]
+        P_, R_ = c[0] / max(1, c[1]), c[0] / max(1, c[2])
+        return 2 * P_ * R_ / max(1e-12, P_ + R_), c
+
+    f1, counts = f1_of(per_pipe[1])
+    f1_lin, _ = f1_of(per_pipe[2])
+
+    # ---- timing
+    st = torch.cuda.current_stream()
+
+    def timed(plain, steps):
+        bt = make_batch(plain)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for k in range(args.warmup):
+            if not plain:
+                predict(k % 2)
+            bt.step(slot=k % 2)
+        bt.drain(to="cuda")
+        torch.cuda.synchronize()
+        e0.record(st)
+        for k in range(args.warmup, args.warmup + steps):
+            if not plain:
+                predict(k % 2)
+            bt.step(slot=k % 2)
+            if (k + 1) % 4 == 0:
+                bt.drain(to="cuda")
+        bt.drain(to="cuda")
+        e1.record(st)
+        torch.cuda.synchronize()
+        bt.close()
+        return e0.elapsed_time(e1) / steps
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    tw0 = time.time()
+    ms_plain = timed(True, args.steps)
+    ms_learn = timed(False, args.steps)
+    tw1 = time.time()
+    clocks.stop()
+    # renderer stand-in cost: one keyframe set vs four frame sets per interval
+    r0 = time.time()
+    for gi, ((W, H), n, _) in enumerate(groups):
+        for i in range(min(n, 32)):
+            scenes.TextureScene(W, H, seed=i).render(np.arange(4), device=dev)
+    torch.cuda.synchronize()
+    render_4_ms = (time.time() - r0) * 1e3 * sum(n for _, n, _ in groups) / sum(min(n, 32) for _, n, _ in groups)
+    px = 4 * npix
+    value = px / (ms_learn / 1e3) / 1e6
+    peak, peak_src = measured_bf16_peak()
+    unet_ms = ms_learn - ms_plain
+    tflops = npix * UNET_FLOP_PER_PX / (max(unet_ms, 1e-3) / 1e3) / 1e12
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "Mpixel-frames/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_learn, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 (U-Net), f32 (events)", "data": "synthetic (seeded procedural scenes rendered on the device)",
+            "config": {"workload": WORKLOADS["batched_learned"]["name"], "sensors": len(sensors),
+                       "pixels_per_interval": npix, "frames_per_interval": 4, "dt_us": DT,
+                       "parallelism": f"replicas x{ws}",
+                       "l2": "frames and activations far larger than L2; no flush"},
+            "f1": round(float(f1), 4), "f1_linear": round(float(f1_lin), 4),
+            "f1_counts": [int(c) for c in counts], "f1_intervals": n_score,
+            "plain_value": round(px / (ms_plain / 1e3) / 1e6, 1),
+            "ms": {"plain_events_per_interval": round(ms_plain, 3), "learned_per_interval": round(ms_learn, 3),
+                   "render_4_frames_per_interval_est": round(render_4_ms, 1),
+                   "render_1_keyframe_per_interval_est": round(render_4_ms / 4, 1)},
+            "e2e_speedup_vs_plain_with_render": round((render_4_ms + ms_plain) / (render_4_ms / 4 + ms_learn), 3),
+            "train": {"steps": args.train_steps, "seconds": round(train_s, 1)},
+            "setup_render_s": round(render_s, 1),
+            "gpu_launches": None,
+            "roofline": {"bound": "tensor", "achieved": round(tflops, 1), "peak": peak, "unit": "TFLOP/s",
+                         "frac": round(tflops / peak, 4), "traffic": None,
+                         "kernel": "U-Net forward over all sensors of one interval (learned minus plain step)",
+                         "peak_source": peak_src},
+            "e2e": None, "cpu_baseline": None,
+            "clocks": clocks.summary(tw0, tw1),
+        }
+        print(json.dumps(line), flush=True)
+    net.close()
+
+
 def _oracle_sample_frames(args, dev):
     wl = WORKLOADS[args.workload]
     n = min(args.cpu_frames, wl["dims"]["T"])
@@ -695,6 +870,8 @@ def main():
     ap.add_argument("--cpu-frames", type=int, default=480)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--keys", type=int, default=126, help="learned workload: keyframes per clip")
+    ap.add_argument("--bl-small", type=int, default=1024, help="batched_learned: 320x240 sensors")
+    ap.add_argument("--bl-big", type=int, default=64, help="batched_learned: 1280x720 sensors")
     ap.add_argument("--train-steps", type=int, default=4000, help="learned workload: training steps")
     ap.add_argument("--frames", type=int, default=0,
                     help="frames per step (default: the workload's); for small profiling cases")
@@ -702,13 +879,15 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
-        if args.workload in ("batch", "learned"):
+        if args.workload in ("batch", "learned", "batched_learned"):
             ap.error("the reference arm runs the plain workloads only")
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "batched_learned":
+        run_batched_learned(args)
     else:
         run_ours(args)
 

@@ -238,6 +238,13 @@ int neurosim_evsim_batch_create(const neurosim_evsim_params *streams,
 int neurosim_evsim_batch_set_frames(neurosim_evsim_batch *b, int32_t slot,
                                     const float *const *frames_dev);
 
+/* As neurosim_evsim_batch_set_frames, with stream i's frame f at
+ * frames_dev[i] + f * frame_strides[i] floats (HOST array; 0 or NULL = W*H,
+ * else >= W*H): frames of many sensors can sit interleaved in one array,
+ * e.g. the [3][batch][H][W] output of the learned interpolator. */
+int neurosim_evsim_batch_set_frames_strided(neurosim_evsim_batch *b, int32_t slot,
+                                            const float *const *frames_dev, const int64_t *frame_strides);
+
 /* Initialises every stream from one frame at t0_us (HOST array of n_streams
  * DEVICE pointers to one [H_i][W_i] FP32 frame each): ref = L_prev = L, no
  * events.  Enqueued on the batch's stream.  NEUROSIM_E_STATE if the batch

@@ -26,7 +26,7 @@ EXPORTS = [
     "neurosim_debug_log", "neurosim_evsim_set_profiling", "neurosim_evsim_get_stats",
     "neurosim_evsim_step_noalloc",
     "neurosim_evsim_batch_default_params", "neurosim_evsim_batch_create",
-    "neurosim_evsim_batch_set_frames", "neurosim_evsim_batch_init", "neurosim_evsim_batch_step",
+    "neurosim_evsim_batch_set_frames", "neurosim_evsim_batch_set_frames_strided", "neurosim_evsim_batch_init", "neurosim_evsim_batch_step",
     "neurosim_evsim_batch_pending", "neurosim_evsim_batch_drain", "neurosim_evsim_batch_get_state",
     "neurosim_evsim_batch_get_thresholds", "neurosim_evsim_batch_counters",
     "neurosim_evsim_batch_destroy", "neurosim_evsim_autotune", "neurosim_debug_umma_gemm",
@@ -133,6 +133,8 @@ def lib():
                                                       C.POINTER(vp)]
             L.neurosim_evsim_batch_set_frames.restype = C.c_int
             L.neurosim_evsim_batch_set_frames.argtypes = [vp, i32, C.POINTER(vp)]
+            L.neurosim_evsim_batch_set_frames_strided.restype = C.c_int
+            L.neurosim_evsim_batch_set_frames_strided.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(i64)]
             L.neurosim_evsim_batch_init.restype = C.c_int
             L.neurosim_evsim_batch_init.argtypes = [vp, C.POINTER(vp)]
             L.neurosim_evsim_batch_step.restype = C.c_int

@@ -130,7 +130,7 @@ void release(neurosim_evsim_batch* b)
 
 // Descriptor of stream i for a launch whose state is read from buffer `par`.
 StreamDesc make_desc(const neurosim_evsim_batch* b, int i, int par, bool init, const float* frames,
-                     int item_base, int seg_base, int64_t chunk_base)
+                     int64_t frame_stride, int item_base, int seg_base, int64_t chunk_base)
 {
     const BatchStream& st = b->s[i];
     StreamDesc d;
@@ -156,7 +156,8 @@ StreamDesc make_desc(const neurosim_evsim_batch* b, int i, int par, bool init, c
     d.seg_base = seg_base;
     d.n_segs = init ? 0 : b->T;
     d.init = init ? 1 : 0;
-    d.vec = (st.npix % 4 == 0 && (reinterpret_cast<uintptr_t>(frames) & 15u) == 0) ? 1 : 0;
+    d.vec = (st.npix % 4 == 0 && frame_stride % 4 == 0 && (reinterpret_cast<uintptr_t>(frames) & 15u) == 0) ? 1 : 0;
+    d.frame_stride = frame_stride;
     d.pix_bits = st.pix_bits;
     d.D0 = b->dt;
     d.ta0 = 0;                   // taken from the device clock
@@ -165,15 +166,19 @@ StreamDesc make_desc(const neurosim_evsim_batch* b, int i, int par, bool init, c
     return d;
 }
 
-// Uploads both parity sets of descriptors for the given frame pointers.
-int upload_descs(neurosim_evsim_batch* b, StreamDesc* dst, bool init, const float* const* frames)
+// Uploads both parity sets of descriptors for the given frame pointers
+// (frame_strides: floats between frames per stream, nullable = W * H).
+int upload_descs(neurosim_evsim_batch* b, StreamDesc* dst, bool init, const float* const* frames,
+                 const int64_t* frame_strides)
 {
     std::vector<StreamDesc> h((size_t)2 * b->n);
     for (int par = 0; par < 2; ++par) {
         int item = 0, seg = 0;
         int64_t chunk = 0;
         for (int i = 0; i < b->n; ++i) {
-            h[(size_t)par * b->n + i] = make_desc(b, i, par, init, frames[i], item, seg, chunk);
+            const int64_t fs = frame_strides ? frame_strides[i] : 0;
+            h[(size_t)par * b->n + i] =
+                make_desc(b, i, par, init, frames[i], fs ? fs : (int64_t)b->s[i].npix, item, seg, chunk);
             item += b->s[i].n_tiles;
             seg += init ? 0 : b->T;
             chunk += (int64_t)b->T * b->s[i].n_tiles;
@@ -391,18 +396,28 @@ int neurosim_evsim_batch_create(const neurosim_evsim_params* streams, const neur
     return NEUROSIM_OK;
 }
 
-int neurosim_evsim_batch_set_frames(neurosim_evsim_batch* b, int32_t slot, const float* const* frames_dev)
+int neurosim_evsim_batch_set_frames_strided(neurosim_evsim_batch* b, int32_t slot, const float* const* frames_dev,
+                                            const int64_t* frame_strides)
 {
     if (!b || !frames_dev) return fail(NEUROSIM_E_INVALID, "batch and frames_dev must not be NULL");
+    if (frame_strides)
+        for (int i = 0; i < b->n; ++i)
+            if (frame_strides[i] != 0 && frame_strides[i] < (int64_t)b->s[i].npix)
+                return fail(NEUROSIM_E_INVALID, "frame_strides[%d] is smaller than W * H", i);
     if (slot < 0 || slot >= b->slots) return fail(NEUROSIM_E_INVALID, "slot %d not in [0, %d)", slot, b->slots);
     for (int i = 0; i < b->n; ++i)
         if (!frames_dev[i]) return fail(NEUROSIM_E_INVALID, "frames_dev[%d] is NULL", i);
     BatchGuard g(b->device);
     if (!g.ok) return fail(NEUROSIM_E_CUDA, "cannot select the batch's device");
-    const int rc = upload_descs(b, b->d_step + (size_t)slot * 2 * b->n, false, frames_dev);
+    const int rc = upload_descs(b, b->d_step + (size_t)slot * 2 * b->n, false, frames_dev, frame_strides);
     if (rc) return rc;
     b->slot_set[slot] = true;
     return NEUROSIM_OK;
+}
+
+int neurosim_evsim_batch_set_frames(neurosim_evsim_batch* b, int32_t slot, const float* const* frames_dev)
+{
+    return neurosim_evsim_batch_set_frames_strided(b, slot, frames_dev, nullptr);
 }
 
 int neurosim_evsim_batch_init(neurosim_evsim_batch* b, const float* const* first_frames_dev)
@@ -413,7 +428,7 @@ int neurosim_evsim_batch_init(neurosim_evsim_batch* b, const float* const* first
         if (!first_frames_dev[i]) return fail(NEUROSIM_E_INVALID, "first_frames_dev[%d] is NULL", i);
     BatchGuard g(b->device);
     if (!g.ok) return fail(NEUROSIM_E_CUDA, "cannot select the batch's device");
-    int rc = upload_descs(b, b->d_init, true, first_frames_dev);
+    int rc = upload_descs(b, b->d_init, true, first_frames_dev, nullptr);
     if (rc) return rc;
     const StepLaunch L = make_launch(b, true, 0);
     BCUDA(launch_step(L, &b->launches));

@@ -373,6 +373,7 @@ __global__ void __launch_bounds__(WARPS * 32) emit_kernel(const __grid_constant_
         c.keep = pol_keep;
         const int lane_g = c.g0 + lane * 4;                  // global pixel of (q=0, c=0)
         const int lane_left = npix - lane_g;                 // valid pixels from there on
+        const int64_t fstride = sdp->frame_stride ? sdp->frame_stride : (int64_t)npix;
         int nvq = 0;                                         // complete float4 groups (vec)
 #pragma unroll
         for (int q = 0; q < NQ; ++q) nvq += (lane_left - q * 128 >= 4) ? 1 : 0;
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(WARPS * 32) emit_kernel(const __grid_constant_
         float4 buf[PF][NQ];
 #pragma unroll
         for (int u = 0; u < PF; ++u)
-            if (u < T) load_frame<PPT>(buf[u], fp + (int64_t)u * npix, nvq, vec, lane_left, pol_stream);
+            if (u < T) load_frame<PPT>(buf[u], fp + (int64_t)u * fstride, nvq, vec, lane_left, pol_stream);
 
         for (int f0 = 0; f0 < T; f0 += PF) {
 #pragma unroll
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(WARPS * 32) emit_kernel(const __grid_constant_
                                      *reinterpret_cast<const float4*>(s.vd() + p)) << (q * 4);
                 }
                 trig &= valid;
-                if (f + PF < T) load_frame<PPT>(buf[u], fp + (int64_t)(f + PF) * npix, nvq, vec, lane_left, pol_stream);
+                if (f + PF < T) load_frame<PPT>(buf[u], fp + (int64_t)(f + PF) * fstride, nvq, vec, lane_left, pol_stream);
                 if (init && f == 0) {
                     for (int k = 0; k < PPT; ++k) {
                         if (!((valid >> k) & 1u)) continue;

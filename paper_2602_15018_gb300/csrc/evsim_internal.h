@@ -73,6 +73,7 @@ struct StreamDesc {
     int64_t ta0;                  // start time of the first interval (us)
     int64_t chunk_base;           // chunk-table offset of (segment 0, tile 0)
     int64_t out_seg_index;        // slot of segment 0 in the pending offset array
+    int64_t frame_stride;         // floats from one frame to the next (0: npix)
 };
 
 // Everything one step launch needs (passed by value as a __grid_constant__).

@@ -287,6 +287,19 @@ class EventSimBatch:
         self._bufs[slot] = list(buffers)
         check(lib().neurosim_evsim_batch_set_frames(self._h, int(slot), _ptr_array(self._bufs[slot])))
 
+    def set_frames_strided(self, frames, strides, slot: int = 0) -> None:
+        """Registers sensor i's frames as views frames[i] (a CUDA float32 tensor whose
+        first element is frame 0) with consecutive frames strides[i] floats apart."""
+        arr = (C.c_void_p * len(frames))()
+        st = (C.c_int64 * len(frames))()
+        for i, (t, s_) in enumerate(zip(frames, strides)):
+            if not (t.is_cuda and t.dtype == torch.float32):
+                raise ValueError("frames must be float32 CUDA tensors")
+            arr[i] = t.data_ptr()
+            st[i] = int(s_)
+        self._bufs[slot] = list(frames)
+        check(lib().neurosim_evsim_batch_set_frames_strided(self._h, int(slot), arr, st))
+
     def step(self, slot: int = 0) -> None:
         check(lib().neurosim_evsim_batch_step(self._h, int(slot)))
 

@@ -232,3 +232,36 @@ def test_autotune_picks_a_variant_and_caches_it(tmp_path):
         res.append(sim.drain())
         sim.close()
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+def test_batch_strided_frames_match_oracle():
+    """Three equal-size sensors whose frames interleave in one [T][3][H][W]
+    array (frame stride 3 H W), as the interpolator's output is laid out."""
+    from paper_2602_15018_gb300 import EventSimBatch
+    T, t0, W, H = 5, 0, 48, 40
+    sensors = [dict(width=W, height=H, c_pos=0.2, c_neg=0.25, sigma_c=0.02, refractory_us=50, seed=60 + i)
+               for i in range(3)]
+    clips = [scenes.render_frames(scenes.TextureScene(W, H, seed=80 + i, speed=(300.0, 600.0)), 1 + 2 * T)
+             for i in range(3)]
+    batch = EventSimBatch(sensors, frames_per_step=T, dt_us=DT, t0_us=t0)
+    orcs = []
+    for i, s in enumerate(sensors):
+        cp, cn = batch.thresholds(i)
+        orcs.append(oracle.OracleSim(W, H, c_pos_map=cp, c_neg_map=cn, refractory_us=50))
+    batch.init([c[0].contiguous().cuda() for c in clips])
+    for i, o in enumerate(orcs):
+        o.step(np.ascontiguousarray(clips[i][:1].numpy()), t0, DT)
+    inter = torch.empty((T, 3, H, W), dtype=torch.float32, device="cuda")
+    batch.set_frames_strided([inter[0, i] for i in range(3)], [3 * H * W] * 3, slot=0)
+    for k in range(2):
+        for i in range(3):
+            inter[:, i] = clips[i][1 + k * T: 1 + (k + 1) * T].cuda()
+        batch.step(slot=0)
+        ev, seg = batch.drain()
+        per = batch.split(ev, seg)
+        for i, o in enumerate(orcs):
+            rev, rseg = o.step(np.ascontiguousarray(clips[i][1 + k * T: 1 + (k + 1) * T].numpy()),
+                               t0 + (1 + k * T) * DT, DT)
+            assert np.array_equal(per[i][0], rev), (k, i)
+            assert np.array_equal(per[i][1], rseg), (k, i)
+    batch.close()
