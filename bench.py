@@ -514,7 +514,7 @@ def run_learned(args):
     npix = W * H
     net = Interpolator(8, H, W, seed=args.seed)
     t_tr = time.time()
-    losses = learned.train(net, args.train_steps, batch=16, size=256, lr=3e-3, speed=(150.0, 600.0),
+    losses = learned.train(net, args.train_steps, batch=16, size=256, lr=1e-3, speed=(150.0, 600.0),
                            seed=10000 + 7919 * rank, report=max(1, args.train_steps // 8))
     torch.cuda.synchronize()
     train_s = time.time() - t_tr
@@ -627,7 +627,7 @@ def run_batched_learned(args):
             sensors.append(dict(width=W, height=H, seed=rank * 100003 + gi * 10007 + i, **sim))
     net = Interpolator(8, 720, 1280, seed=args.seed)
     t_tr = time.time()
-    learned.train(net, args.train_steps, batch=16, size=256, lr=3e-3, speed=(150.0, 600.0), seed=10000 + 7919 * rank)
+    learned.train(net, args.train_steps, batch=16, size=256, lr=1e-3, speed=(150.0, 600.0), seed=10000 + 7919 * rank)
     torch.cuda.synchronize()
     train_s = time.time() - t_tr
 
@@ -872,7 +872,7 @@ def main():
     ap.add_argument("--keys", type=int, default=126, help="learned workload: keyframes per clip")
     ap.add_argument("--bl-small", type=int, default=1024, help="batched_learned: 320x240 sensors")
     ap.add_argument("--bl-big", type=int, default=64, help="batched_learned: 1280x720 sensors")
-    ap.add_argument("--train-steps", type=int, default=4000, help="learned workload: training steps")
+    ap.add_argument("--train-steps", type=int, default=8000, help="learned workload: training steps")
     ap.add_argument("--frames", type=int, default=0,
                     help="frames per step (default: the workload's); for small profiling cases")
     args = ap.parse_args()

@@ -413,8 +413,8 @@ int32_t neurosim_abi_version(void);
  * interpolator): C[M][N] (FP32, DEVICE, row-major) = sum_k A(m, k) B(n, k)
  * with BF16 DEVICE operands; modes 0-3 gather the operands with CUDA cores:
  * bit 0: A stored [K][M] (else [M][K]), bit 1: B stored [K][N] (else
- * [N][K]); mode 4 loads A [M][K] and B [N][K] with TMA into 128-byte-swizzled
- * tiles (16-byte-aligned operands).  16 <= N <= 256, N % 16 == 0, K % 8 == 0,
+ * [N][K]); modes 4 and 5 load A [M][K] and B [N][K] with TMA into 128- or
+ * 64-byte-swizzled tiles (16-byte-aligned operands).  16 <= N <= 256, N % 16 == 0, K % 8 == 0,
  * M % 8 == 0 when A is stored [K][M].  Synchronises cuda_stream. */
 int neurosim_debug_umma_gemm(int32_t mode, int32_t M, int32_t N, int32_t K, const void *A,
                              const void *B, float *C, void *cuda_stream);

@@ -58,19 +58,19 @@ struct StoreRow {
     }
 };
 
-template <int BN>
+template <int BN, int SW>
 int run_tma(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, unsigned int* err,
             cudaStream_t st)
 {
     utma::TmaArgs<utma::DenseA, StoreRow> g;
-    if (!utma::encode_kmajor(&g.ta, A, M, K, utma::BM) || !utma::encode_kmajor(&g.tb, B, N, K, BN))
+    if (!utma::encode_kmajor(&g.ta, A, M, K, utma::BM, SW) || !utma::encode_kmajor(&g.tb, B, N, K, BN, SW))
         return NEUROSIM_E_CUDA;
-    g.a = utma::DenseA{M, K};
+    g.a = utma::DenseA{M, K, 0, utma::bk_of(SW)};
     g.ep = StoreRow{C, N};
     g.N = N;
     g.err = err;
     g.limit_ns = 2000000000ull;
-    if (utma::launch_tma_gemm<BN>(g, (M + utma::BM - 1) / utma::BM, st) != cudaSuccess) return NEUROSIM_E_CUDA;
+    if (utma::launch_tma_gemm<BN, SW>(g, (M + utma::BM - 1) / utma::BM, st) != cudaSuccess) return NEUROSIM_E_CUDA;
     return NEUROSIM_OK;
 }
 
@@ -80,10 +80,11 @@ extern "C" int neurosim_debug_umma_gemm(int32_t mode, int32_t M, int32_t N, int3
                                         const void* B, float* C, void* cuda_stream)
 {
     if (!A || !B || !C) return nsim::report_error(NEUROSIM_E_INVALID, "NULL operand");
-    if (mode < 0 || mode > 4) return nsim::report_error(NEUROSIM_E_INVALID, "mode must be in [0, 4]");
-    if (mode == 4 && (reinterpret_cast<uintptr_t>(A) & 15u || reinterpret_cast<uintptr_t>(B) & 15u))
+    if (mode < 0 || mode > 5) return nsim::report_error(NEUROSIM_E_INVALID, "mode must be in [0, 5]");
+    if (mode >= 4 && (reinterpret_cast<uintptr_t>(A) & 15u || reinterpret_cast<uintptr_t>(B) & 15u))
         return nsim::report_error(NEUROSIM_E_INVALID, "TMA operands must be 16-byte aligned");
-    if (M < 1 || N < 16 || N > 256 || N % 16 || K < 8 || K % 8 || ((mode & 1) && M % 8) || ((mode & 2) && N % 8))
+    const bool amn = mode < 4 && (mode & 1), bmn = mode < 4 && (mode & 2);
+    if (M < 1 || N < 16 || N > 256 || N % 16 || K < 8 || K % 8 || (amn && M % 8) || (bmn && N % 8))
         return nsim::report_error(NEUROSIM_E_INVALID,
                                   "need M >= 1, 16 <= N <= 256 with N % 16 == 0, K % 8 == 0, MN-major rows % 8 == 0");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -93,7 +94,8 @@ extern "C" int neurosim_debug_umma_gemm(int32_t mode, int32_t M, int32_t N, int3
         return nsim::report_error(NEUROSIM_E_CUDA, "cannot allocate the error word");
     const auto* a = static_cast<const __nv_bfloat16*>(A);
     const auto* b = static_cast<const __nv_bfloat16*>(B);
-    int rc = mode == 4 ? (N <= 64 ? run_tma<64>(M, N, K, a, b, C, err, st) : run_tma<256>(M, N, K, a, b, C, err, st))
+    int rc = mode == 4 ? (N <= 64 ? run_tma<64, 128>(M, N, K, a, b, C, err, st) : run_tma<256, 128>(M, N, K, a, b, C, err, st))
+             : mode == 5 ? (N <= 64 ? run_tma<64, 64>(M, N, K, a, b, C, err, st) : run_tma<256, 64>(M, N, K, a, b, C, err, st))
              : N <= 64 ? dispatch<64>(mode, M, N, K, a, b, C, err, st)
                        : dispatch<256>(mode, M, N, K, a, b, C, err, st);
     unsigned int h = 0;

@@ -336,39 +336,66 @@ void pick_tile(int W, int H, int* TW, int* TH)
     }
 }
 
-template <int BN, class EP>
+template <int BN, int SW, class EP>
 cudaError_t conv_tma_bn(neurosim_interp* h, const bf16* buf, int cstride, int off, int C, int flip, int N, int H,
                         int W, const bf16* wpacked, int n_out, const EP& ep)
 {
+    constexpr int BKS = utma::bk_of(SW);
     int TW = 128, TH = 1;
     pick_tile(W, H, &TW, &TH);
     utma::TmaArgs<utma::ConvTapA, EP> g;
     const cuuint64_t dims[4] = {(cuuint64_t)cstride, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
     const cuuint64_t strides[3] = {(cuuint64_t)cstride * 2u, (cuuint64_t)W * cstride * 2u,
                                    (cuuint64_t)H * W * cstride * 2u};
-    const cuuint32_t box[4] = {(cuuint32_t)utma::BK, (cuuint32_t)TW, (cuuint32_t)TH, 1u};
-    if (!utma::encode_tiled(&g.ta, 4, buf, dims, strides, box) ||
-        !utma::encode_kmajor(&g.tb, wpacked, n_out, 9 * C, BN))
+    const cuuint32_t box[4] = {(cuuint32_t)BKS, (cuuint32_t)TW, (cuuint32_t)TH, 1u};
+    if (!utma::encode_tiled(&g.ta, 4, buf, dims, strides, box, SW) ||
+        !utma::encode_kmajor(&g.tb, wpacked, n_out, 9 * C, BN, SW))
         return cudaErrorInvalidValue;
     const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH;
-    g.a = utma::ConvTapA{C, off, flip, W, H, N, TW, TH, tx, ty};
+    g.a = utma::ConvTapA{C, off, flip, W, H, N, TW, TH, tx, ty, BKS};
     g.ep = ep;
     g.N = n_out;
     g.err = h->err;
     g.limit_ns = 2000000000ull;
     h->launches += 1;
-    return utma::launch_tma_gemm<BN>(g, N * tx * ty, h->stream);
+    return utma::launch_tma_gemm<BN, SW>(g, N * tx * ty, h->stream);
 }
 
 // out = conv3x3 (stride 1) of the view [off, off + C) of `buf`; flip = 1 for
-// the data gradient (taps mirrored).  C must be a multiple of 64.
+// the data gradient (taps mirrored).  C must be a multiple of 64 (128-byte
+// swizzle) or equal 32 (64-byte swizzle).
 template <class EP>
 cudaError_t conv_tma(neurosim_interp* h, const bf16* buf, int cstride, int off, int C, int flip, int N, int H, int W,
                      const bf16* wpacked, int n_out, const EP& ep)
 {
-    if (n_out <= 32) return conv_tma_bn<32>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
-    if (n_out <= 64) return conv_tma_bn<64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
-    return conv_tma_bn<128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+    if (C == 32) {
+        if (n_out <= 32) return conv_tma_bn<32, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+        if (n_out <= 64) return conv_tma_bn<64, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+        return conv_tma_bn<128, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+    }
+    if (n_out <= 32) return conv_tma_bn<32, 128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+    if (n_out <= 64) return conv_tma_bn<64, 128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+    return conv_tma_bn<128, 128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+}
+
+// out[P][n_out] = view [off, off + C) of the rows of a [P][cstride] buffer
+// times the packed [n_out][C] weights (1x1 layers, transposed-conv
+// forward).  C: 32 (64-byte swizzle) or a multiple of 64.
+template <int BN, int SW, class EP>
+cudaError_t pix_tma_bn(neurosim_interp* h, const bf16* buf, int cstride, int off, int C, int P, const bf16* wpacked,
+                       int n_out, const EP& ep)
+{
+    utma::TmaArgs<utma::DenseA, EP> g;
+    if (!utma::encode_kmajor(&g.ta, buf, P, cstride, utma::BM, SW, cstride) ||
+        !utma::encode_kmajor(&g.tb, wpacked, n_out, C, BN, SW))
+        return cudaErrorInvalidValue;
+    g.a = utma::DenseA{P, C, off, utma::bk_of(SW)};
+    g.ep = ep;
+    g.N = n_out;
+    g.err = h->err;
+    g.limit_ns = 2000000000ull;
+    h->launches += 1;
+    return utma::launch_tma_gemm<BN, SW>(g, (P + utma::BM - 1) / utma::BM, h->stream);
 }
 
 struct Shape {
@@ -421,18 +448,17 @@ int forward(neurosim_interp* h, const Shape& s, const float* L0, const float* L4
     // e4
     ICUDA(conv_tma(h, h->e3, 128, 0, 128, 0, N, H4, W4, h->wf[3], 128, EpiAct{h->e4, 128, 0, bias_of(h, 3), 1}));
     // u1 -> cat2[:, 0:64]
-    ICUDA(gemm(h, PixK{act(h->e4, N, H4, W4, 128, 0), s.P4}, ugemm::DenseK{h->wf[4], 256, 128},
-               EpiConvT{h->cat2, 128, 0, bias_of(h, 4), 64, H4, W4}, s.P4, 256, 128, false));
+    ICUDA((pix_tma_bn<256, 128>(h, h->e4, 128, 0, 128, s.P4, h->wf[4], 256,
+                                 EpiConvT{h->cat2, 128, 0, bias_of(h, 4), 64, H4, W4})));
     // d1
     ICUDA(conv_tma(h, h->cat2, 128, 0, 128, 0, N, H2, W2, h->wf[5], 64, EpiAct{h->d1, 64, 0, bias_of(h, 5), 1}));
     // u2 -> cat1[:, 0:32]
-    ICUDA(gemm(h, PixK{act(h->d1, N, H2, W2, 64, 0), s.P2}, ugemm::DenseK{h->wf[6], 128, 64},
-               EpiConvT{h->cat1, 64, 0, bias_of(h, 6), 32, H2, W2}, s.P2, 128, 64, false));
+    ICUDA((pix_tma_bn<128, 128>(h, h->d1, 64, 0, 64, s.P2, h->wf[6], 128,
+                                 EpiConvT{h->cat1, 64, 0, bias_of(h, 6), 32, H2, W2})));
     // d2
     ICUDA(conv_tma(h, h->cat1, 64, 0, 64, 0, N, H, W, h->wf[7], 32, EpiAct{h->d2, 32, 0, bias_of(h, 7), 1}));
     // frames
-    ICUDA(gemm(h, PixK{act(h->d2, N, H, W, 32, 0), s.P}, ugemm::DenseK{h->wf[8], 16, 32},
-               EpiOut{h->out, h->l0, h->l4, bias_of(h, 8), s.P}, s.P, 16, 32, false));
+    ICUDA((pix_tma_bn<16, 64>(h, h->d2, 32, 0, 32, s.P, h->wf[8], 16, EpiOut{h->out, h->l0, h->l4, bias_of(h, 8), s.P})));
     return NEUROSIM_OK;
 }
 
@@ -465,8 +491,7 @@ int backward(neurosim_interp* h, const Shape& s)
     ICUDA(gemm(h, Im2colMN{act(h->cat1, N, H, W, 64, 0), 64, H, W, 1, 576, s.P}, PixMN{act(h->gd2, N, H, W, 32, 0), 32, s.P},
                EpiDW{G + L.w_off[7], 32}, 576, 32, s.P, true));
     if ((rc = bias_grad(h, h->gd2, s.P, 32, 0, 32, 7))) return rc;
-    ICUDA(gemm(h, conv3tk(act(h->gd2, N, H, W, 32, 0), 32, H, W, 1, s.P), ugemm::DenseK{h->wb[7], 64, 288},
-               EpiGrad{h->gcat1, 64, 0, h->cat1, 64, 0, 32, 0}, s.P, 64, 288, false));
+    ICUDA(conv_tma(h, h->gd2, 32, 0, 32, 1, N, H, W, h->wb[7], 64, EpiGrad{h->gcat1, 64, 0, h->cat1, 64, 0, 32, 0}));
     // ---- convT2 (d1 -> u2): W7, b7, d(d1)
     ICUDA(gemm(h, PixMN{act(h->d1, N, H2, W2, 64, 0), 64, s.P2}, S2DMN{act(h->gcat1, N, H, W, 64, 0), 32, H2, W2, 128, s.P2},
                EpiDW{G + L.w_off[6], 128}, 64, 128, s.P2, true));

@@ -22,15 +22,17 @@
 namespace utma {
 
 constexpr int BM = 128;
-constexpr int BK = 64;           // one 128-byte swizzle row of BF16
+constexpr int BK = 64;           // K of one 128-byte swizzle row of BF16
 constexpr int STAGES = 4;
+// K of one stage for a swizzle width SW (bytes): one swizzle row of BF16
+__host__ __device__ constexpr int bk_of(int SW) { return SW / 2; }
 constexpr uint32_t kErrTimeout = 1u;
 
 // ---- host: tensor maps (driver entry point looked up through the runtime) -------------
-// BF16 tiled map with 128-byte swizzle and zero fill outside the tensor;
-// strides_bytes has rank - 1 entries (dimension 0 is contiguous).
+// BF16 tiled map with a 128- or 64-byte swizzle and zero fill outside the
+// tensor; strides_bytes has rank - 1 entries (dimension 0 is contiguous).
 inline bool encode_tiled(CUtensorMap* map, int rank, const void* base, const cuuint64_t* dims,
-                         const cuuint64_t* strides_bytes, const cuuint32_t* box)
+                         const cuuint64_t* strides_bytes, const cuuint32_t* box, int swizzle = 128)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -43,17 +45,20 @@ inline bool encode_tiled(CUtensorMap* map, int rank, const void* base, const cuu
     }
     const cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), dims, strides_bytes,
-              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              swizzle == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Packed K-major BF16 matrix [rows][K] as a 2-D map, box (64, box_rows).
-inline bool encode_kmajor(CUtensorMap* map, const void* base, int rows, int K, int box_rows)
+// K-major BF16 matrix [rows][ld] (K = the first `K` columns) as a 2-D map,
+// box (SW / 2, box_rows).
+inline bool encode_kmajor(CUtensorMap* map, const void* base, int rows, int K, int box_rows, int swizzle = 128,
+                          int ld = 0)
 {
     const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)K * 2u};
-    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
-    return encode_tiled(map, 2, base, dims, strides, box);
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld ? ld : K) * 2u};
+    const cuuint32_t box[2] = {(cuuint32_t)bk_of(swizzle), (cuuint32_t)box_rows};
+    return encode_tiled(map, 2, base, dims, strides, box, swizzle);
 }
 
 // ---- device helpers --------------------------------------------------------------------
@@ -80,24 +85,28 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
            "r"(umma::smem_u32(mbar)) : "memory");
 }
 
-// K-major operand in the 128-byte swizzle layout written by TMA: rows of
-// 128 B (64 BF16 of K), 8-row atoms of 1024 B; k-step s (K = 16) starts
-// 32 B further inside the row.  Layout type 2 = SWIZZLE_128B.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr, int s)
+// K-major operand in the swizzled layout written by TMA: rows of SW bytes
+// (SW / 2 BF16 of K), 8-row atoms of 8 SW bytes; k-step s (K = 16) starts
+// 32 B further inside the row.  Layout type 2 = SWIZZLE_128B, 4 = SWIZZLE_64B.
+template <int SW>
+__device__ __forceinline__ uint64_t desc_sw(uint32_t saddr, int s)
 {
-    uint64_t d = umma::smem_desc(saddr + (uint32_t)s * 32u, 16u, 1024u);
-    d |= (uint64_t)2u << 61;
+    static_assert(SW == 128 || SW == 64, "128- or 64-byte swizzle");
+    uint64_t d = umma::smem_desc(saddr + (uint32_t)s * 32u, 16u, 8u * SW);
+    d |= (uint64_t)(SW == 128 ? 2u : 4u) << 61;
     return d;
 }
 
 // ---- A loaders ---------------------------------------------------------------------------
-// Dense row-major A [M][K]: 2-D map (K, M), box (64, 128).
+// Row-major A: row m is K values starting at column `off` of a [M][ld]
+// matrix (a dense matrix, or the pixels x channels view of an NHWC buffer);
+// 2-D map (ld, M), box (bk, 128).
 struct DenseA {
-    int M, K;
-    __device__ __forceinline__ int n_kt() const { return (K + BK - 1) / BK; }
+    int M, K, off, bk;
+    __device__ __forceinline__ int n_kt() const { return (K + bk - 1) / bk; }
     __device__ __forceinline__ void load(void* dst, const CUtensorMap* map, int tile, int kt, uint64_t* mbar) const
     {
-        tma_load_2d(dst, map, kt * BK, tile * BM, mbar);
+        tma_load_2d(dst, map, off + kt * bk, tile * BM, mbar);
     }
     __device__ __forceinline__ int row_of(int tile, int r) const
     {
@@ -115,7 +124,8 @@ struct ConvTapA {
     int C, off, flip;
     int W, H, N;          // image size (input = output size at stride 1)
     int TW, TH, tiles_x, tiles_y;
-    __device__ __forceinline__ int n_kt() const { return 9 * (C / BK); }
+    int bk;               // channels per K tile (the swizzle row)
+    __device__ __forceinline__ int n_kt() const { return 9 * (C / bk); }
     __device__ __forceinline__ void origin(int tile, int& n, int& x0, int& y0) const
     {
         const int per = tiles_x * tiles_y;
@@ -129,8 +139,8 @@ struct ConvTapA {
     {
         int n, x0, y0;
         origin(tile, n, x0, y0);
-        const int cc = C / BK;
-        const int tap = kt / cc, c = off + (kt - tap * cc) * BK;
+        const int cc = C / bk;
+        const int tap = kt / cc, c = off + (kt - tap * cc) * bk;
         const int dy = tap / 3 - 1, dx = tap % 3 - 1;
         tma_load_4d(dst, map, c, flip ? x0 - dx : x0 + dx, flip ? y0 - dy : y0 + dy, n, mbar);
     }
@@ -154,18 +164,19 @@ struct TmaArgs {
     uint64_t limit_ns;
 };
 
-template <int BN>
+template <int BN, int SW = 128>
 __host__ __device__ constexpr size_t tma_smem_bytes()
 {
-    return 1024 + (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 256;
+    return 1024 + (size_t)STAGES * (BM * SW + BN * SW) + 256;
 }
 
-template <int BN, class AL, class EP>
+template <int BN, int SW, class AL, class EP>
 __global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ TmaArgs<AL, EP> g)
 {
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "tcgen05 N for M = 128");
     constexpr uint32_t TCOLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
-    constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+    constexpr int SBK = bk_of(SW);
+    constexpr uint32_t A_BYTES = BM * SW, B_BYTES = BN * SW;
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte alignment of the swizzled tiles
     unsigned char* smem = smem_raw + ((1024u - (umma::smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -208,7 +219,7 @@ __global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ T
             }
             mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
             g.a.load(sA + s * A_BYTES, &g.ta, tile, kt, &full[s]);
-            tma_load_2d(sB + s * B_BYTES, &g.tb, kt * BK, 0, &full[s]);
+            tma_load_2d(sB + s * B_BYTES, &g.tb, kt * SBK, 0, &full[s]);
         }
     } else if (tid == 32) {
         // MMA issuer
@@ -221,8 +232,8 @@ __global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ T
             umma::fence_after_sync();
             const uint32_t a0 = umma::smem_u32(sA + s * A_BYTES), b0 = umma::smem_u32(sB + s * B_BYTES);
 #pragma unroll
-            for (int k = 0; k < BK / 16; ++k)
-                umma::mma_bf16(tmem, desc_sw128(a0, k), desc_sw128(b0, k), idesc, (kt > 0 || k > 0) ? 1u : 0u);
+            for (int k = 0; k < SBK / 16; ++k)
+                umma::mma_bf16(tmem, desc_sw<SW>(a0, k), desc_sw<SW>(b0, k), idesc, (kt > 0 || k > 0) ? 1u : 0u);
             umma::mma_commit(&empty[s]);
         }
         umma::mma_commit(done);
@@ -248,14 +259,14 @@ __global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ T
     if (warp == 0) umma::tmem_dealloc(tmem, TCOLS);
 }
 
-template <int BN, class AL, class EP>
+template <int BN, int SW, class AL, class EP>
 cudaError_t launch_tma_gemm(const TmaArgs<AL, EP>& g, int tiles, cudaStream_t stream)
 {
-    const size_t smem = tma_smem_bytes<BN>();
-    cudaError_t e = cudaFuncSetAttribute(tma_gemm_kernel<BN, AL, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const size_t smem = tma_smem_bytes<BN, SW>();
+    cudaError_t e = cudaFuncSetAttribute(tma_gemm_kernel<BN, SW, AL, EP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    tma_gemm_kernel<BN, AL, EP><<<tiles, 128, smem, stream>>>(g);
+    tma_gemm_kernel<BN, SW, AL, EP><<<tiles, 128, smem, stream>>>(g);
     return cudaGetLastError();
 }
 
