@@ -295,7 +295,7 @@ def run_ours(args):
         host_frames_rev = frames_rev.cpu().pin_memory()
         del frames, frames_rev
         torch.cuda.empty_cache()
-        host_out = np.empty(cap, np.uint64)
+        host_out = torch.empty(max(1 << 20, int(ev_per_step * 1.5)), dtype=torch.int64).pin_memory()
         sim2 = EventSim(W, H, **wl["sim"], max_frames_per_step=T)
         d2h = 0
 
@@ -303,10 +303,10 @@ def run_ours(args):
             nonlocal host_out
             sim2.step_host(host_frames if kk % 2 == 0 else host_frames_rev, kk * span, DT)
             n, _ = sim2.pending()
-            if n > host_out.size:
-                host_out = np.empty(int(n * 1.25), np.uint64)
-            ev, _ = sim2.drain(to="cpu")
-            return ev.nbytes
+            if n > host_out.numel():
+                host_out = torch.empty(int(n * 1.25), dtype=torch.int64).pin_memory()
+            ev, _ = sim2.drain(to="cpu", out=host_out)
+            return ev.numel() * 8
 
         for kk in range(min(args.warmup, 2)):
             e2e_step(kk)

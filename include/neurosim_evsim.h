@@ -109,10 +109,14 @@ int neurosim_evsim_create(const neurosim_evsim_params *p, void *cuda_stream,
 int neurosim_evsim_step(neurosim_evsim *h, const float *frames_dev, int32_t n_frames,
                         int64_t t0_us, int32_t dt_us);
 
-/* As neurosim_evsim_step, but `frames_host` is HOST memory (pinned for best
- * speed): the frames are copied to a library-owned device buffer on the
- * handle's stream before the step.  The host frames must stay valid until
- * the next successful drain (replay on overflow). */
+/* As neurosim_evsim_step, but `frames_host` is HOST memory holding n_frames
+ * frames.  Page-locked memory that is mapped into the device's address space
+ * (cudaHostAlloc / cudaHostRegister memory on a system with unified
+ * addressing) is read in place by the emission kernel: each frame crosses the
+ * host link once, while the step runs.  Other host memory is first copied to
+ * a library-owned device buffer on the handle's stream.  The host frames must
+ * stay valid and unchanged until the next successful drain (replay on
+ * overflow). */
 int neurosim_evsim_step_host(neurosim_evsim *h, const float *frames_host, int32_t n_frames,
                              int64_t t0_us, int32_t dt_us);
 

@@ -373,6 +373,25 @@ int upload_host_frames(neurosim_evsim* h, const float* frames_host, int32_t T)
     return NEUROSIM_OK;
 }
 
+// Device address from which the step reads host frames.  Page-locked host
+// memory mapped into the device's address space is read in place by the
+// emission kernel (each frame crosses the host link once, while the kernel
+// runs); any other host memory is first copied to the staging buffer.
+int host_frames_for_step(neurosim_evsim* h, const float* frames_host, int32_t T, const float** out)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, frames_host) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+        a.devicePointer != nullptr) {
+        *out = static_cast<const float*>(a.devicePointer);
+        return NEUROSIM_OK;
+    }
+    (void)cudaGetLastError();
+    const int rc = upload_host_frames(h, frames_host, T);
+    if (rc) return rc;
+    *out = h->staging;
+    return NEUROSIM_OK;
+}
+
 int read_ctl(neurosim_evsim* h, Ctl* c)
 {
     CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -409,9 +428,8 @@ int resolve(neurosim_evsim* h, Ctl* c)
         for (const StepRec& s : steps) {
             const float* fr = s.frames;
             if (s.host) {
-                rc = upload_host_frames(h, s.frames, s.T);
+                rc = host_frames_for_step(h, s.frames, s.T, &fr);
                 if (rc) return rc;
-                fr = h->staging;
             }
             rc = enqueue_step(h, fr, s.T, s.t0, s.dt);
             if (rc) return rc;
@@ -559,9 +577,10 @@ int neurosim_evsim_step_host(neurosim_evsim* h, const float* frames_host, int32_
     if (!frames_host) return fail(NEUROSIM_E_INVALID, "frames_host is NULL");
     DeviceGuard g(h->device);
     if (!g.ok) return fail(NEUROSIM_E_CUDA, "cannot select the handle's device");
-    rc = upload_host_frames(h, frames_host, n_frames);
+    const float* fr = nullptr;
+    rc = host_frames_for_step(h, frames_host, n_frames, &fr);
     if (rc) return rc;
-    rc = enqueue_step(h, h->staging, n_frames, t0_us, dt_us);
+    rc = enqueue_step(h, fr, n_frames, t0_us, dt_us);
     if (rc) return rc;
     h->pending.push_back(StepRec{frames_host, true, n_frames, t0_us, dt_us});
     return NEUROSIM_OK;

@@ -338,21 +338,25 @@ void pick_tile(int W, int H, int* TW, int* TH)
 
 template <int BN, int SW, class EP>
 cudaError_t conv_tma_bn(neurosim_interp* h, const bf16* buf, int cstride, int off, int C, int flip, int N, int H,
-                        int W, const bf16* wpacked, int n_out, const EP& ep)
+                        int W, const bf16* wpacked, int n_out, const EP& ep, int stride)
 {
     constexpr int BKS = utma::bk_of(SW);
+    if (stride != 1 && (stride != 2 || flip)) return cudaErrorInvalidValue;
     int TW = 128, TH = 1;
     pick_tile(W, H, &TW, &TH);
     utma::TmaArgs<utma::ConvTapA, EP> g;
-    const cuuint64_t dims[4] = {(cuuint64_t)cstride, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
-    const cuuint64_t strides[3] = {(cuuint64_t)cstride * 2u, (cuuint64_t)W * cstride * 2u,
-                                   (cuuint64_t)H * W * cstride * 2u};
-    const cuuint32_t box[4] = {(cuuint32_t)BKS, (cuuint32_t)TW, (cuuint32_t)TH, 1u};
-    if (!utma::encode_tiled(&g.ta, 4, buf, dims, strides, box, SW) ||
+    // the input is stride x the output size
+    const int Wi = stride * W, Hi = stride * H;
+    const cuuint64_t dims[4] = {(cuuint64_t)cstride, (cuuint64_t)Wi, (cuuint64_t)Hi, (cuuint64_t)N};
+    const cuuint64_t strides[3] = {(cuuint64_t)cstride * 2u, (cuuint64_t)Wi * cstride * 2u,
+                                   (cuuint64_t)Hi * Wi * cstride * 2u};
+    const cuuint32_t box[4] = {(cuuint32_t)BKS, (cuuint32_t)(stride * TW), (cuuint32_t)(stride * TH), 1u};
+    const cuuint32_t estr[4] = {1u, (cuuint32_t)stride, (cuuint32_t)stride, 1u};
+    if (!utma::encode_tiled(&g.ta, 4, buf, dims, strides, box, SW, estr) ||
         !utma::encode_kmajor(&g.tb, wpacked, n_out, 9 * C, BN, SW))
         return cudaErrorInvalidValue;
     const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH;
-    g.a = utma::ConvTapA{C, off, flip, W, H, N, TW, TH, tx, ty, BKS};
+    g.a = utma::ConvTapA{C, off, flip, W, H, N, TW, TH, tx, ty, BKS, stride};
     g.ep = ep;
     g.N = n_out;
     g.err = h->err;
@@ -361,21 +365,22 @@ cudaError_t conv_tma_bn(neurosim_interp* h, const bf16* buf, int cstride, int of
     return utma::launch_tma_gemm<BN, SW>(g, N * tx * ty, h->stream);
 }
 
-// out = conv3x3 (stride 1) of the view [off, off + C) of `buf`; flip = 1 for
-// the data gradient (taps mirrored).  C must be a multiple of 64 (128-byte
+// out (H x W) = conv3x3 with padding 1 and the given stride of the view
+// [off, off + C) of `buf` (stride H x stride W); flip = 1 for the data
+// gradient (taps mirrored, stride 1).  C must be a multiple of 64 (128-byte
 // swizzle) or equal 32 (64-byte swizzle).
 template <class EP>
 cudaError_t conv_tma(neurosim_interp* h, const bf16* buf, int cstride, int off, int C, int flip, int N, int H, int W,
-                     const bf16* wpacked, int n_out, const EP& ep)
+                     const bf16* wpacked, int n_out, const EP& ep, int stride = 1)
 {
     if (C == 32) {
-        if (n_out <= 32) return conv_tma_bn<32, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
-        if (n_out <= 64) return conv_tma_bn<64, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
-        return conv_tma_bn<128, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+        if (n_out <= 32) return conv_tma_bn<32, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep, stride);
+        if (n_out <= 64) return conv_tma_bn<64, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep, stride);
+        return conv_tma_bn<128, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep, stride);
     }
-    if (n_out <= 32) return conv_tma_bn<32, 128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
-    if (n_out <= 64) return conv_tma_bn<64, 128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
-    return conv_tma_bn<128, 128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+    if (n_out <= 32) return conv_tma_bn<32, 128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep, stride);
+    if (n_out <= 64) return conv_tma_bn<64, 128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep, stride);
+    return conv_tma_bn<128, 128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep, stride);
 }
 
 // out[P][n_out] = view [off, off + C) of the rows of a [P][cstride] buffer
@@ -440,11 +445,9 @@ int forward(neurosim_interp* h, const Shape& s, const float* L0, const float* L4
     ICUDA(gemm(h, conv3k(act(h->x0, N, H, W, 8, 0), 8, H, W, 1, s.P), ugemm::DenseK{h->wf[0], 32, 72},
                EpiAct{h->cat1, 64, 32, bias_of(h, 0), 1}, s.P, 32, 72, false));
     // e2 -> cat2[:, 64:128]
-    ICUDA(gemm(h, conv3k(act(h->cat1, N, H, W, 64, 32), 32, H2, W2, 2, s.P2), ugemm::DenseK{h->wf[1], 64, 288},
-               EpiAct{h->cat2, 128, 64, bias_of(h, 1), 1}, s.P2, 64, 288, false));
+    ICUDA(conv_tma(h, h->cat1, 64, 32, 32, 0, N, H2, W2, h->wf[1], 64, EpiAct{h->cat2, 128, 64, bias_of(h, 1), 1}, 2));
     // e3
-    ICUDA(gemm(h, conv3k(act(h->cat2, N, H2, W2, 128, 64), 64, H4, W4, 2, s.P4), ugemm::DenseK{h->wf[2], 128, 576},
-               EpiAct{h->e3, 128, 0, bias_of(h, 2), 1}, s.P4, 128, 576, false));
+    ICUDA(conv_tma(h, h->cat2, 128, 64, 64, 0, N, H4, W4, h->wf[2], 128, EpiAct{h->e3, 128, 0, bias_of(h, 2), 1}, 2));
     // e4
     ICUDA(conv_tma(h, h->e3, 128, 0, 128, 0, N, H4, W4, h->wf[3], 128, EpiAct{h->e4, 128, 0, bias_of(h, 3), 1}));
     // u1 -> cat2[:, 0:64]

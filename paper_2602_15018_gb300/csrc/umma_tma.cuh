@@ -31,8 +31,11 @@ constexpr uint32_t kErrTimeout = 1u;
 // ---- host: tensor maps (driver entry point looked up through the runtime) -------------
 // BF16 tiled map with a 128- or 64-byte swizzle and zero fill outside the
 // tensor; strides_bytes has rank - 1 entries (dimension 0 is contiguous).
+// elem_strides (optional, rank entries): traversal stride per dimension; a
+// box then holds box[i] / elem_strides[i] elements along dimension i.
 inline bool encode_tiled(CUtensorMap* map, int rank, const void* base, const cuuint64_t* dims,
-                         const cuuint64_t* strides_bytes, const cuuint32_t* box, int swizzle = 128)
+                         const cuuint64_t* strides_bytes, const cuuint32_t* box, int swizzle = 128,
+                         const cuuint32_t* elem_strides = nullptr)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -43,9 +46,9 @@ inline bool encode_tiled(CUtensorMap* map, int rank, const void* base, const cuu
             return false;
         fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     }
-    const cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
+    const cuuint32_t ones[5] = {1u, 1u, 1u, 1u, 1u};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), dims, strides_bytes,
-              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              box, elem_strides ? elem_strides : ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
               swizzle == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -103,7 +106,7 @@ __device__ __forceinline__ uint64_t desc_sw(uint32_t saddr, int s)
 // 2-D map (ld, M), box (bk, 128).
 struct DenseA {
     int M, K, off, bk;
-    __device__ __forceinline__ int n_kt() const { return (K + bk - 1) / bk; }
+    __host__ __device__ __forceinline__ int n_kt() const { return (K + bk - 1) / bk; }
     __device__ __forceinline__ void load(void* dst, const CUtensorMap* map, int tile, int kt, uint64_t* mbar) const
     {
         tma_load_2d(dst, map, off + kt * bk, tile * BM, mbar);
@@ -115,17 +118,20 @@ struct DenseA {
     }
 };
 
-// 3 x 3 stride-1 convolution over NHWC activations (4-D map: channels of
-// the buffer, W, H, N; box 64 x TW x TH x 1).  Output tile = TW x TH pixels of
-// one image; K tile = (tap, 64-channel chunk) of the view [off, off + C).
-// flip = 0: out(y, x) reads in(y + dy - 1, x + dx - 1)          (forward)
-// flip = 1: out(y, x) reads g(y + 1 - dy, x + 1 - dx)           (data gradient)
+// 3 x 3 convolution with padding 1 over NHWC activations (4-D map: channels
+// of the buffer, W, H, N of the input; box bk x s TW x s TH x 1 with traversal
+// stride s in W and H, so that one box holds TW x TH pixels).  Output tile =
+// TW x TH pixels of one image; K tile = (tap, bk-channel chunk) of the view
+// [off, off + C).
+// flip = 0: out(y, x) reads in(s y + dy - 1, s x + dx - 1)      (forward)
+// flip = 1: out(y, x) reads g(y + 1 - dy, x + 1 - dx), s = 1    (data gradient)
 struct ConvTapA {
     int C, off, flip;
-    int W, H, N;          // image size (input = output size at stride 1)
+    int W, H, N;          // output size
     int TW, TH, tiles_x, tiles_y;
     int bk;               // channels per K tile (the swizzle row)
-    __device__ __forceinline__ int n_kt() const { return 9 * (C / bk); }
+    int stride;           // 1 or 2
+    __host__ __device__ __forceinline__ int n_kt() const { return 9 * (C / bk); }
     __device__ __forceinline__ void origin(int tile, int& n, int& x0, int& y0) const
     {
         const int per = tiles_x * tiles_y;
@@ -142,7 +148,7 @@ struct ConvTapA {
         const int cc = C / bk;
         const int tap = kt / cc, c = off + (kt - tap * cc) * bk;
         const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        tma_load_4d(dst, map, c, flip ? x0 - dx : x0 + dx, flip ? y0 - dy : y0 + dy, n, mbar);
+        tma_load_4d(dst, map, c, flip ? x0 - dx : stride * x0 + dx, flip ? y0 - dy : stride * y0 + dy, n, mbar);
     }
     __device__ __forceinline__ int row_of(int tile, int r) const
     {
@@ -164,10 +170,11 @@ struct TmaArgs {
     uint64_t limit_ns;
 };
 
+// Dynamic shared memory of a launch with `ns` pipeline stages.
 template <int BN, int SW = 128>
-__host__ __device__ constexpr size_t tma_smem_bytes()
+__host__ __device__ constexpr size_t tma_smem_bytes(int ns = STAGES)
 {
-    return 1024 + (size_t)STAGES * (BM * SW + BN * SW) + 256;
+    return 1024 + (size_t)ns * (BM * SW + BN * SW) + 256;
 }
 
 template <int BN, int SW, class AL, class EP>
@@ -180,18 +187,20 @@ __global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ T
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte alignment of the swizzled tiles
     unsigned char* smem = smem_raw + ((1024u - (umma::smem_u32(smem_raw) & 1023u)) & 1023u);
-    unsigned char* sA = smem;
-    unsigned char* sB = smem + STAGES * A_BYTES;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
-    uint64_t* empty = full + STAGES;
-    uint64_t* done = empty + STAGES;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int tile = blockIdx.x;
     const int n_kt = g.a.n_kt();
+    // stages in use: no more than the K tiles (the launch sized the shared memory so)
+    const int ns = n_kt < STAGES ? (n_kt > 0 ? n_kt : 1) : STAGES;
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + ns * A_BYTES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + ns * B_BYTES);
+    uint64_t* empty = full + ns;
+    uint64_t* done = empty + ns;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
 
     if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < ns; ++s) {
             umma::mbar_init(&full[s], 1);
             umma::mbar_init(&empty[s], 1);
         }
@@ -211,9 +220,9 @@ __global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ T
     if (tid == 0) {
         // producer: TMA loads of A and B, one stage ahead of the tensor core
         for (int kt = 0; kt < n_kt; ++kt) {
-            const int s = kt % STAGES;
-            if (kt >= STAGES &&
-                !umma::mbar_wait(&empty[s], (uint32_t)((kt / STAGES - 1) & 1), g.limit_ns)) {
+            const int s = kt % ns;
+            if (kt >= ns &&
+                !umma::mbar_wait(&empty[s], (uint32_t)((kt / ns - 1) & 1), g.limit_ns)) {
                 atomicOr(&s_fail, 1u);
                 break;
             }
@@ -224,8 +233,8 @@ __global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ T
     } else if (tid == 32) {
         // MMA issuer
         for (int kt = 0; kt < n_kt; ++kt) {
-            const int s = kt % STAGES;
-            if (!umma::mbar_wait(&full[s], (uint32_t)((kt / STAGES) & 1), g.limit_ns)) {
+            const int s = kt % ns;
+            if (!umma::mbar_wait(&full[s], (uint32_t)((kt / ns) & 1), g.limit_ns)) {
                 atomicOr(&s_fail, 1u);
                 break;
             }
@@ -262,11 +271,12 @@ __global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ T
 template <int BN, int SW, class AL, class EP>
 cudaError_t launch_tma_gemm(const TmaArgs<AL, EP>& g, int tiles, cudaStream_t stream)
 {
-    const size_t smem = tma_smem_bytes<BN, SW>();
+    const int n_kt = g.a.n_kt();
+    const int ns = n_kt < STAGES ? (n_kt > 0 ? n_kt : 1) : STAGES;
     cudaError_t e = cudaFuncSetAttribute(tma_gemm_kernel<BN, SW, AL, EP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes<BN, SW>());
     if (e != cudaSuccess) return e;
-    tma_gemm_kernel<BN, SW, AL, EP><<<tiles, 128, smem, stream>>>(g);
+    tma_gemm_kernel<BN, SW, AL, EP><<<tiles, 128, tma_smem_bytes<BN, SW>(ns), stream>>>(g);
     return cudaGetLastError();
 }
 

@@ -122,9 +122,11 @@ class EventSim:
     def drain(self, to: str = "cpu", out: torch.Tensor | None = None):
         """Returns (events, seg_offsets).
 
-        to="cpu": events as a numpy uint64 array; to="cuda": an int64 CUDA tensor
-        holding the same 64-bit records (or `out`, a preallocated int64 CUDA
-        tensor, sliced to the count)."""
+        to="cpu": events as a numpy uint64 array (or `out`, a preallocated
+        host buffer -- a numpy uint64 array or a 64-bit CPU tensor, pinned for
+        the fastest copy -- sliced to the count); to="cuda": an int64 CUDA
+        tensor holding the same 64-bit records (or `out`, a preallocated int64
+        CUDA tensor, sliced to the count)."""
         n_ev, n_seg = self.pending()
         seg = np.zeros(n_seg + 1, np.int64)
         n_out, n_segs = C.c_uint64(0), C.c_int64(0)
@@ -137,11 +139,19 @@ class EventSim:
                 seg.size, C.byref(n_segs)))
             ev = out[: n_out.value]
         else:
-            buf = np.empty(max(n_ev, 1), np.uint64)
+            if out is None:
+                out = np.empty(max(n_ev, 1), np.uint64)
+            if isinstance(out, torch.Tensor):
+                if out.is_cuda or out.element_size() != 8 or not out.is_contiguous():
+                    raise ValueError("out must be a contiguous 64-bit CPU tensor")
+                ptr, size = out.data_ptr(), out.numel()
+            else:
+                if out.dtype != np.uint64 or not out.flags["C_CONTIGUOUS"]:
+                    raise ValueError("out must be a C-contiguous uint64 array")
+                ptr, size = out.ctypes.data, out.size
             check(lib().neurosim_evsim_drain_events(
-                self._h, C.c_void_p(buf.ctypes.data), buf.size, 0, C.byref(n_out), segp,
-                seg.size, C.byref(n_segs)))
-            ev = buf[: n_out.value]
+                self._h, C.c_void_p(ptr), size, 0, C.byref(n_out), segp, seg.size, C.byref(n_segs)))
+            ev = out[: n_out.value]
         self._keep = []
         return ev, seg
 

@@ -186,6 +186,24 @@ def test_multi_step_gaps_host_and_device_drain():
     g.close()
 
 
+def test_pinned_host_frames_read_in_place_and_replayed():
+    """Pinned host frames (read in place by the emission kernel) and pageable
+    ones (copied to the staging buffer) give the oracle's events, also when an
+    overflow makes the drain replay both steps from the host frames."""
+    W, H, T = 240, 180, 40
+    fr = scenes.render_frames(scenes.SinusoidScene(W, H, seed=5), T)
+    g, o = _sims(W, H, c_pos=0.2, c_neg=0.2, max_frames_per_step=T, event_capacity=1000)
+    pinned = fr[:20].contiguous().pin_memory()
+    g.step_host(pinned, 0, DT)
+    g.step_host(np.ascontiguousarray(fr[20:].numpy()), 20 * DT, DT)
+    host_out = torch.empty(1 << 20, dtype=torch.int64).pin_memory()
+    ev, seg = g.drain(to="cpu", out=host_out)
+    rev, rseg = o.step(fr.numpy(), 0, DT)
+    assert_same(ev.numpy().view(np.uint64), seg, rev, rseg, "host frames")
+    _check_state(g, o)
+    g.close()
+
+
 def test_overflow_regrowth_is_exact():
     """A tiny initial capacity must regrow and replay without changing a bit."""
     W, H, T = 240, 180, 60
