@@ -240,13 +240,23 @@ struct RecordSink {        // final pass: packed 64-bit records
     int W;
     int tshift;
     uint32_t pixmask;
+    float invW;            // fl(1 / W)
     template <typename KeyT>
     __device__ __forceinline__ void put(uint32_t pos, KeyT key) const
     {
         const uint32_t toff = (uint32_t)(key >> tshift);
         const uint32_t pix = (uint32_t)(key >> 1) & pixmask;
-        const uint32_t y = pix / (uint32_t)W;
-        const uint32_t x = pix - y * (uint32_t)W;
+        // y = pix / W: pix < 2^23 converts exactly and the product errs by
+        // less than 1, so one correction step makes the quotient exact
+        int y = (int)((float)pix * invW);
+        int x = (int)pix - y * W;
+        if (x < 0) {
+            --y;
+            x += W;
+        } else if (x >= W) {
+            ++y;
+            x -= W;
+        }
         out[pos] = ((uint64_t)(ta + toff) << 32) | ((uint64_t)y << 17) | ((uint64_t)x << 1) |
                    (uint64_t)(key & (KeyT)1);
     }
@@ -258,10 +268,23 @@ struct KeySink {
     __device__ __forceinline__ void put(uint32_t pos, KeyT key) const { p[pos] = key; }
 };
 
+// Lanes of the warp (among `m`) whose digit d (of `bits` bits) equals this
+// lane's: one ballot per digit bit, every lane of the warp taking part.
+__device__ __forceinline__ unsigned digit_peers(uint32_t d, int bits, unsigned m)
+{
+    unsigned peers = m;
+    for (int k = 0; k < bits; ++k) {
+        const bool bit = (d >> k) & 1u;
+        const unsigned b = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? b : ~b;
+    }
+    return peers;
+}
+
 // One stable counting pass of the CTA over [0, N): digit = (key >> shift) & (NB-1).
 // Warp w owns the contiguous range [w N / NW, (w+1) N / NW); inside a warp,
-// groups of 32 consecutive keys are ranked with match_any, so the pass keeps
-// the input order of equal digits.
+// groups of 32 consecutive keys are ranked by their digit peers (lanes below
+// with the same digit), so the pass keeps the input order of equal digits.
 template <int THREADS, typename KeyT, typename Src, typename Sink>
 __device__ __forceinline__ void radix_pass(const Src& src, const Sink& sink, uint32_t N, int shift,
                                            int NB, uint32_t* hist /*[NW][64]*/, uint32_t* binbase)
@@ -274,18 +297,10 @@ __device__ __forceinline__ void radix_pass(const Src& src, const Sink& sink, uin
     for (int d = lane; d < 64; d += 32) h[d] = 0u;
     __syncwarp();
     const uint32_t lt = (1u << lane) - 1u;
-    for (uint32_t g = lo; g < hi; g += 32) {
-        const uint32_t i = g + lane;
-        const bool act = i < hi;
-        const unsigned m = __ballot_sync(0xffffffffu, act);
-        if (act) {
-            const KeyT key = src(i);
-            const uint32_t d = (uint32_t)(key >> shift) & (uint32_t)(NB - 1);
-            const unsigned peers = __match_any_sync(m, d);
-            if ((peers & lt) == 0u) h[d] += (uint32_t)__popc(peers);
-        }
-        __syncwarp();
-    }
+    const int bits = 31 - __clz(NB);
+    // counts of the warp's range (order does not matter here)
+    for (uint32_t i = lo + lane; i < hi; i += 32)
+        atomicAdd(&h[(uint32_t)(src(i) >> shift) & (uint32_t)(NB - 1)], 1u);
     __syncthreads();
     if (tid < NB) {
         uint32_t run = 0;
@@ -324,11 +339,12 @@ __device__ __forceinline__ void radix_pass(const Src& src, const Sink& sink, uin
         const unsigned m = __ballot_sync(0xffffffffu, act);
         KeyT key = 0;
         uint32_t d = 0;
-        unsigned peers = 0;
         if (act) {
             key = src(i);
             d = (uint32_t)(key >> shift) & (uint32_t)(NB - 1);
-            peers = __match_any_sync(m, d);
+        }
+        const unsigned peers = digit_peers(d, bits, m);
+        if (act) {
             const uint32_t pos = binbase[d] + h[d] + (uint32_t)__popc(peers & lt);
             sink.put(pos, key);
         }
@@ -412,18 +428,35 @@ __global__ void __launch_bounds__(kSortThreads) sort_kernel(const __grid_constan
 
         const int tshift = sdp->pix_bits + 1;
         const uint32_t ta = (uint32_t)interval_start(step_ta0(L, *sdp), *sdp, j, L.dt);
-        const RecordSink rsink{L.out + abs0, ta, sdp->W, tshift, (1u << sdp->pix_bits) - 1u};
+        const RecordSink rsink{L.out + abs0, ta, sdp->W, tshift, (1u << sdp->pix_bits) - 1u, 1.0f / (float)sdp->W};
         if (2u * N <= cap) {
             // the interval fits twice in shared memory: copy its chunks (tile
             // order) into one array, then sort between two shared arrays
             KeyT* X = sbuf;
             KeyT* Y = sbuf + N;
             const KeyT* keys = reinterpret_cast<const KeyT*>(L.keys);
-            for (int c = tid; c < nt; c += THREADS) {
-                const KeyT* src = keys + coff[c];
-                KeyT* dst = X + cpre[c];
-                const uint32_t cnt = cpre[c + 1] - cpre[c];
-                for (uint32_t i = 0; i < cnt; ++i) dst[i] = src[i];
+            // chunk of every key (16-bit, in Y until the first pass), then
+            // consecutive threads copy consecutive keys, all of a thread's
+            // loads (up to 16) in flight before its stores
+            uint16_t* owner = reinterpret_cast<uint16_t*>(Y);
+            for (int c = tid; c < nt; c += THREADS)
+                for (uint32_t k = cpre[c]; k < cpre[c + 1]; ++k) owner[k] = (uint16_t)c;
+            __syncthreads();
+            for (uint32_t i0 = tid; i0 < N; i0 += 16 * THREADS) {
+                KeyT v[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const uint32_t i = i0 + u * THREADS;
+                    if (i < N) {
+                        const int c = owner[i];
+                        v[u] = keys[(size_t)coff[c] + (i - cpre[c])];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const uint32_t i = i0 + u * THREADS;
+                    if (i < N) X[i] = v[u];
+                }
             }
             __syncthreads();
             KeyT* cur = X;
