@@ -61,8 +61,9 @@ def render_config2(seed: int = 0, device="cuda", n_frames: int = HD["T"]) -> tor
 # Batched workload: 256 independent sensors, resolutions 346x260 / 640x480 /
 # 1280x720 by index mod 3, texture scenes as the HD workload, per-sensor
 # C+ and C- drawn from U[0.15, 0.35], sigma 0.03, refractory 100 us; steps of
-# 16 frames at 1000 FPS, each a CUDA-graph replay of one batched step.
-BATCH = dict(n=256, sizes=((346, 260), (640, 480), (1280, 720)), T=16)
+# 125 frames at 1000 FPS (a 500-frame clip is 4 steps), each a CUDA-graph
+# replay of one batched step.
+BATCH = dict(n=256, sizes=((346, 260), (640, 480), (1280, 720)), T=125)
 
 
 def batch_sensors(seed: int = 0, n: int = BATCH["n"]):
@@ -98,7 +99,7 @@ WORKLOADS = {
                                  "refractory 100us"),
     "batch": dict(dims=None, sim=None, render=None,
                   name="batched: 256 sensors (346x260 / 640x480 / 1280x720 by index mod 3), "
-                       "16 frames @1000 FPS per step, texture scenes, C+- ~ U[0.15,0.35], "
+                       "125 frames @1000 FPS per step (500-frame clips in 4 steps), texture scenes, C+- ~ U[0.15,0.35], "
                        "sigma 0.03, refractory 100us, one CUDA-graph replay per step"),
 }
 

@@ -365,6 +365,36 @@ cudaError_t conv_tma_bn(neurosim_interp* h, const bf16* buf, int cstride, int of
     return utma::launch_tma_gemm<BN, SW>(g, N * tx * ty, h->stream);
 }
 
+// out = conv3x3 (stride 1) of the view [off, off + C) of `buf` from halo
+// tiles (W a multiple of 128; C 32 with a 64-byte swizzle of the weights, or
+// 64 with a 128-byte swizzle).
+template <int BN, int SW, int SWA, class EP>
+cudaError_t conv_halo_bn(neurosim_interp* h, const bf16* buf, int cstride, int off, int C, int flip, int N, int H,
+                         int W, const bf16* wpacked, int n_out, const EP& ep)
+{
+    utma::HaloArgs<EP> g;
+    const cuuint64_t dims[4] = {(cuuint64_t)cstride, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t strides[3] = {(cuuint64_t)cstride * 2u, (cuuint64_t)W * cstride * 2u,
+                                   (cuuint64_t)H * W * cstride * 2u};
+    const cuuint32_t box[4] = {SWA ? (cuuint32_t)(SWA / 2) : 8u, (cuuint32_t)utma::kHaloW, 3u, 1u};
+    if (!utma::encode_tiled(&g.ta, 4, buf, dims, strides, box, SWA) ||
+        !utma::encode_kmajor(&g.tb, wpacked, n_out, 9 * C, BN, SW))
+        return cudaErrorInvalidValue;
+    g.ep = ep;
+    g.C = C;
+    g.off = off;
+    g.flip = flip;
+    g.W = W;
+    g.H = H;
+    g.N = N;
+    g.n_tiles = N * H * (W / 128);
+    g.n_out = n_out;
+    g.err = h->err;
+    g.limit_ns = 2000000000ull;
+    h->launches += 1;
+    return utma::launch_halo_conv<BN, SW, SWA, SWA == 64 ? 32 : 64>(g, h->sms, h->stream);
+}
+
 // out (H x W) = conv3x3 with padding 1 and the given stride of the view
 // [off, off + C) of `buf` (stride H x stride W); flip = 1 for the data
 // gradient (taps mirrored, stride 1).  C must be a multiple of 64 (128-byte
@@ -373,6 +403,13 @@ template <class EP>
 cudaError_t conv_tma(neurosim_interp* h, const bf16* buf, int cstride, int off, int C, int flip, int N, int H, int W,
                      const bf16* wpacked, int n_out, const EP& ep, int stride = 1)
 {
+    if (stride == 1 && W % 128 == 0 && n_out <= 64 && (C == 32 || C == 64)) {
+        if (C == 32)
+            return n_out <= 32 ? conv_halo_bn<32, 64, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep)
+                               : conv_halo_bn<64, 64, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+        return n_out <= 32 ? conv_halo_bn<32, 128, 128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep)
+                           : conv_halo_bn<64, 128, 128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+    }
     if (C == 32) {
         if (n_out <= 32) return conv_tma_bn<32, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep, stride);
         if (n_out <= 64) return conv_tma_bn<64, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep, stride);

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "umma.cuh"
 
 namespace utma {
@@ -49,7 +51,9 @@ inline bool encode_tiled(CUtensorMap* map, int rank, const void* base, const cuu
     const cuuint32_t ones[5] = {1u, 1u, 1u, 1u, 1u};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), dims, strides_bytes,
               box, elem_strides ? elem_strides : ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              swizzle == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              swizzle == 0 ? CU_TENSOR_MAP_SWIZZLE_NONE
+                           : swizzle == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -159,6 +163,41 @@ struct ConvTapA {
     }
 };
 
+// Epilogue of one accumulator row: 32 columns per TMEM load (one wait), then
+// the epilogue functor on 8 columns at a time, unrolled so that the global
+// loads some functors make (masks, accumulation) are in flight together.
+template <int BN, class EP>
+__device__ __forceinline__ void drain_row(uint32_t lane_addr, int row, int n_cols, const EP& ep)
+{
+    static_assert(BN % 16 == 0, "columns");
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        if (c0 + 32 <= BN) {
+            umma::tmem_ld32(lane_addr + (uint32_t)c0, v);
+        } else {
+            float w[8];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                umma::tmem_ld8(lane_addr + (uint32_t)(c0 + 8 * q), w);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) v[8 * q + i] = w[i];
+            }
+        }
+        if (row < 0) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = c0 + 8 * q;
+            if (c < BN && c < n_cols) {
+                float u[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) u[i] = v[8 * q + i];
+                ep.store(row, c, u, 0);
+            }
+        }
+    }
+}
+
 template <class AL, class EP>
 struct TmaArgs {
     CUtensorMap ta;       // A map
@@ -254,12 +293,7 @@ __global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ T
         const int r = warp * 32 + (tid & 31);
         const int row = g.a.row_of(tile, r);
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-        for (int c = 0; c < BN; c += 8) {
-            float v[8];
-            umma::tmem_ld8(lane_addr + (uint32_t)c, v);
-            if (row >= 0 && c < g.N) g.ep.store(row, c, v, 0);
-        }
+        drain_row<BN>(lane_addr, row, g.N, g.ep);
     } else if (tid == 0) {
         atomicOr(g.err, kErrTimeout);
     }
@@ -277,6 +311,249 @@ cudaError_t launch_tma_gemm(const TmaArgs<AL, EP>& g, int tiles, cudaStream_t st
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes<BN, SW>());
     if (e != cudaSuccess) return e;
     tma_gemm_kernel<BN, SW, AL, EP><<<tiles, 128, tma_smem_bytes<BN, SW>(ns), stream>>>(g);
+    return cudaGetLastError();
+}
+
+
+// ---- 3 x 3 stride-1 convolution from a halo tile ----------------------------------------
+// Output tile: 128 consecutive pixels x0 .. x0 + 127 of row y0 of image n
+// (W a multiple of 128).  The A operands of all 9 taps come from one halo
+// tile: the channel view [off, off + C) of rows y0 - 1 .. y0 + 1 and pixels
+// x0 - 1 .. x0 + 128, brought in by TMA as C / 8 planes of 3 x 130 pixels x 8
+// channels (16 bytes per pixel, no swizzle; zero fill outside the image is
+// the padding), planes padded to 128-byte multiples.  Inside a plane the
+// pixels of the three rows follow each other 16 bytes apart, so the
+// 128 x 16 operand of tap (dy, dx) and channel group g is a canonical
+// no-swizzle K-major matrix that starts (row * 130 + col) * 16 bytes into
+// plane 2g: core matrices of 8 pixels x 16 bytes, SBO = 128 bytes (next 8
+// pixels), LBO = one plane (next 8 channels).  Each input pixel is read from
+// L2 once per tile instead of once per tap.
+// With a 128- or 64-byte swizzle (SWA = 128 or 64, C a multiple of SWA / 2)
+// the halo instead comes as C / (SWA / 2) boxes of 3 x 130 pixels x SWA / 2
+// channels (rows of SWA bytes, far fewer TMA rows).  The operand of tap
+// (dy, dx) then starts on a pixel row that is not 8-row aligned; the tensor
+// core applies the swizzle by shared-memory address bits, as the TMA wrote
+// it, so such a start needs no base offset (measured on GB300: base offset
+// (start >> 7) & 7 gave wrong results, 0 gives exact ones).
+// flip = 0: out(y, x) reads in(y + dy - 1, x + dx - 1)          (forward)
+// flip = 1: out(y, x) reads g(y + 1 - dy, x + 1 - dx)           (data gradient)
+//
+// Persistent, warp-specialised CTA of 6 warps: warp 4 loads (the packed
+// weights of all taps once, then one halo per tile into two alternating
+// buffers), warp 5 issues the MMAs of a tile into one of two TMEM
+// accumulators, warps 0-3 drain the other accumulator through the epilogue.
+// So the next tile's halo load and MMAs overlap this tile's epilogue.
+constexpr int kHaloW = 130;                         // 128 + 2 pixels
+constexpr uint32_t kHaloPlane = 3 * kHaloW * 16;    // 6240 bytes written per plane
+constexpr uint32_t kHaloPlaneStride = (kHaloPlane + 127u) / 128u * 128u;
+constexpr int kHaloThreads = 192;
+// one halo box of the swizzled forms: 390 rows of SWA bytes, padded to 1024
+__host__ __device__ constexpr uint32_t halo_box_bytes(int SWA) { return 3u * kHaloW * (uint32_t)SWA; }
+__host__ __device__ constexpr uint32_t halo_box_stride(int SWA) { return (halo_box_bytes(SWA) + 1023u) / 1024u * 1024u; }
+
+__host__ __device__ constexpr uint32_t halo_bytes_of(int C, int SWA)
+{
+    return SWA ? (uint32_t)(C / (SWA / 2)) * halo_box_stride(SWA) : (uint32_t)(C / 8) * kHaloPlaneStride;
+}
+
+template <class EP>
+struct HaloArgs {
+    CUtensorMap ta;       // NHWC activations: (cstride, W, H, N), box (8, 130, 3, 1), no swizzle
+    CUtensorMap tb;       // packed weights (9C, n_out), box (bk, BN)
+    EP ep;
+    int C, off, flip;
+    int W, H, N;          // image size (input = output)
+    int n_tiles;
+    int n_out;            // real columns (<= BN)
+    unsigned int* err;
+    uint64_t limit_ns;
+};
+
+template <int BN, int SW, int SWA>
+__host__ __device__ constexpr size_t halo_smem_bytes(int C)
+{
+    return 1024 + (size_t)9 * (C / bk_of(SW)) * BN * SW + 2 * (size_t)halo_bytes_of(C, SWA) + 256;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_u32(mbar)) : "memory");
+}
+
+template <int BN, int SW, int SWA, int CC, class EP>
+__global__ void __launch_bounds__(kHaloThreads) halo_conv_kernel(const __grid_constant__ HaloArgs<EP> g)
+{
+    static_assert(SWA == 0 || SWA == 64 || SWA == 128, "halo layouts");
+    static_assert(CC % 16 == 0 && (SWA == 0 || CC % (SWA / 2) == 0) && CC % bk_of(SW) == 0, "channels");
+    constexpr int HC = SWA ? SWA / 2 : 8;           // channels per halo box
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "tcgen05 N for M = 128, two accumulators");
+    constexpr uint32_t TC = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;    // columns of one accumulator
+    constexpr int SBK = bk_of(SW);
+    constexpr uint32_t B_BYTES = BN * SW;           // one K tile of the weights
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024u - (umma::smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int planes = CC / 8;
+    constexpr int n_kt = 9 * (CC / SBK);
+    constexpr uint32_t halo_bytes = halo_bytes_of(CC, SWA);
+    unsigned char* sB = smem;                                   // 1024-aligned swizzled tiles
+    unsigned char* sA = smem + (size_t)n_kt * B_BYTES;          // two halo buffers
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sA + 2 * (size_t)halo_bytes);
+    uint64_t* bfull = bar;          // weights landed
+    uint64_t* afull = bar + 1;      // [2] halo landed
+    uint64_t* aempty = bar + 3;     // [2] halo consumed by the MMAs
+    uint64_t* tfull = bar + 5;      // [2] accumulator complete
+    uint64_t* tempty = bar + 7;     // [2] accumulator drained by the epilogue
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 9);
+    __shared__ unsigned int s_fail;
+    const int tiles_x = g.W / 128;
+    const int per = g.H * tiles_x;
+
+    if (tid == 0) {
+        s_fail = 0u;
+        umma::mbar_init(bfull, 1);
+        for (int b = 0; b < 2; ++b) {
+            umma::mbar_init(&afull[b], 1);
+            umma::mbar_init(&aempty[b], 1);
+            umma::mbar_init(&tfull[b], 1);
+            umma::mbar_init(&tempty[b], 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) umma::tmem_alloc(tslot, 2 * TC);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(BM, BN, false, false);
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // producer: the weights once, then one halo per tile
+            uint32_t issued = 0;
+            mbar_expect_tx(bfull, (uint32_t)n_kt * B_BYTES);
+            for (int kt = 0; kt < n_kt; ++kt) tma_load_2d(sB + (size_t)kt * B_BYTES, &g.tb, kt * SBK, 0, bfull);
+            uint32_t i = 0;
+            for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
+                const uint32_t b = i & 1u, use = i >> 1;
+                if (i >= 2 && !umma::mbar_wait(&aempty[b], (use - 1u) & 1u, g.limit_ns)) {
+                    atomicOr(&s_fail, 1u);
+                    break;
+                }
+                if (*(volatile unsigned int*)&s_fail) break;
+                issued = i + 1;
+                const int n = tile / per;
+                const int rem = tile - n * per;
+                const int y0 = rem / tiles_x;
+                const int x0 = (rem - y0 * tiles_x) * 128;
+                unsigned char* dst = sA + (size_t)b * halo_bytes;
+                if (SWA) {
+                    mbar_expect_tx(&afull[b], (uint32_t)(CC / HC) * halo_box_bytes(SWA));
+                    for (int p = 0; p < CC / HC; ++p)
+                        tma_load_4d(dst + (size_t)p * halo_box_stride(SWA), &g.ta, g.off + HC * p, x0 - 1, y0 - 1,
+                                    n, &afull[b]);
+                } else {
+                    mbar_expect_tx(&afull[b], (uint32_t)planes * kHaloPlane);
+                    for (int p = 0; p < planes; ++p)
+                        tma_load_4d(dst + (size_t)p * kHaloPlaneStride, &g.ta, g.off + 8 * p, x0 - 1, y0 - 1, n,
+                                    &afull[b]);
+                }
+            }
+            if (*(volatile unsigned int*)&s_fail) {
+                // let the copies in flight land before the CTA leaves (bounded)
+                umma::mbar_wait(bfull, 0u, g.limit_ns);
+                for (uint32_t j = issued >= 2 ? issued - 2 : 0; j < issued; ++j)
+                    umma::mbar_wait(&afull[j & 1u], (j >> 1) & 1u, g.limit_ns);
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // MMA issuer: 9 taps x C / 16 channel groups per tile
+            bool ok = umma::mbar_wait(bfull, 0u, g.limit_ns);
+            uint32_t i = 0;
+            for (int tile = blockIdx.x; ok && tile < g.n_tiles; tile += gridDim.x, ++i) {
+                const uint32_t b = i & 1u, use = i >> 1;
+                ok = umma::mbar_wait(&afull[b], use & 1u, g.limit_ns) &&
+                     (i < 2 || umma::mbar_wait(&tempty[b], (use - 1u) & 1u, g.limit_ns));
+                if (!ok || *(volatile unsigned int*)&s_fail) break;
+                umma::fence_after_sync();
+                // descriptors differ from the tile's first ones only in the
+                // start-address field: add (byte offset >> 4)
+                const uint32_t a0 = umma::smem_u32(sA + (size_t)b * halo_bytes), b0 = umma::smem_u32(sB);
+                const uint64_t ad0 = SWA == 128  ? (umma::smem_desc(a0, 16u, 1024u) | ((uint64_t)2u << 61))
+                                     : SWA == 64 ? (umma::smem_desc(a0, 16u, 512u) | ((uint64_t)4u << 61))
+                                                 : umma::smem_desc(a0, kHaloPlaneStride, 128u);
+                const uint64_t bd0 = desc_sw<SW>(b0, 0);
+                const uint32_t d = tmem + b * TC;
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap % 3;
+                    const uint32_t shift = (uint32_t)(g.flip ? (2 - dy) * kHaloW + (2 - dx) : dy * kHaloW + dx);
+#pragma unroll
+                    for (int c16 = 0; c16 < CC / 16; ++c16) {
+                        constexpr int KS = HC / 16;           // K steps of 16 per swizzled row
+                        const uint32_t aoff = SWA ? (uint32_t)(c16 / KS) * halo_box_stride(SWA) + shift * (uint32_t)SWA +
+                                                        (uint32_t)(c16 % KS) * 32u
+                                                  : (uint32_t)(2 * c16) * kHaloPlaneStride + shift * 16u;
+                        const int kt = tap * (CC / SBK) + (c16 * 16) / SBK;
+                        const uint32_t boff = (uint32_t)kt * B_BYTES + (uint32_t)((c16 * 16 % SBK) / 16) * 32u;
+                        umma::mma_bf16(d, ad0 + (aoff >> 4), bd0 + (boff >> 4), idesc,
+                                       (tap > 0 || c16 > 0) ? 1u : 0u);
+                    }
+                }
+                umma::mma_commit(&aempty[b]);
+                umma::mma_commit(&tfull[b]);
+            }
+            if (!ok) atomicOr(&s_fail, 1u);
+        }
+    } else {
+        // epilogue warps 0-3: TMEM lanes 32 w .. 32 w + 31 = tile rows
+        uint32_t i = 0;
+        for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
+            const uint32_t b = i & 1u, use = i >> 1;
+            bool ok = umma::mbar_wait(&tfull[b], use & 1u, g.limit_ns);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) atomicOr(&s_fail, 1u);
+                break;
+            }
+            umma::fence_after_sync();
+            const int n = tile / per;
+            const int rem = tile - n * per;
+            const int y0 = rem / tiles_x;
+            const int x0 = (rem - y0 * tiles_x) * 128;
+            const int row = (n * g.H + y0) * g.W + x0 + warp * 32 + lane;
+            const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + b * TC;
+            drain_row<BN>(lane_addr, row, g.n_out, g.ep);
+            umma::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (tid == 0 && s_fail) atomicOr(g.err, kErrTimeout);
+    if (warp == 0) umma::tmem_dealloc(tmem, 2 * TC);
+}
+
+template <int BN, int SW, int SWA, int CC, class EP>
+cudaError_t launch_halo_conv(const HaloArgs<EP>& g, int num_sms, cudaStream_t stream)
+{
+    if (g.C != CC) return cudaErrorInvalidValue;
+    const size_t smem = halo_smem_bytes<BN, SW, SWA>(CC);
+    cudaError_t e = cudaFuncSetAttribute(halo_conv_kernel<BN, SW, SWA, CC, EP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, halo_conv_kernel<BN, SW, SWA, CC, EP>, kHaloThreads,
+                                                      smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // resident CTAs must also fit in the SM's 512 TMEM columns (2 accumulators each)
+    constexpr int tc = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
+    per_sm = std::min(per_sm, 512 / (2 * tc));
+    const int grid = std::min(g.n_tiles, num_sms * per_sm);
+    halo_conv_kernel<BN, SW, SWA, CC, EP><<<grid, kHaloThreads, smem, stream>>>(g);
     return cudaGetLastError();
 }
 

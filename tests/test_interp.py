@@ -5,7 +5,8 @@ activations), so the two differ by FP32 accumulation order and by the BF16
 rounding of gradients the GPU keeps between layers; the tolerances below are
 derived from that: outputs within 1 % of the residual scale, gradients within
 a few BF16 ulps (2^-8) relative in norm.  Shapes: batch 2, 16 x 24 (several
-128-row tiles at full size, ragged tails at the quarter size).
+128-row tiles at full size, ragged tails at the quarter size), and 1 x 8 x 128,
+whose full-size 3x3 layers run from halo tiles (rows of 128 pixels).
 """
 import numpy as np
 import pytest
@@ -72,10 +73,14 @@ def test_param_roundtrip_and_untrained_is_linear():
     net.close()
 
 
-def test_forward_matches_oracle():
+SHAPES = [(2, 16, 24), (1, 8, 128)]
+
+
+@pytest.mark.parametrize("N,H,W", SHAPES)
+def test_forward_matches_oracle(N, H, W):
     p = _params(11)
-    clips = _clips(1, 2, 16, 24)
-    net = _net(p)
+    clips = _clips(1, N, H, W)
+    net = _net(p, N, H, W)
     c = torch.from_numpy(clips).float().cuda()
     out = net.forward(c[:, 0].contiguous(), c[:, 4].contiguous()).cpu().numpy()
     ref, _ = io.forward(p, clips[:, 0].astype(np.float32), clips[:, 4].astype(np.float32), quantize=True)
@@ -87,10 +92,11 @@ def test_forward_matches_oracle():
     net.close()
 
 
-def test_gradients_match_oracle():
+@pytest.mark.parametrize("N,H,W", SHAPES)
+def test_gradients_match_oracle(N, H, W):
     p = _params(12)
-    clips = _clips(2, 2, 16, 24).astype(np.float32)
-    net = _net(p)
+    clips = _clips(2, N, H, W).astype(np.float32)
+    net = _net(p, N, H, W)
     loss, g = net.gradients(torch.from_numpy(clips).cuda())
     from paper_2602_15018_gb300.interp import to_dict
     gd = to_dict(g)
