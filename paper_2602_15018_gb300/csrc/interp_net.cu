@@ -368,7 +368,7 @@ cudaError_t conv_tma_bn(neurosim_interp* h, const bf16* buf, int cstride, int of
 // out = conv3x3 (stride 1) of the view [off, off + C) of `buf` from halo
 // tiles (W a multiple of 128; C 32 with a 64-byte swizzle of the weights, or
 // 64 with a 128-byte swizzle).
-template <int BN, int SW, int SWA, class EP>
+template <int BN, int SW, int SWA, int CC, class EP>
 cudaError_t conv_halo_bn(neurosim_interp* h, const bf16* buf, int cstride, int off, int C, int flip, int N, int H,
                          int W, const bf16* wpacked, int n_out, const EP& ep)
 {
@@ -392,7 +392,7 @@ cudaError_t conv_halo_bn(neurosim_interp* h, const bf16* buf, int cstride, int o
     g.err = h->err;
     g.limit_ns = 2000000000ull;
     h->launches += 1;
-    return utma::launch_halo_conv<BN, SW, SWA, SWA == 64 ? 32 : 64>(g, h->sms, h->stream);
+    return utma::launch_halo_conv<BN, SW, SWA, CC>(g, h->sms, h->stream);
 }
 
 // out (H x W) = conv3x3 with padding 1 and the given stride of the view
@@ -403,12 +403,14 @@ template <class EP>
 cudaError_t conv_tma(neurosim_interp* h, const bf16* buf, int cstride, int off, int C, int flip, int N, int H, int W,
                      const bf16* wpacked, int n_out, const EP& ep, int stride = 1)
 {
-    if (stride == 1 && W % 128 == 0 && n_out <= 64 && (C == 32 || C == 64)) {
+    if (stride == 1 && W % 128 == 0 && n_out <= 64 && (C == 32 || C == 64 || (C == 8 && !flip && n_out <= 32))) {
+        if (C == 8)
+            return conv_halo_bn<32, 128, 0, 8>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
         if (C == 32)
-            return n_out <= 32 ? conv_halo_bn<32, 64, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep)
-                               : conv_halo_bn<64, 64, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
-        return n_out <= 32 ? conv_halo_bn<32, 128, 128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep)
-                           : conv_halo_bn<64, 128, 128>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+            return n_out <= 32 ? conv_halo_bn<32, 64, 64, 32>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep)
+                               : conv_halo_bn<64, 64, 64, 32>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
+        return n_out <= 32 ? conv_halo_bn<32, 128, 128, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep)
+                           : conv_halo_bn<64, 128, 128, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
     }
     if (C == 32) {
         if (n_out <= 32) return conv_tma_bn<32, 64>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep, stride);
@@ -479,8 +481,11 @@ int forward(neurosim_interp* h, const Shape& s, const float* L0, const float* L4
     h->launches += 1;
     ICUDA(cudaGetLastError());
     // e1 -> cat1[:, 32:64]
-    ICUDA(gemm(h, conv3k(act(h->x0, N, H, W, 8, 0), 8, H, W, 1, s.P), ugemm::DenseK{h->wf[0], 32, 72},
-               EpiAct{h->cat1, 64, 32, bias_of(h, 0), 1}, s.P, 32, 72, false));
+    if (W % 128 == 0)
+        ICUDA(conv_tma(h, h->x0, 8, 0, 8, 0, N, H, W, h->wf[0], 32, EpiAct{h->cat1, 64, 32, bias_of(h, 0), 1}));
+    else
+        ICUDA(gemm(h, conv3k(act(h->x0, N, H, W, 8, 0), 8, H, W, 1, s.P), ugemm::DenseK{h->wf[0], 32, 72},
+                   EpiAct{h->cat1, 64, 32, bias_of(h, 0), 1}, s.P, 32, 72, false));
     // e2 -> cat2[:, 64:128]
     ICUDA(conv_tma(h, h->cat1, 64, 32, 32, 0, N, H2, W2, h->wf[1], 64, EpiAct{h->cat2, 128, 64, bias_of(h, 1), 1}, 2));
     // e3

@@ -335,6 +335,10 @@ cudaError_t launch_tma_gemm(const TmaArgs<AL, EP>& g, int tiles, cudaStream_t st
 // core applies the swizzle by shared-memory address bits, as the TMA wrote
 // it, so such a start needs no base offset (measured on GB300: base offset
 // (start >> 7) & 7 gave wrong results, 0 gives exact ones).
+// With 8 channels (one plane) a K = 16 step takes two taps: the second core
+// matrix along K is the same plane shifted to the next tap, so LBO is the
+// distance between the two taps' start rows; the 9th tap pairs with the
+// zero-filled weight columns 72..79 (and the plane's zeroed padding rows).
 // flip = 0: out(y, x) reads in(y + dy - 1, x + dx - 1)          (forward)
 // flip = 1: out(y, x) reads g(y + 1 - dy, x + 1 - dx)           (data gradient)
 //
@@ -372,7 +376,7 @@ struct HaloArgs {
 template <int BN, int SW, int SWA>
 __host__ __device__ constexpr size_t halo_smem_bytes(int C)
 {
-    return 1024 + (size_t)9 * (C / bk_of(SW)) * BN * SW + 2 * (size_t)halo_bytes_of(C, SWA) + 256;
+    return 1024 + (size_t)((9 * C + bk_of(SW) - 1) / bk_of(SW)) * BN * SW + 2 * (size_t)halo_bytes_of(C, SWA) + 256;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar)
@@ -384,7 +388,8 @@ template <int BN, int SW, int SWA, int CC, class EP>
 __global__ void __launch_bounds__(kHaloThreads) halo_conv_kernel(const __grid_constant__ HaloArgs<EP> g)
 {
     static_assert(SWA == 0 || SWA == 64 || SWA == 128, "halo layouts");
-    static_assert(CC % 16 == 0 && (SWA == 0 || CC % (SWA / 2) == 0) && CC % bk_of(SW) == 0, "channels");
+    static_assert((CC == 8 && SWA == 0) || (CC % 16 == 0 && (SWA == 0 || CC % (SWA / 2) == 0) && CC % bk_of(SW) == 0),
+                  "channels");
     constexpr int HC = SWA ? SWA / 2 : 8;           // channels per halo box
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "tcgen05 N for M = 128, two accumulators");
     constexpr uint32_t TC = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;    // columns of one accumulator
@@ -394,7 +399,7 @@ __global__ void __launch_bounds__(kHaloThreads) halo_conv_kernel(const __grid_co
     unsigned char* smem = smem_raw + ((1024u - (umma::smem_u32(smem_raw) & 1023u)) & 1023u);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int planes = CC / 8;
-    constexpr int n_kt = 9 * (CC / SBK);
+    constexpr int n_kt = (9 * CC + SBK - 1) / SBK;             // K tiles of the weights (zero-filled tail)
     constexpr uint32_t halo_bytes = halo_bytes_of(CC, SWA);
     unsigned char* sB = smem;                                   // 1024-aligned swizzled tiles
     unsigned char* sA = smem + (size_t)n_kt * B_BYTES;          // two halo buffers
@@ -419,6 +424,13 @@ __global__ void __launch_bounds__(kHaloThreads) halo_conv_kernel(const __grid_co
             umma::mbar_init(&tempty[b], 4);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (CC == 8 && tid < 2 * (int)((kHaloPlaneStride - kHaloPlane) / 16)) {
+        // the rows past the plane's 390 (read, times zero weights, by the 9th tap)
+        constexpr int per_buf = (int)((kHaloPlaneStride - kHaloPlane) / 16);
+        *reinterpret_cast<uint4*>(sA + (size_t)(tid / per_buf) * halo_bytes + kHaloPlane + (tid % per_buf) * 16) =
+            make_uint4(0u, 0u, 0u, 0u);
+        umma::fence_async_smem();
     }
     if (warp == 0) umma::tmem_alloc(tslot, 2 * TC);
     umma::fence_before_sync();
@@ -485,8 +497,23 @@ __global__ void __launch_bounds__(kHaloThreads) halo_conv_kernel(const __grid_co
                                                  : umma::smem_desc(a0, kHaloPlaneStride, 128u);
                 const uint64_t bd0 = desc_sw<SW>(b0, 0);
                 const uint32_t d = tmem + b * TC;
+                if (CC == 8) {
+                    // tap pairs (2j, 2j + 1) per K = 16 step; tap 9 is the zero weight tail
 #pragma unroll
-                for (int tap = 0; tap < 9; ++tap) {
+                    for (int j = 0; j < 5; ++j) {
+                        const int t0 = 2 * j, t1 = 2 * j + 1;
+                        const int s0 = g.flip ? (2 - t0 / 3) * kHaloW + (2 - t0 % 3) : (t0 / 3) * kHaloW + t0 % 3;
+                        const int s1 = t1 < 9 ? (g.flip ? (2 - t1 / 3) * kHaloW + (2 - t1 % 3)
+                                                        : (t1 / 3) * kHaloW + t1 % 3)
+                                              : s0 + 1;
+                        const uint64_t adesc =
+                            umma::smem_desc(a0 + (uint32_t)s0 * 16u, (uint32_t)(s1 - s0) * 16u, 128u);
+                        const uint32_t boff = (uint32_t)((16 * j) / SBK) * B_BYTES + (uint32_t)((16 * j % SBK) / 16) * 32u;
+                        umma::mma_bf16(d, adesc, bd0 + (boff >> 4), idesc, j > 0 ? 1u : 0u);
+                    }
+                }
+#pragma unroll
+                for (int tap = 0; tap < (CC == 8 ? 0 : 9); ++tap) {
                     const int dy = tap / 3, dx = tap % 3;
                     const uint32_t shift = (uint32_t)(g.flip ? (2 - dy) * kHaloW + (2 - dx) : dy * kHaloW + dx);
 #pragma unroll
