@@ -366,8 +366,8 @@ cudaError_t conv_tma_bn(neurosim_interp* h, const bf16* buf, int cstride, int of
 }
 
 // out = conv3x3 (stride 1) of the view [off, off + C) of `buf` from halo
-// tiles (W a multiple of 128; C 32 with a 64-byte swizzle of the weights, or
-// 64 with a 128-byte swizzle).
+// tiles of 128-pixel rows (W >= 128; C 8 (forward), 32 with a 64-byte swizzle
+// of the weights, or 64 with a 128-byte swizzle).
 template <int BN, int SW, int SWA, int CC, class EP>
 cudaError_t conv_halo_bn(neurosim_interp* h, const bf16* buf, int cstride, int off, int C, int flip, int N, int H,
                          int W, const bf16* wpacked, int n_out, const EP& ep)
@@ -387,7 +387,7 @@ cudaError_t conv_halo_bn(neurosim_interp* h, const bf16* buf, int cstride, int o
     g.W = W;
     g.H = H;
     g.N = N;
-    g.n_tiles = N * H * (W / 128);
+    g.n_tiles = N * H * ((W + 127) / 128);
     g.n_out = n_out;
     g.err = h->err;
     g.limit_ns = 2000000000ull;
@@ -403,7 +403,7 @@ template <class EP>
 cudaError_t conv_tma(neurosim_interp* h, const bf16* buf, int cstride, int off, int C, int flip, int N, int H, int W,
                      const bf16* wpacked, int n_out, const EP& ep, int stride = 1)
 {
-    if (stride == 1 && W % 128 == 0 && n_out <= 64 && (C == 32 || C == 64 || (C == 8 && !flip && n_out <= 32))) {
+    if (stride == 1 && W >= 128 && n_out <= 64 && (C == 32 || C == 64 || (C == 8 && !flip && n_out <= 32))) {
         if (C == 8)
             return conv_halo_bn<32, 128, 0, 8>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);
         if (C == 32)
@@ -481,7 +481,7 @@ int forward(neurosim_interp* h, const Shape& s, const float* L0, const float* L4
     h->launches += 1;
     ICUDA(cudaGetLastError());
     // e1 -> cat1[:, 32:64]
-    if (W % 128 == 0)
+    if (W >= 128)
         ICUDA(conv_tma(h, h->x0, 8, 0, 8, 0, N, H, W, h->wf[0], 32, EpiAct{h->cat1, 64, 32, bias_of(h, 0), 1}));
     else
         ICUDA(gemm(h, conv3k(act(h->x0, N, H, W, 8, 0), 8, H, W, 1, s.P), ugemm::DenseK{h->wf[0], 32, 72},

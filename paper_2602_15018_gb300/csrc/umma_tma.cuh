@@ -317,7 +317,8 @@ cudaError_t launch_tma_gemm(const TmaArgs<AL, EP>& g, int tiles, cudaStream_t st
 
 // ---- 3 x 3 stride-1 convolution from a halo tile ----------------------------------------
 // Output tile: 128 consecutive pixels x0 .. x0 + 127 of row y0 of image n
-// (W a multiple of 128).  The A operands of all 9 taps come from one halo
+// (W >= 128; the last tile of a row may reach past W: its halo reads the zero
+// fill and its rows past W are not stored).  The A operands of all 9 taps come from one halo
 // tile: the channel view [off, off + C) of rows y0 - 1 .. y0 + 1 and pixels
 // x0 - 1 .. x0 + 128, brought in by TMA as C / 8 planes of 3 x 130 pixels x 8
 // channels (16 bytes per pixel, no swizzle; zero fill outside the image is
@@ -411,7 +412,7 @@ __global__ void __launch_bounds__(kHaloThreads) halo_conv_kernel(const __grid_co
     uint64_t* tempty = bar + 7;     // [2] accumulator drained by the epilogue
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 9);
     __shared__ unsigned int s_fail;
-    const int tiles_x = g.W / 128;
+    const int tiles_x = (g.W + 127) / 128;
     const int per = g.H * tiles_x;
 
     if (tid == 0) {
@@ -549,7 +550,8 @@ __global__ void __launch_bounds__(kHaloThreads) halo_conv_kernel(const __grid_co
             const int rem = tile - n * per;
             const int y0 = rem / tiles_x;
             const int x0 = (rem - y0 * tiles_x) * 128;
-            const int row = (n * g.H + y0) * g.W + x0 + warp * 32 + lane;
+            const int x = x0 + warp * 32 + lane;
+            const int row = x < g.W ? (n * g.H + y0) * g.W + x : -1;
             const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + b * TC;
             drain_row<BN>(lane_addr, row, g.n_out, g.ep);
             umma::fence_before_sync();

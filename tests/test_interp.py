@@ -5,8 +5,9 @@ activations), so the two differ by FP32 accumulation order and by the BF16
 rounding of gradients the GPU keeps between layers; the tolerances below are
 derived from that: outputs within 1 % of the residual scale, gradients within
 a few BF16 ulps (2^-8) relative in norm.  Shapes: batch 2, 16 x 24 (several
-128-row tiles at full size, ragged tails at the quarter size), and 1 x 8 x 128,
-whose full-size 3x3 layers run from halo tiles (rows of 128 pixels).
+128-row tiles at full size, ragged tails at the quarter size), and 1 x 8 x 128
+and 1 x 8 x 160, whose full-size 3x3 layers run from halo tiles (rows of 128
+pixels; at width 160 the second tile of a row reaches past the image).
 """
 import numpy as np
 import pytest
@@ -73,7 +74,7 @@ def test_param_roundtrip_and_untrained_is_linear():
     net.close()
 
 
-SHAPES = [(2, 16, 24), (1, 8, 128)]
+SHAPES = [(2, 16, 24), (1, 8, 128), (1, 8, 160)]
 
 
 @pytest.mark.parametrize("N,H,W", SHAPES)
