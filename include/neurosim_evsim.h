@@ -82,7 +82,9 @@ typedef struct neurosim_evsim_params {
     int32_t pixels_per_thread;   /* emission pixels per CUDA thread: 8 or 16
                                     (a warp owns 32x that many pixels); 0 = auto */
     int32_t prefetch_frames;     /* frames each thread keeps in flight: 2 or 3;
-                                    0 = auto                                    */
+                                    0 = auto.  The emission kernel models the
+                                    frames in pairs and keeps one pair in
+                                    flight: 2 and 3 behave the same          */
     int32_t reserved[6];         /* must be zero                               */
 } neurosim_evsim_params;
 
@@ -213,7 +215,8 @@ typedef struct {
     uint64_t event_capacity;     /* records kept between drains (0 = auto:
                                     sum(W*H) * T * max_pending_steps / 16)        */
     int32_t pixels_per_thread;   /* emission tile: 0 (16), 8 or 16                */
-    int32_t prefetch_frames;     /* frames in flight per lane: 0 (2), 2 or 3      */
+    int32_t prefetch_frames;     /* frames in flight per lane: 0 (2), 2 or 3
+                                    (one pair of frames either way)              */
     int32_t frame_slots;         /* frame-buffer sets that can be registered
                                     (0 = 2, at most 16): a renderer fills one
                                     while the steps read another               */

@@ -28,16 +28,20 @@
 // the filter may send a pixel to the slow path for nothing, never the other
 // way.  A NaN input fails both comparisons and is always tested exactly.
 //
-// Slow path: the warp's pixels outside their bounds are compacted into a
-// list in pixel order and handed out one per lane, 32 per round, so that
-// neighbouring pixels that trigger together are processed in parallel.  Each
-// lane runs the exact FP32 model for its pixel, commits the state, keeps the
-// first two keys in registers; a warp prefix of the counts (list order =
-// pixel order) places the keys of the tile's events in this interval as one
-// contiguous chunk of the paged key buffer (one global atomic per page, not
-// per frame).  More than one round, or more than two events for a pixel,
-// takes the general path that regenerates keys from values saved in scratch
-// slots of shared memory.
+// Slow path, once per pair of frames (f, f + 1): both frames are filtered
+// with the bounds from before the pair.  A pixel out of its band at f is
+// modelled exactly over both frames (its filter result at f + 1 is stale); a
+// pixel in its band at f but out at f + 1 only over f + 1.  These pixels are
+// compacted into a list in pixel order and handed out one per lane, so that
+// the list build, the threshold loads, the log of the previous input and the
+// bounds update are paid once per pair, not once per frame.  Each lane runs
+// the exact FP32 model for its pixel, commits the state and keeps the first
+// two keys of each frame in registers; per frame a warp prefix of the counts
+// (list order = pixel order) places the tile's keys of that interval as one
+// contiguous chunk of the paged key buffer, both frames' chunks in one run
+// (one global atomic per page, not per frame).  More than 32 listed pixels
+// fall back to the general path frame by frame; more than two events of a
+// pixel in a frame regenerate its keys from the saved state.
 
 constexpr float kBoundMargin = 1.0e-4f;
 constexpr float kMaxIntensity = 1.0e6f;
@@ -159,34 +163,37 @@ __device__ __forceinline__ int pixel_events(float& r, uint32_t& tl, float a, flo
 
 // Per-warp shared-memory slice (arrays of WPX = 32*PPT entries indexed by the
 // tile-local pixel, plus the trigger list and the lanes' "L cached" masks).
+// The raw inputs of frame f live in input slot f % 3: the previous frame and
+// the two frames of the current pair.
 template <int PPT>
 struct WarpSlice {
     static constexpr int WPX = 32 * PPT;
-    static constexpr int FLOATS = 7 * WPX + WPX + 32;   // 7 arrays, list (u32), masks
+    static constexpr int FLOATS = 8 * WPX + WPX + 32;   // 8 arrays, list (u32), masks
     float* base;
-    __device__ __forceinline__ float* vs(int parity) const { return base + parity * WPX; }
-    __device__ __forceinline__ float* vu() const { return base + 2 * WPX; }
-    __device__ __forceinline__ float* vd() const { return base + 3 * WPX; }
-    __device__ __forceinline__ float* ref() const { return base + 4 * WPX; }
-    __device__ __forceinline__ uint32_t* tl() const { return reinterpret_cast<uint32_t*>(base + 5 * WPX); }
-    __device__ __forceinline__ float* lb() const { return base + 6 * WPX; }
-    __device__ __forceinline__ uint32_t* list() const { return reinterpret_cast<uint32_t*>(base + 7 * WPX); }
-    __device__ __forceinline__ uint32_t* lvm() const { return reinterpret_cast<uint32_t*>(base + 8 * WPX); }
+    __device__ __forceinline__ float* vs(int slot) const { return base + slot * WPX; }
+    __device__ __forceinline__ float* vu() const { return base + 3 * WPX; }
+    __device__ __forceinline__ float* vd() const { return base + 4 * WPX; }
+    __device__ __forceinline__ float* ref() const { return base + 5 * WPX; }
+    __device__ __forceinline__ uint32_t* tl() const { return reinterpret_cast<uint32_t*>(base + 6 * WPX); }
+    __device__ __forceinline__ float* lb() const { return base + 7 * WPX; }
+    __device__ __forceinline__ uint32_t* list() const { return reinterpret_cast<uint32_t*>(base + 8 * WPX); }
+    __device__ __forceinline__ uint32_t* lvm() const { return reinterpret_cast<uint32_t*>(base + 9 * WPX); }
 };
 
-// Everything the slow path needs about the current tile and interval.
+// Everything the slow path needs about the current tile and frame.
 struct TileCtx {
     const float* cpos;   // per-pixel thresholds of the stream (global), or null
     const float* cneg;
     float cpos_u, cneg_u;
-    uint32_t ta;
+    uint32_t ta;         // start and length of the frame's interval
     float Df;
     uint32_t R;
     float eps;
     int is_log;
     int tshift;
     int g0;              // global index of the tile's pixel 0
-    int cur;             // parity of the current frame's input slot
+    const float* vcur;   // raw inputs of the frame and of the one before it
+    float* vprev;
     uint64_t keep;       // L2 evict_last policy for the thresholds
 };
 
@@ -204,18 +211,101 @@ __device__ __forceinline__ void thresholds_of(const TileCtx& c, int p, float& cp
 // L_a of pixel p: cached L of the previous frame if its owner lane's mask says
 // so, else the model's log of the previous input.
 template <int PPT>
-__device__ __forceinline__ float L_prev(const WarpSlice<PPT>& s, const TileCtx& c, int p)
+__device__ __forceinline__ float L_prev(const WarpSlice<PPT>& s, const TileCtx& c, const float* vprev, int p)
 {
     const int owner = (p & 127) >> 2;
     const int bit = ((p >> 7) << 2) | (p & 3);
     if ((s.lvm()[owner] >> bit) & 1u) return s.lb()[p];
-    return model_L(s.vs(c.cur ^ 1)[p], c.eps, c.is_log);
+    return model_L(vprev[p], c.eps, c.is_log);
 }
 
-// General path for one warp-frame: any number of list entries and events.
-// Pass 1 commits every entry and saves (L_a, ref, t_last) before the step in
-// the vu / vd / previous-input slots and its count in the list entry; then
-// the keys are regenerated into out[] in list order; then fresh bounds.
+// `total` consecutive keys from the warp's page (a new page run when they do
+// not fit); kNoChunk and the overflow bit when the key buffer is exhausted.
+__device__ __forceinline__ uint32_t take_keys(uint32_t& pg_cur, uint32_t& pg_end, uint32_t total, int lane,
+                                              uint32_t page_keys, uint32_t n_pages, unsigned int* page_ctr,
+                                              unsigned int* err)
+{
+    if (total == 0u) return kNoChunk;
+    if (pg_end - pg_cur >= total) {
+        const uint32_t b = pg_cur;
+        pg_cur += total;
+        return b;
+    }
+    const uint32_t np_ = (total + page_keys - 1u) / page_keys;
+    uint32_t first = 0u;
+    if (lane == 0) first = atomicAdd(page_ctr, np_);
+    first = __shfl_sync(0xffffffffu, first, 0);
+    if ((uint64_t)first + np_ <= (uint64_t)n_pages) {
+        const uint32_t b = first * page_keys;
+        pg_cur = b + total;
+        pg_end = (first + np_) * page_keys;
+        return b;
+    }
+    if (lane == 0) atomicOr(err, kErrPageOverflow);
+    pg_cur = pg_end = 0u;
+    return kNoChunk;
+}
+
+// Writes the tile-local pixels whose bit is set in the lanes' masks m (bit
+// q*4 + c = pixel q*128 + lane*4 + c) to list[] in pixel order (group q, then
+// lane, then component), each entry p | (bit of `flag` for p) << 10.
+// Returns the count (warp-uniform).
+template <int PPT>
+__device__ __forceinline__ int build_list(uint32_t m, uint32_t flag, int lane, uint32_t* list)
+{
+    constexpr int NQ = PPT / 4;
+    uint32_t packed = 0u;   // 8-bit count per group (at most 128)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) packed |= (uint32_t)__popc((m >> (q * 4)) & 15u) << (q * 8);
+    uint32_t incl = packed;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t nb = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += nb;
+    }
+    const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t ex = incl - packed;
+    int n = 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        int pos = n + (int)((ex >> (q * 8)) & 255u);
+        uint32_t mm = (m >> (q * 4)) & 15u;
+        while (mm) {
+            const int cbit = __ffs(mm) - 1;
+            mm &= mm - 1u;
+            list[pos++] = (uint32_t)(q * 128 + lane * 4 + cbit) | (((flag >> (q * 4 + cbit)) & 1u) << 10);
+        }
+        n += (int)((tot >> (q * 8)) & 255u);
+    }
+    return n;
+}
+
+// Exclusive prefix and total of the lanes' counts n >= 0.
+__device__ __forceinline__ void count_prefix(int n, int lane, int& excl, uint32_t& total)
+{
+    if (__any_sync(0xffffffffu, n > 3)) {
+        int in = n;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int nb = __shfl_up_sync(0xffffffffu, in, d);
+            if (lane >= d) in += nb;
+        }
+        excl = in - n;
+        total = (uint32_t)__shfl_sync(0xffffffffu, in, 31);
+    } else {
+        const uint32_t lt = (1u << lane) - 1u;
+        const uint32_t b0 = __ballot_sync(0xffffffffu, (n & 1) != 0);
+        const uint32_t b1 = __ballot_sync(0xffffffffu, (n & 2) != 0);
+        excl = __popc(b0 & lt) + 2 * __popc(b1 & lt);
+        total = (uint32_t)(__popc(b0) + 2 * __popc(b1));
+    }
+}
+
+// General path for one warp-frame: any number of list entries (n_list, in
+// pixel order) and events.  Pass 1 commits every entry and saves (L_a, ref,
+// t_last) before the step in the vu / vd / previous-input slots and its count
+// in the list entry; then the keys are regenerated into out[] in list order;
+// then fresh bounds.
 template <int PPT, typename KeyT>
 __device__ __noinline__ void slow_general(const WarpSlice<PPT> s, const TileCtx c, int lane,
                                           int n_list, KeyT* keys, uint32_t page_keys, uint32_t n_pages,
@@ -223,7 +313,7 @@ __device__ __noinline__ void slow_general(const WarpSlice<PPT> s, const TileCtx 
                                           uint32_t& pg_cur, uint32_t& pg_end, uint32_t* chunk_off,
                                           uint32_t* chunk_cnt)
 {
-    uint32_t* vprev_bits = reinterpret_cast<uint32_t*>(s.vs(c.cur ^ 1));
+    uint32_t* vprev_bits = reinterpret_cast<uint32_t*>(c.vprev);
     uint32_t total = 0;
     for (int r0 = 0; r0 < n_list; r0 += 32) {
         const int e = r0 + lane;
@@ -232,8 +322,8 @@ __device__ __noinline__ void slow_general(const WarpSlice<PPT> s, const TileCtx 
             const int p = (int)(s.list()[e] & 1023u);
             float cp, cn;
             thresholds_of(c, p, cp, cn);
-            const float b = model_L(s.vs(c.cur)[p], c.eps, c.is_log);
-            const float a = L_prev(s, c, p);
+            const float b = model_L(c.vcur[p], c.eps, c.is_log);
+            const float a = L_prev(s, c, c.vprev, p);
             float r = s.ref()[p];
             uint32_t tl = s.tl()[p];
             s.vu()[p] = a;
@@ -246,33 +336,11 @@ __device__ __noinline__ void slow_general(const WarpSlice<PPT> s, const TileCtx 
             s.tl()[p] = tl;
             s.list()[e] = (uint32_t)p | ((uint32_t)n << 10);
         }
-        int sum = n;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
-        total += (uint32_t)sum;
+        total += __reduce_add_sync(0xffffffffu, (uint32_t)n);
     }
     __syncwarp();
     // one contiguous chunk for the whole warp-frame
-    uint32_t base = kNoChunk;
-    if (total > 0u) {
-        if (pg_end - pg_cur >= total) {
-            base = pg_cur;
-            pg_cur += total;
-        } else {
-            const uint32_t np_ = (total + page_keys - 1u) / page_keys;
-            uint32_t first = 0u;
-            if (lane == 0) first = atomicAdd(page_ctr, np_);
-            first = __shfl_sync(0xffffffffu, first, 0);
-            if ((uint64_t)first + np_ <= (uint64_t)n_pages) {
-                base = first * page_keys;
-                pg_cur = base + total;
-                pg_end = (first + np_) * page_keys;
-            } else {
-                if (lane == 0) atomicOr(err, kErrPageOverflow);
-                pg_cur = pg_end = 0u;
-            }
-        }
-    }
+    const uint32_t base = take_keys(pg_cur, pg_end, total, lane, page_keys, n_pages, page_ctr, err);
     *chunk_off = base == kNoChunk ? 0u : base;
     *chunk_cnt = base == kNoChunk ? 0u : total;
     uint32_t carry = 0;
@@ -304,6 +372,7 @@ __device__ __noinline__ void slow_general(const WarpSlice<PPT> s, const TileCtx 
         }
         carry += (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
     }
+    __syncwarp();
 }
 
 template <int PPT>
@@ -331,9 +400,17 @@ __device__ __forceinline__ uint32_t outside4(const float4 v, const float4 u, con
            ((v.z < u.z && v.z > d.z) ? 0u : 4u) | ((v.w < u.w && v.w > d.w) ? 0u : 8u);
 }
 
+// Start and length of interval j of the step.
+__device__ __forceinline__ void interval_of(int64_t ta0, int D0, int dt, int j, uint32_t& ta, float& Df)
+{
+    ta = (uint32_t)(ta0 + (j == 0 ? 0 : (int64_t)D0 + (int64_t)(j - 1) * dt));
+    Df = (float)(j == 0 ? D0 : dt);
+}
+
 template <int PPT, int WARPS, int PF, typename KeyT>
 __global__ void __launch_bounds__(WARPS * 32) emit_kernel(const __grid_constant__ StepLaunch L)
 {
+    (void)PF;   // one pair of frames in flight whatever the prefetch setting
     constexpr int NQ = PPT / 4;
     constexpr int WPX = 32 * PPT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -423,172 +500,211 @@ __global__ void __launch_bounds__(WARPS * 32) emit_kernel(const __grid_constant_
             *reinterpret_cast<float4*>(s.vu() + p) = make_float4(u[0], u[1], u[2], u[3]);
             *reinterpret_cast<float4*>(s.vd() + p) = make_float4(d[0], d[1], d[2], d[3]);
         }
-        uint32_t lvalid = init ? 0u : valid;   // lb holds L of the previous frame
+        uint32_t lvalid = init ? 0u : valid;   // lb holds L of the frame before the next one
 
-        // frame pipeline: PF frames in flight per lane
+        // frame pipeline: one pair of frames in flight per lane
         const float* fp = sdp->frames + lane_g;
-        float4 buf[PF][NQ];
+        float4 buf[2][NQ];
 #pragma unroll
-        for (int u = 0; u < PF; ++u)
+        for (int u = 0; u < 2; ++u)
             if (u < T) load_frame<PPT>(buf[u], fp + (int64_t)u * fstride, nvq, vec, lane_left, pol_stream);
-
-        for (int f0 = 0; f0 < T; f0 += PF) {
+        int fs = 0;
+        if (init && T > 0) {
+            // frame 0 initialises the state; the pairs start at frame 1
 #pragma unroll
-            for (int u = 0; u < PF; ++u) {
-                const int f = f0 + u;
-                if (f >= T) break;
-                c.cur = f & 1;
-                float* vc = s.vs(c.cur);
-                uint32_t trig = 0u;
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    const int p = q * 128 + lane * 4;
-                    *reinterpret_cast<float4*>(vc + p) = buf[u][q];
-                    trig |= outside4(buf[u][q], *reinterpret_cast<const float4*>(s.vu() + p),
-                                     *reinterpret_cast<const float4*>(s.vd() + p)) << (q * 4);
-                }
-                trig &= valid;
-                if (f + PF < T) load_frame<PPT>(buf[u], fp + (int64_t)(f + PF) * fstride, nvq, vec, lane_left, pol_stream);
-                if (init && f == 0) {
-                    for (int k = 0; k < PPT; ++k) {
-                        if (!((valid >> k) & 1u)) continue;
-                        const int p = (k >> 2) * 128 + lane * 4 + (k & 3);
-                        float cp, cn;
-                        thresholds_of(c, p, cp, cn);
-                        const float Lv = model_L(vc[p], c.eps, c.is_log);
-                        s.ref()[p] = Lv;
-                        s.lb()[p] = Lv;
-                        s.vu()[p] = raw_bound_up(__fadd_rn(Lv, cp), c.eps, c.is_log);
-                        s.vd()[p] = raw_bound_dn(__fsub_rn(Lv, cn), c.eps, c.is_log);
-                    }
-                    lvalid = valid;
-                    continue;
-                }
-                const int j = f - init;                       // interval index
-                if (!__any_sync(0xffffffffu, trig != 0u)) {
-                    if (lane == 0) chunk_col[(int64_t)j * n_tiles] = make_uint2(0u, 0u);
-                    lvalid = 0u;
-                    continue;
-                }
-                c.ta = (uint32_t)(ta0 + (j == 0 ? 0 : (int64_t)D0 + (int64_t)(j - 1) * dt));
-                c.Df = (float)(j == 0 ? D0 : dt);
-
-                // trigger list in pixel order: group q, then lane, then component
-                uint32_t packed = 0u;
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) packed |= (uint32_t)__popc((trig >> (q * 4)) & 15u) << (q * 8);
-                uint32_t incl = packed;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t nb = __shfl_up_sync(0xffffffffu, incl, d);
-                    if (lane >= d) incl += nb;
-                }
-                const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-                const uint32_t ex = incl - packed;
-                int n_list = 0;
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    int pos = n_list + (int)((ex >> (q * 8)) & 255u);
-                    uint32_t m = (trig >> (q * 4)) & 15u;
-                    while (m) {
-                        const int cbit = __ffs(m) - 1;
-                        m &= m - 1u;
-                        s.list()[pos++] = (uint32_t)(q * 128 + lane * 4 + cbit);
-                    }
-                    n_list += (int)((tot >> (q * 8)) & 255u);
-                }
-                s.lvm()[lane] = lvalid;
-                __syncwarp();
-
-                if (n_list <= 32) {
-                    // one round: lane e handles list entry e
-                    int n = 0;
-                    KeyT k0 = 0, k1 = 0;
-                    int p = 0;
-                    float cp = 0.f, cn = 0.f, a = 0.f, b = 0.f, r0 = 0.f;
-                    uint32_t tl0 = 0u;
-                    if (lane < n_list) {
-                        p = (int)s.list()[lane];
-                        thresholds_of(c, p, cp, cn);
-                        b = model_L(vc[p], c.eps, c.is_log);
-                        a = L_prev(s, c, p);
-                        r0 = s.ref()[p];
-                        tl0 = s.tl()[p];
-                        float r = r0;
-                        uint32_t tl = tl0;
-                        n = pixel_events<1, KeyT>(r, tl, a, b, cp, cn, c.ta, c.Df, c.R,
-                                                  (KeyT)(c.g0 + p) << 1, c.tshift, k0, k1, nullptr);
-                        s.ref()[p] = r;
-                        s.tl()[p] = tl;
-                        s.lb()[p] = b;
-                        s.vu()[p] = raw_bound_up(__fadd_rn(r, cp), c.eps, c.is_log);
-                        s.vd()[p] = raw_bound_dn(__fsub_rn(r, cn), c.eps, c.is_log);
-                    }
-                    int excl_n;
-                    uint32_t total;
-                    if (__any_sync(0xffffffffu, n > 3)) {
-                        int in = n;
-#pragma unroll
-                        for (int d = 1; d < 32; d <<= 1) {
-                            const int nb = __shfl_up_sync(0xffffffffu, in, d);
-                            if (lane >= d) in += nb;
-                        }
-                        excl_n = in - n;
-                        total = (uint32_t)__shfl_sync(0xffffffffu, in, 31);
-                    } else {
-                        const uint32_t b0 = __ballot_sync(0xffffffffu, (n & 1) != 0);
-                        const uint32_t b1 = __ballot_sync(0xffffffffu, (n & 2) != 0);
-                        excl_n = __popc(b0 & lt) + 2 * __popc(b1 & lt);
-                        total = (uint32_t)(__popc(b0) + 2 * __popc(b1));
-                    }
-                    uint32_t base = kNoChunk;
-                    if (total > 0u) {
-                        if (pg_end - pg_cur >= total) {
-                            base = pg_cur;
-                            pg_cur += total;
-                        } else {
-                            const uint32_t np_ = (total + L.page_keys - 1u) / L.page_keys;
-                            uint32_t first = 0u;
-                            if (lane == 0) first = atomicAdd(&L.ctl->page_ctr, np_);
-                            first = __shfl_sync(0xffffffffu, first, 0);
-                            if ((uint64_t)first + np_ <= (uint64_t)L.n_pages) {
-                                base = first * L.page_keys;
-                                pg_cur = base + total;
-                                pg_end = (first + np_) * L.page_keys;
-                            } else {
-                                if (lane == 0) atomicOr(&L.ctl->err, kErrPageOverflow);
-                                pg_cur = pg_end = 0u;
-                            }
-                        }
-                    }
-                    if (lane == 0)
-                        chunk_col[(int64_t)j * n_tiles] =
-                            make_uint2(base == kNoChunk ? 0u : base, base == kNoChunk ? 0u : total);
-                    if (base != kNoChunk && n > 0) {
-                        KeyT* out = keys + (size_t)base + (size_t)excl_n;
-                        if (n <= 2) {
-                            out[0] = k0;
-                            if (n == 2) out[1] = k1;
-                        } else {
-                            float r = r0;
-                            uint32_t tl = tl0;
-                            pixel_events<2, KeyT>(r, tl, a, b, cp, cn, c.ta, c.Df, c.R,
-                                                  (KeyT)(c.g0 + p) << 1, c.tshift, k0, k1, out);
-                        }
-                    }
-                } else {
-                    uint32_t off = 0u, cntv = 0u;
-                    slow_general<PPT, KeyT>(s, c, lane, n_list, keys, L.page_keys, L.n_pages,
-                                            &L.ctl->page_ctr, &L.ctl->err, pg_cur, pg_end, &off, &cntv);
-                    if (lane == 0) chunk_col[(int64_t)j * n_tiles] = make_uint2(off, cntv);
-                }
-                __syncwarp();
-                lvalid = trig;
+            for (int q = 0; q < NQ; ++q)
+                *reinterpret_cast<float4*>(s.vs(0) + q * 128 + lane * 4) = buf[0][q];
+            for (int k = 0; k < PPT; ++k) {
+                if (!((valid >> k) & 1u)) continue;
+                const int p = (k >> 2) * 128 + lane * 4 + (k & 3);
+                float cp, cn;
+                thresholds_of(c, p, cp, cn);
+                const float Lv = model_L(s.vs(0)[p], c.eps, c.is_log);
+                s.ref()[p] = Lv;
+                s.lb()[p] = Lv;
+                s.vu()[p] = raw_bound_up(__fadd_rn(Lv, cp), c.eps, c.is_log);
+                s.vd()[p] = raw_bound_dn(__fsub_rn(Lv, cn), c.eps, c.is_log);
             }
+            lvalid = valid;
+            fs = 1;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) buf[0][q] = buf[1][q];
+            if (2 < T) load_frame<PPT>(buf[1], fp + 2 * fstride, nvq, vec, lane_left, pol_stream);
+        }
+        __syncwarp();
+
+        for (int f0 = fs; f0 < T; f0 += 2) {
+            const int nf = (T - f0 >= 2) ? 2 : 1;
+            float* v0 = s.vs(f0 % 3);
+            float* v1 = s.vs((f0 + 1) % 3);
+            float* vp = s.vs((f0 + 2) % 3);               // frame f0 - 1
+            uint32_t trig0 = 0u, trig1 = 0u;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int p = q * 128 + lane * 4;
+                const float4 u4 = *reinterpret_cast<const float4*>(s.vu() + p);
+                const float4 d4 = *reinterpret_cast<const float4*>(s.vd() + p);
+                *reinterpret_cast<float4*>(v0 + p) = buf[0][q];
+                trig0 |= outside4(buf[0][q], u4, d4) << (q * 4);
+                if (nf == 2) {
+                    *reinterpret_cast<float4*>(v1 + p) = buf[1][q];
+                    trig1 |= outside4(buf[1][q], u4, d4) << (q * 4);
+                }
+            }
+            trig0 &= valid;
+            trig1 &= valid;
+            if (f0 + 2 < T) load_frame<PPT>(buf[0], fp + (int64_t)(f0 + 2) * fstride, nvq, vec, lane_left, pol_stream);
+            if (f0 + 3 < T) load_frame<PPT>(buf[1], fp + (int64_t)(f0 + 3) * fstride, nvq, vec, lane_left, pol_stream);
+            const int j0 = f0 - init;                     // intervals of the pair's frames
+            const uint32_t mall = trig0 | trig1;
+            if (!__any_sync(0xffffffffu, mall != 0u)) {
+                if (lane == 0) {
+                    chunk_col[(int64_t)j0 * n_tiles] = make_uint2(0u, 0u);
+                    if (nf == 2) chunk_col[(int64_t)(j0 + 1) * n_tiles] = make_uint2(0u, 0u);
+                }
+                lvalid = 0u;
+                continue;
+            }
+            s.lvm()[lane] = lvalid;
+            const int n_list = build_list<PPT>(mall, trig0, lane, s.list());
+            __syncwarp();
+
+            if (n_list <= 32) {
+                // one round: lane e handles list entry e over the pair's frames
+                uint32_t ta0i, ta1i;
+                float Df0, Df1;
+                interval_of(ta0, D0, dt, j0, ta0i, Df0);
+                interval_of(ta0, D0, dt, j0 + 1, ta1i, Df1);
+                int n0 = 0, n1 = 0, p = 0;
+                KeyT k00 = 0, k01 = 0, k10 = 0, k11 = 0, pixkey = 0;
+                float cp = 0.f, cn = 0.f, a = 0.f, b = 0.f, cL = 0.f, rs0 = 0.f, rs1 = 0.f;
+                uint32_t ts0 = 0u, ts1 = 0u;
+                if (lane < n_list) {
+                    const uint32_t ent = s.list()[lane];
+                    p = (int)(ent & 1023u);
+                    const bool both = (ent >> 10) & 1u;
+                    pixkey = (KeyT)(c.g0 + p) << 1;
+                    thresholds_of(c, p, cp, cn);
+                    float r = s.ref()[p];
+                    uint32_t tl = s.tl()[p];
+                    b = model_L(v0[p], c.eps, c.is_log);
+                    if (both) {
+                        a = L_prev(s, c, vp, p);
+                        rs0 = r;
+                        ts0 = tl;
+                        n0 = pixel_events<1, KeyT>(r, tl, a, b, cp, cn, ta0i, Df0, c.R, pixkey, c.tshift, k00, k01,
+                                                   nullptr);
+                    }
+                    cL = b;
+                    if (nf == 2) {
+                        cL = model_L(v1[p], c.eps, c.is_log);
+                        rs1 = r;
+                        ts1 = tl;
+                        n1 = pixel_events<1, KeyT>(r, tl, b, cL, cp, cn, ta1i, Df1, c.R, pixkey, c.tshift, k10, k11,
+                                                   nullptr);
+                    }
+                    s.ref()[p] = r;
+                    s.tl()[p] = tl;
+                    s.lb()[p] = cL;
+                    s.vu()[p] = raw_bound_up(__fadd_rn(r, cp), c.eps, c.is_log);
+                    s.vd()[p] = raw_bound_dn(__fsub_rn(r, cn), c.eps, c.is_log);
+                }
+                int ex0, ex1;
+                uint32_t tot0, tot1;
+                count_prefix(n0, lane, ex0, tot0);
+                count_prefix(n1, lane, ex1, tot1);
+                const uint32_t base = take_keys(pg_cur, pg_end, tot0 + tot1, lane, L.page_keys, L.n_pages,
+                                                &L.ctl->page_ctr, &L.ctl->err);
+                if (lane == 0) {
+                    chunk_col[(int64_t)j0 * n_tiles] =
+                        make_uint2(base == kNoChunk ? 0u : base, base == kNoChunk ? 0u : tot0);
+                    if (nf == 2)
+                        chunk_col[(int64_t)(j0 + 1) * n_tiles] =
+                            make_uint2(base == kNoChunk ? 0u : base + tot0, base == kNoChunk ? 0u : tot1);
+                }
+                if (base != kNoChunk) {
+                    if (n0 > 0) {
+                        KeyT* out = keys + (size_t)base + (size_t)ex0;
+                        if (n0 <= 2) {
+                            out[0] = k00;
+                            if (n0 == 2) out[1] = k01;
+                        } else {
+                            float rr = rs0;
+                            uint32_t tt = ts0;
+                            pixel_events<2, KeyT>(rr, tt, a, b, cp, cn, ta0i, Df0, c.R, pixkey, c.tshift, k00, k01,
+                                                  out);
+                        }
+                    }
+                    if (n1 > 0) {
+                        KeyT* out = keys + (size_t)base + tot0 + (size_t)ex1;
+                        if (n1 <= 2) {
+                            out[0] = k10;
+                            if (n1 == 2) out[1] = k11;
+                        } else {
+                            float rr = rs1;
+                            uint32_t tt = ts1;
+                            pixel_events<2, KeyT>(rr, tt, b, cL, cp, cn, ta1i, Df1, c.R, pixkey, c.tshift, k10, k11,
+                                                  out);
+                        }
+                    }
+                }
+                lvalid = mall;
+            } else {
+                // many pixels at once: the general path, frame by frame
+                uint32_t off = 0u, cntv = 0u;
+                int n0l = 0;
+                if (__any_sync(0xffffffffu, trig0 != 0u)) {
+                    __syncwarp();
+                    n0l = build_list<PPT>(trig0, 0u, lane, s.list());
+                    __syncwarp();
+                }
+                if (n0l > 0) {
+                    interval_of(ta0, D0, dt, j0, c.ta, c.Df);
+                    c.vcur = v0;
+                    c.vprev = vp;
+                    slow_general<PPT, KeyT>(s, c, lane, n0l, keys, L.page_keys, L.n_pages, &L.ctl->page_ctr,
+                                            &L.ctl->err, pg_cur, pg_end, &off, &cntv);
+                    lvalid = trig0;
+                } else {
+                    lvalid = 0u;
+                }
+                if (lane == 0) chunk_col[(int64_t)j0 * n_tiles] = make_uint2(off, cntv);
+                if (nf == 2) {
+                    __syncwarp();
+                    // the second frame against the bounds after the first
+                    uint32_t t1 = 0u;
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        const int pq = q * 128 + lane * 4;
+                        t1 |= outside4(*reinterpret_cast<const float4*>(v1 + pq),
+                                       *reinterpret_cast<const float4*>(s.vu() + pq),
+                                       *reinterpret_cast<const float4*>(s.vd() + pq))
+                              << (q * 4);
+                    }
+                    t1 &= valid;
+                    off = 0u;
+                    cntv = 0u;
+                    if (__any_sync(0xffffffffu, t1 != 0u)) {
+                        s.lvm()[lane] = lvalid;
+                        const int n1l = build_list<PPT>(t1, 0u, lane, s.list());
+                        __syncwarp();
+                        interval_of(ta0, D0, dt, j0 + 1, c.ta, c.Df);
+                        c.vcur = v1;
+                        c.vprev = v0;
+                        slow_general<PPT, KeyT>(s, c, lane, n1l, keys, L.page_keys, L.n_pages, &L.ctl->page_ctr,
+                                                &L.ctl->err, pg_cur, pg_end, &off, &cntv);
+                        lvalid = t1;
+                    } else {
+                        lvalid = 0u;
+                    }
+                    if (lane == 0) chunk_col[(int64_t)(j0 + 1) * n_tiles] = make_uint2(off, cntv);
+                }
+            }
+            __syncwarp();
         }
 
         // shared memory -> state
-        const float* vl = s.vs((T - 1) & 1);
+        const float* vl = s.vs((T - 1) % 3);
         for (int k = 0; k < PPT; ++k) {
             if (!((valid >> k) & 1u)) continue;
             const int p = (k >> 2) * 128 + lane * 4 + (k & 3);
