@@ -303,9 +303,10 @@ int neurosim_evsim_batch_counters(neurosim_evsim_batch *b, uint64_t *launches, u
 void neurosim_evsim_batch_destroy(neurosim_evsim_batch *b);
 
 /* ------------------------------------------------------------------------
- * Autotuner: picks the emission tile (pixels_per_thread) and the frame
- * prefetch depth for a workload by timing every variant on the caller's
- * frames.  The paper has no autotuner (it fixes one thread per pixel).
+ * Autotuner: picks the emission tile (pixels_per_thread: 8 or 16) for a
+ * workload by timing every variant on the caller's frames (prefetch_frames
+ * is reported as 2: the kernel keeps one pair of frames in flight).  The
+ * paper has no autotuner (it fixes one thread per pixel).
  *
  * Times `repeats` (>= 1) steps of n_frames frames (DEVICE [T][H][W] FP32 at
  * spacing dt_us) with each variant on a fresh simulator of params p (the
