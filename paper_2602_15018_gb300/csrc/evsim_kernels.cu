@@ -434,26 +434,18 @@ __global__ void __launch_bounds__(kSortThreads) sort_kernel(const __grid_constan
             // order) into one array, then sort between two shared arrays
             KeyT* X = sbuf;
             KeyT* Y = sbuf + N;
-            const KeyT* keys = reinterpret_cast<const KeyT*>(L.keys);
-            // chunk of every key (16-bit, in Y until the first pass), then
-            // consecutive threads copy consecutive keys, all of a thread's
-            // loads (up to 16) in flight before its stores
-            uint16_t* owner = reinterpret_cast<uint16_t*>(Y);
-            for (int c = tid; c < nt; c += THREADS)
-                for (uint32_t k = cpre[c]; k < cpre[c + 1]; ++k) owner[k] = (uint16_t)c;
-            __syncthreads();
-            for (uint32_t i0 = tid; i0 < N; i0 += 16 * THREADS) {
-                KeyT v[16];
+            const ChunkSrc<KeyT> csrc{reinterpret_cast<const KeyT*>(L.keys), cpre, coff, nt};
+            // consecutive threads take consecutive keys; four independent
+            // chunk searches and loads in flight per thread
+            for (uint32_t i0 = tid; i0 < N; i0 += 4 * THREADS) {
+                KeyT v[4];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
+                for (int u = 0; u < 4; ++u) {
                     const uint32_t i = i0 + u * THREADS;
-                    if (i < N) {
-                        const int c = owner[i];
-                        v[u] = keys[(size_t)coff[c] + (i - cpre[c])];
-                    }
+                    v[u] = (i < N) ? csrc(i) : (KeyT)0;
                 }
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
+                for (int u = 0; u < 4; ++u) {
                     const uint32_t i = i0 + u * THREADS;
                     if (i < N) X[i] = v[u];
                 }
