@@ -114,6 +114,24 @@ def dist_env():
     return ws, rank, local
 
 
+def combine_ranks(dist, device, ms: float, n_events: int = 0):
+    """Whole-job timing over the ranks of a replica run: the slowest rank's
+    time (every rank's work counts only when all have finished) and the events
+    of all ranks.  With dist None (one process) the inputs come back."""
+    if dist is None:
+        return ms, n_events
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(n_events)], device=device, dtype=torch.float64)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(e.item())
+
+
+def job_value(px_frames_per_rank: int, ws: int, ms: float) -> float:
+    """Whole-job Mpixel-frames/s: every rank's pixel-frames over the slowest rank's time."""
+    return px_frames_per_rank * ws / (ms / 1e3) / 1e6
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -270,19 +288,10 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     st1 = sim.stats()
     sim.set_profiling(False)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        ev_t = torch.tensor([n_events], device=dev, dtype=torch.float64)
-        dist.all_reduce(ev_t, op=dist.ReduceOp.SUM)
-        n_events_all = int(ev_t.item())
-    else:
-        n_events_all = n_events
+    ms, n_events_all = combine_ranks(dist, dev, ms, n_events)
 
     px_frames_step = T * npix
-    total_px = px_frames_step * args.steps * ws
-    value = total_px / (ms / 1e3) / 1e6
+    value = job_value(px_frames_step * args.steps, ws, ms)
     launches = int(st1["kernel_launches"] - st0["kernel_launches"])
     timed = st1["timed_steps"] - st0["timed_steps"]
     emit_ms = (st1["emit_ms"] - st0["emit_ms"]) / max(1, timed)
@@ -322,12 +331,8 @@ def run_ours(args):
         for kk in range(args.e2e_steps):
             d2h += e2e_step(kk + 2)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": round(px_frames_step * args.e2e_steps * ws / e2e_s / 1e6, 1),
+        e2e_ms, _ = combine_ranks(dist, dev, (time.perf_counter() - t0) * 1e3)
+        e2e = {"value": round(job_value(px_frames_step * args.e2e_steps, ws, e2e_ms), 1),
                "unit": "Mpixel-frames/s",
                "h2d_bytes_per_step": 4 * px_frames_step,
                "d2h_bytes_per_step": int(d2h / args.e2e_steps)}
@@ -457,12 +462,9 @@ def run_batch(args):
     ms = e0.elapsed_time(e1)
     la1, _ = batch.counters()
     launches = (la1 - la0) + 5 * args.steps    # graph replays are not counted by the library
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, n_events_all = combine_ranks(dist, dev, ms, n_events)
     px_step = T * npix
-    value = px_step * args.steps * ws / (ms / 1e3) / 1e6
+    value = job_value(px_step * args.steps, ws, ms)
     ev_step = n_events / max(1, args.steps)
     alg = 4.0 * px_step + 32.0 * npix + 4.0 * ev_step
     peak, peak_src = measured_peaks()
@@ -477,7 +479,7 @@ def run_batch(args):
                        "pixels_per_frame_step": npix, "frames_per_step": T, "dt_us": DT,
                        "parallelism": f"replicas x{ws} (independent batches)",
                        "l2": "inputs 4*T*sum(H*W) bytes per step, far larger than L2; no flush"},
-            "events_per_s": round(n_events * ws / (ms / 1e3), 1),
+            "events_per_s": round(n_events_all / (ms / 1e3), 1),
             "events_per_step": round(ev_step, 1),
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
