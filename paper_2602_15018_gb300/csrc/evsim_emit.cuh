@@ -11,9 +11,10 @@
 // pixel p = q*128 + lane*4 + c (q < PPT/4, c < 4) is loaded by lane `lane`
 // as part of its q-th float4, so every load instruction of the warp reads 512
 // contiguous bytes.  The exact per-pixel state (ref, t_last, last computed
-// log intensity), the raw inputs of the current and previous frame and the
-// pixel's filter bounds live in the warp's slice of shared memory, indexed by
-// p; per-pixel thresholds are read from global memory when needed.
+// log intensity), the raw inputs of the frame before the current pair and of
+// the pair, and the pixel's filter bounds live in the warp's slice of shared
+// memory, indexed by p; per-pixel thresholds are read from global memory when
+// needed.
 //
 // Fast path (every pixel, every frame): the raw input v is compared with
 // bounds vd < v < vu chosen so that inside them the model's log intensity of
