@@ -395,6 +395,35 @@ cudaError_t conv_halo_bn(neurosim_interp* h, const bf16* buf, int cstride, int o
     return utma::launch_halo_conv<BN, SW, SWA, CC>(g, h->sms, h->stream);
 }
 
+// As conv_halo_bn with the weights streamed per (tap, 64-channel) K tile, for
+// inputs whose weights do not fit resident (C a multiple of 64).
+template <int BN, int CC, class EP>
+cudaError_t conv_halo_stream_bn(neurosim_interp* h, const bf16* buf, int cstride, int off, int flip, int N, int H,
+                                int W, const bf16* wpacked, int n_out, const EP& ep)
+{
+    utma::HaloArgs<EP> g;
+    const cuuint64_t dims[4] = {(cuuint64_t)cstride, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t strides[3] = {(cuuint64_t)cstride * 2u, (cuuint64_t)W * cstride * 2u,
+                                   (cuuint64_t)H * W * cstride * 2u};
+    const cuuint32_t box[4] = {64u, (cuuint32_t)utma::kHaloW, 3u, 1u};
+    if (!utma::encode_tiled(&g.ta, 4, buf, dims, strides, box, 128) ||
+        !utma::encode_kmajor(&g.tb, wpacked, n_out, 9 * CC, BN, 128))
+        return cudaErrorInvalidValue;
+    g.ep = ep;
+    g.C = CC;
+    g.off = off;
+    g.flip = flip;
+    g.W = W;
+    g.H = H;
+    g.N = N;
+    g.n_tiles = N * H * ((W + 127) / 128);
+    g.n_out = n_out;
+    g.err = h->err;
+    g.limit_ns = 2000000000ull;
+    h->launches += 1;
+    return utma::launch_halo_conv_stream<BN, CC>(g, h->sms, h->stream);
+}
+
 // out (H x W) = conv3x3 with padding 1 and the given stride of the view
 // [off, off + C) of `buf` (stride H x stride W); flip = 1 for the data
 // gradient (taps mirrored, stride 1).  C must be a multiple of 64 (128-byte
@@ -403,6 +432,12 @@ template <class EP>
 cudaError_t conv_tma(neurosim_interp* h, const bf16* buf, int cstride, int off, int C, int flip, int N, int H, int W,
                      const bf16* wpacked, int n_out, const EP& ep, int stride = 1)
 {
+    if (stride == 1 && W >= 128 && n_out <= 128 && ((C == 128) || (C == 64 && n_out > 64))) {
+        if (C == 128)
+            return n_out <= 64 ? conv_halo_stream_bn<64, 128>(h, buf, cstride, off, flip, N, H, W, wpacked, n_out, ep)
+                               : conv_halo_stream_bn<128, 128>(h, buf, cstride, off, flip, N, H, W, wpacked, n_out, ep);
+        return conv_halo_stream_bn<128, 64>(h, buf, cstride, off, flip, N, H, W, wpacked, n_out, ep);
+    }
     if (stride == 1 && W >= 128 && n_out <= 64 && (C == 32 || C == 64 || (C == 8 && !flip && n_out <= 32))) {
         if (C == 8)
             return conv_halo_bn<32, 128, 0, 8>(h, buf, cstride, off, C, flip, N, H, W, wpacked, n_out, ep);

@@ -586,4 +586,212 @@ cudaError_t launch_halo_conv(const HaloArgs<EP>& g, int num_sms, cudaStream_t st
     return cudaGetLastError();
 }
 
+// ---- 3 x 3 stride-1 convolution from halo tiles, weights streamed ---------------------------
+// For inputs whose weights of all taps do not fit in shared memory beside two
+// halos (C a multiple of 64 with 128 output channels, or C = 128): the halo of
+// a tile comes one 64-channel box (3 x 130 pixels, 128-byte swizzle) at a time
+// through a ring of two box slots, and the weights one (tap, 64-channel) K
+// tile at a time through a ring of kHaloBStages stages.  The K loop of a tile
+// runs box by box, tap by tap; tile t + 1's first box loads while tile t's
+// second box is multiplied.  Taps are shifted descriptors into the box as in
+// halo_conv_kernel; warps as there (4 = loads, 5 = MMAs, 0-3 = epilogue, two
+// TMEM accumulators).
+constexpr int kHaloBStages = 4;
+
+template <int BN>
+__host__ __device__ constexpr size_t halo_stream_smem_bytes()
+{
+    return 1024 + 2 * (size_t)halo_box_stride(128) + (size_t)kHaloBStages * BN * 128 + 256;
+}
+
+template <int BN, int CC, class EP>
+__global__ void __launch_bounds__(kHaloThreads) halo_conv_stream_kernel(const __grid_constant__ HaloArgs<EP> g)
+{
+    static_assert(CC % 64 == 0 && BN % 16 == 0 && BN >= 16 && BN <= 128, "shape");
+    constexpr uint32_t TC = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
+    constexpr int NBOX = CC / 64;
+    constexpr int S = kHaloBStages;
+    constexpr uint32_t B_BYTES = BN * 128;           // one (tap, 64-channel) K tile of the weights
+    constexpr uint32_t BOX = halo_box_stride(128);
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024u - (umma::smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* sA = smem;                        // two box slots
+    unsigned char* sB = smem + 2 * (size_t)BOX;      // weight stages
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sB + (size_t)S * B_BYTES);
+    uint64_t* afull = bar;                           // [2] box landed
+    uint64_t* aempty = bar + 2;                      // [2] box consumed
+    uint64_t* bfull = bar + 4;                       // [S] weight tile landed
+    uint64_t* bempty = bfull + S;                    // [S] weight tile consumed
+    uint64_t* tfull = bempty + S;                    // [2] accumulator complete
+    uint64_t* tempty = tfull + 2;                    // [2] accumulator drained
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
+    __shared__ unsigned int s_fail;
+    const int tiles_x = (g.W + 127) / 128;
+    const int per = g.H * tiles_x;
+
+    if (tid == 0) {
+        s_fail = 0u;
+        for (int k = 0; k < 2; ++k) {
+            umma::mbar_init(&afull[k], 1);
+            umma::mbar_init(&aempty[k], 1);
+            umma::mbar_init(&tfull[k], 1);
+            umma::mbar_init(&tempty[k], 4);
+        }
+        for (int k = 0; k < S; ++k) {
+            umma::mbar_init(&bfull[k], 1);
+            umma::mbar_init(&bempty[k], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) umma::tmem_alloc(tslot, 2 * TC);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(BM, BN, false, false);
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // producer: per tile, per box: the box, then its 9 weight tiles
+            uint32_t ia = 0, ib = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < g.n_tiles; tile += gridDim.x) {
+                const int n = tile / per;
+                const int rem = tile - n * per;
+                const int y0 = rem / tiles_x;
+                const int x0 = (rem - y0 * tiles_x) * 128;
+                for (int box = 0; ok && box < NBOX; ++box) {
+                    const uint32_t sa = ia & 1u, ua = ia >> 1;
+                    if (ia >= 2 && !umma::mbar_wait(&aempty[sa], (ua - 1u) & 1u, g.limit_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    if (*(volatile unsigned int*)&s_fail) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&afull[sa], halo_box_bytes(128));
+                    tma_load_4d(sA + (size_t)sa * BOX, &g.ta, g.off + 64 * box, x0 - 1, y0 - 1, n, &afull[sa]);
+                    ++ia;
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const uint32_t sb = ib % S, ub = ib / S;
+                        if (ib >= S && !umma::mbar_wait(&bempty[sb], (ub - 1u) & 1u, g.limit_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(&bfull[sb], B_BYTES);
+                        tma_load_2d(sB + (size_t)sb * B_BYTES, &g.tb, tap * CC + 64 * box, 0, &bfull[sb]);
+                        ++ib;
+                    }
+                }
+            }
+            if (!ok) {
+                atomicOr(&s_fail, 1u);
+                // let the copies in flight land before the CTA leaves (bounded)
+                for (uint32_t j = ia >= 2 ? ia - 2 : 0; j < ia; ++j)
+                    umma::mbar_wait(&afull[j & 1u], (j >> 1) & 1u, g.limit_ns);
+                for (uint32_t j = ib >= (uint32_t)S ? ib - S : 0; j < ib; ++j)
+                    umma::mbar_wait(&bfull[j % S], (j / S) & 1u, g.limit_ns);
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // MMA issuer: per tile, per box, per tap, 4 K = 16 steps inside the box's 128-byte rows
+            uint32_t ia = 0, ib = 0, it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < g.n_tiles; tile += gridDim.x, ++it) {
+                const uint32_t b = it & 1u, use = it >> 1;
+                if (it >= 2 && !umma::mbar_wait(&tempty[b], (use - 1u) & 1u, g.limit_ns)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t d = tmem + b * TC;
+                int k = 0;
+                for (int box = 0; ok && box < NBOX; ++box) {
+                    const uint32_t sa = ia & 1u, ua = ia >> 1;
+                    if (!umma::mbar_wait(&afull[sa], ua & 1u, g.limit_ns) || *(volatile unsigned int*)&s_fail) {
+                        ok = false;
+                        break;
+                    }
+                    ++ia;
+                    const uint32_t a0 = umma::smem_u32(sA + (size_t)sa * BOX);
+                    const uint64_t ad0 = umma::smem_desc(a0, 16u, 1024u) | ((uint64_t)2u << 61);
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const uint32_t sb = ib % S, ub = ib / S;
+                        if (!umma::mbar_wait(&bfull[sb], ub & 1u, g.limit_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        ++ib;
+                        umma::fence_after_sync();
+                        const uint64_t bd0 = desc_sw<128>(umma::smem_u32(sB + (size_t)sb * B_BYTES), 0);
+                        const int dy = tap / 3, dx = tap % 3;
+                        const uint32_t shift = (uint32_t)(g.flip ? (2 - dy) * kHaloW + (2 - dx) : dy * kHaloW + dx);
+#pragma unroll
+                        for (int c16 = 0; c16 < 4; ++c16, ++k) {
+                            const uint32_t aoff = shift * 128u + (uint32_t)c16 * 32u;
+                            umma::mma_bf16(d, ad0 + (aoff >> 4), bd0 + (((uint32_t)c16 * 32u) >> 4), idesc,
+                                           k > 0 ? 1u : 0u);
+                        }
+                        umma::mma_commit(&bempty[sb]);
+                    }
+                    if (ok) umma::mma_commit(&aempty[sa]);
+                }
+                if (ok) umma::mma_commit(&tfull[b]);
+            }
+            if (!ok) atomicOr(&s_fail, 1u);
+        }
+    } else {
+        // epilogue warps 0-3: TMEM lanes 32 w .. 32 w + 31 = tile rows
+        uint32_t it = 0;
+        for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++it) {
+            const uint32_t b = it & 1u, use = it >> 1;
+            bool ok = umma::mbar_wait(&tfull[b], use & 1u, g.limit_ns);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) atomicOr(&s_fail, 1u);
+                break;
+            }
+            umma::fence_after_sync();
+            const int n = tile / per;
+            const int rem = tile - n * per;
+            const int y0 = rem / tiles_x;
+            const int x0 = (rem - y0 * tiles_x) * 128;
+            const int x = x0 + warp * 32 + lane;
+            const int row = x < g.W ? (n * g.H + y0) * g.W + x : -1;
+            const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + b * TC;
+            drain_row<BN>(lane_addr, row, g.n_out, g.ep);
+            umma::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (tid == 0 && s_fail) atomicOr(g.err, kErrTimeout);
+    if (warp == 0) umma::tmem_dealloc(tmem, 2 * TC);
+}
+
+template <int BN, int CC, class EP>
+cudaError_t launch_halo_conv_stream(const HaloArgs<EP>& g, int num_sms, cudaStream_t stream)
+{
+    if (g.C != CC) return cudaErrorInvalidValue;
+    constexpr size_t smem = halo_stream_smem_bytes<BN>();
+    cudaError_t e = cudaFuncSetAttribute(halo_conv_stream_kernel<BN, CC, EP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, halo_conv_stream_kernel<BN, CC, EP>, kHaloThreads,
+                                                      smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    constexpr int tc = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
+    per_sm = std::min(per_sm, 512 / (2 * tc));
+    const int grid = std::min(g.n_tiles, num_sms * per_sm);
+    halo_conv_stream_kernel<BN, CC, EP><<<grid, kHaloThreads, smem, stream>>>(g);
+    return cudaGetLastError();
+}
+
+
 }  // namespace utma

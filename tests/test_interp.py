@@ -7,7 +7,8 @@ derived from that: outputs within 1 % of the residual scale, gradients within
 a few BF16 ulps (2^-8) relative in norm.  Shapes: batch 2, 16 x 24 (several
 128-row tiles at full size, ragged tails at the quarter size), and 1 x 8 x 128
 and 1 x 8 x 160, whose full-size 3x3 layers run from halo tiles (rows of 128
-pixels; at width 160 the second tile of a row reaches past the image).
+pixels; at width 160 the second tile of a row reaches past the image), and
+1 x 8 x 256, whose half-size 128-channel layers stream their weights.
 """
 import numpy as np
 import pytest
@@ -74,7 +75,7 @@ def test_param_roundtrip_and_untrained_is_linear():
     net.close()
 
 
-SHAPES = [(2, 16, 24), (1, 8, 128), (1, 8, 160)]
+SHAPES = [(2, 16, 24), (1, 8, 128), (1, 8, 160), (1, 8, 256)]
 
 
 @pytest.mark.parametrize("N,H,W", SHAPES)
