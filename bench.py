@@ -716,18 +716,22 @@ def run_batched_learned(args):
     def timed(plain, steps):
         bt = make_batch(plain)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # at most 4 intervals pend between drains (max_pending_steps)
         for k in range(args.warmup):
             if not plain:
                 predict(k % 2)
             bt.step(slot=k % 2)
+            if (k + 1) % 4 == 0:
+                bt.drain(to="cuda")
         bt.drain(to="cuda")
         torch.cuda.synchronize()
         e0.record(st)
-        for k in range(args.warmup, args.warmup + steps):
+        for j in range(steps):
+            k = args.warmup + j
             if not plain:
                 predict(k % 2)
             bt.step(slot=k % 2)
-            if (k + 1) % 4 == 0:
+            if (j + 1) % 4 == 0:
                 bt.drain(to="cuda")
         bt.drain(to="cuda")
         e1.record(st)

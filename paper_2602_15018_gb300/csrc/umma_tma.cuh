@@ -591,17 +591,31 @@ cudaError_t launch_halo_conv(const HaloArgs<EP>& g, int num_sms, cudaStream_t st
 // halos (C a multiple of 64 with 128 output channels, or C = 128): the halo of
 // a tile comes one 64-channel box (3 x 130 pixels, 128-byte swizzle) at a time
 // through a ring of two box slots, and the weights one (tap, 64-channel) K
-// tile at a time through a ring of kHaloBStages stages.  The K loop of a tile
-// runs box by box, tap by tap; tile t + 1's first box loads while tile t's
-// second box is multiplied.  Taps are shifted descriptors into the box as in
-// halo_conv_kernel; warps as there (4 = loads, 5 = MMAs, 0-3 = epilogue, two
-// TMEM accumulators).
-constexpr int kHaloBStages = 4;
+// tile at a time through a ring of halo_stream_stages<BN>() stages.  The K
+// loop of a tile runs box by box, tap by tap; tile t + 1's first box loads
+// while tile t's second box is multiplied.  Taps are shifted descriptors into
+// the box as in halo_conv_kernel; warps as there (4 = loads, 5 = MMAs, 0-3 =
+// epilogue, two TMEM accumulators).
+//
+// Every tile re-reads its weights from L2.  The ring holds 4 K tiles: 12
+// stages (64 output channels) measured no faster on GB300, and 7 (128 output
+// channels) 12 % slower.
+constexpr size_t kHaloSmemMax = 227u * 1024u;   // dynamic shared memory per CTA
+constexpr size_t kHaloStreamTail = 512;         // barriers (4 + 2 S + 4) and the TMEM slot
+constexpr int kHaloStreamMaxStages = 4;
+
+template <int BN>
+__host__ __device__ constexpr int halo_stream_stages()
+{
+    constexpr size_t room = kHaloSmemMax - 1024 - 2 * (size_t)halo_box_stride(128) - kHaloStreamTail;
+    return room / ((size_t)BN * 128) < (size_t)kHaloStreamMaxStages ? (int)(room / ((size_t)BN * 128))
+                                                                     : kHaloStreamMaxStages;
+}
 
 template <int BN>
 __host__ __device__ constexpr size_t halo_stream_smem_bytes()
 {
-    return 1024 + 2 * (size_t)halo_box_stride(128) + (size_t)kHaloBStages * BN * 128 + 256;
+    return 1024 + 2 * (size_t)halo_box_stride(128) + (size_t)halo_stream_stages<BN>() * BN * 128 + kHaloStreamTail;
 }
 
 template <int BN, int CC, class EP>
@@ -610,7 +624,9 @@ __global__ void __launch_bounds__(kHaloThreads) halo_conv_stream_kernel(const __
     static_assert(CC % 64 == 0 && BN % 16 == 0 && BN >= 16 && BN <= 128, "shape");
     constexpr uint32_t TC = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
     constexpr int NBOX = CC / 64;
-    constexpr int S = kHaloBStages;
+    constexpr int S = halo_stream_stages<BN>();
+    static_assert(S >= 2 && (4 + 2 * S + 4) * 8 + 4 <= (int)kHaloStreamTail, "weight ring");
+    static_assert(halo_stream_smem_bytes<BN>() <= kHaloSmemMax, "shared memory");
     constexpr uint32_t B_BYTES = BN * 128;           // one (tap, 64-channel) K tile of the weights
     constexpr uint32_t BOX = halo_box_stride(128);
     extern __shared__ unsigned char smem_raw[];
