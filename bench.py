@@ -538,7 +538,7 @@ def run_learned(args):
         a.record(st)
         fr = scenes.render_frames(sc, T, device=dev, chunk=32)
         b.record(st)
-        n = len(learned.events_of(fr, False, **CONFIG2_SIM))
+        n = len(learned.events_of(fr, False, launches=ev_launches, **CONFIG2_SIM))
         c.record(st)
         torch.cuda.synchronize()
         return a.elapsed_time(b), b.elapsed_time(c), n
@@ -550,7 +550,7 @@ def run_learned(args):
         b.record(st)
         seq = learned.interpolate_sequence(net, log_intensity(keys))
         c.record(st)
-        n = len(learned.events_of(seq, True, **CONFIG2_SIM))
+        n = len(learned.events_of(seq, True, launches=ev_launches, **CONFIG2_SIM))
         d.record(st)
         torch.cuda.synchronize()
         return a.elapsed_time(b), b.elapsed_time(c), c.elapsed_time(d), n
@@ -566,6 +566,7 @@ def run_learned(args):
         torch.cuda.synchronize()
         return a.elapsed_time(b)
 
+    ev_launches = []                # kernels of each event simulation
     for _ in range(args.warmup):
         plain_once()
         learned_once()
@@ -573,12 +574,15 @@ def run_learned(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    ev_launches.clear()
+    net_l0 = net.launches()
     tw0 = time.time()
     pl = [plain_once() for _ in range(args.steps)]
     le = [learned_once() for _ in range(args.steps)]
     un = [unet_only() for _ in range(args.steps)]
     tw1 = time.time()
     clocks.stop()
+    launches = net.launches() - net_l0 + sum(ev_launches)
     med = lambda xs: float(statistics.median(xs))
     r_all, e_plain = med([x[0] for x in pl]), med([x[1] for x in pl])
     r_keys, u_ms, e_learn = med([x[0] for x in le]), med([x[1] for x in le]), med([x[2] for x in le])
@@ -605,7 +609,7 @@ def run_learned(args):
             "e2e_speedup_vs_plain": round((r_all + e_plain) / (r_keys + u_ms + e_learn), 3),
             "train": {"steps": args.train_steps, "seconds": round(train_s, 1), "crops": "16 x 256x256",
                       "loss": [[int(i), round(float(l), 6)] for i, l in losses]},
-            "gpu_launches": None,
+            "gpu_launches": int(launches),
             "roofline": {"bound": "tensor", "achieved": round(tflops, 1), "peak": peak, "unit": "TFLOP/s",
                          "frac": round(tflops / peak, 4), "traffic": None,
                          "kernel": "U-Net forward, 8 HD intervals (9 tcgen05 GEMMs)", "peak_source": peak_src},
@@ -713,6 +717,8 @@ def run_batched_learned(args):
     # ---- timing
     st = torch.cuda.current_stream()
 
+    timed_launches = {}             # library kernels inside each timed loop
+
     def timed(plain, steps):
         bt = make_batch(plain)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -725,6 +731,7 @@ def run_batched_learned(args):
                 bt.drain(to="cuda")
         bt.drain(to="cuda")
         torch.cuda.synchronize()
+        l0 = bt.counters()[0] + net.launches()
         e0.record(st)
         for j in range(steps):
             k = args.warmup + j
@@ -736,6 +743,7 @@ def run_batched_learned(args):
         bt.drain(to="cuda")
         e1.record(st)
         torch.cuda.synchronize()
+        timed_launches[plain] = bt.counters()[0] + net.launches() - l0
         bt.close()
         return e0.elapsed_time(e1) / steps
 
@@ -778,7 +786,7 @@ def run_batched_learned(args):
             "e2e_speedup_vs_plain_with_render": round((render_4_ms + ms_plain) / (render_4_ms / 4 + ms_learn), 3),
             "train": {"steps": args.train_steps, "seconds": round(train_s, 1)},
             "setup_render_s": round(render_s, 1),
-            "gpu_launches": None,
+            "gpu_launches": int(sum(timed_launches.values())),
             "roofline": {"bound": "tensor", "achieved": round(tflops, 1), "peak": peak, "unit": "TFLOP/s",
                          "frac": round(tflops / peak, 4), "traffic": None,
                          "kernel": "U-Net forward over all sensors of one interval (learned minus plain step)",

@@ -65,12 +65,16 @@ def interpolate_sequence(net: Interpolator, keys: torch.Tensor, chunk: int = 8) 
     return seq
 
 
-def events_of(frames: torch.Tensor, input_is_log: bool, t0_us: int = 0, dt_us: int = 1000, **sim):
-    """Events (host uint64 records) of one sensor over `frames` [T, H, W]."""
+def events_of(frames: torch.Tensor, input_is_log: bool, t0_us: int = 0, dt_us: int = 1000, launches=None, **sim):
+    """Events (host uint64 records) of one sensor over `frames` [T, H, W].
+    If `launches` is a list, the number of kernels the simulator launched is
+    appended to it."""
     T, H, W = frames.shape
     s = EventSim(W, H, input_is_log=input_is_log, max_frames_per_step=T, **sim)
     s.step(frames.contiguous(), t0_us, dt_us)
     ev, _ = s.drain()
+    if launches is not None:
+        launches.append(int(s.stats()["kernel_launches"]))
     s.close()
     return ev
 
