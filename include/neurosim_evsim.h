@@ -55,7 +55,8 @@ enum neurosim_status {
     NEUROSIM_E_OVERFLOW = 4,  /* event or interval capacity exceeded          */
     NEUROSIM_E_TIMEOUT = 5,   /* a bounded device wait gave up                */
     NEUROSIM_E_NOMEM = 6,     /* device or host allocation failed             */
-    NEUROSIM_E_STATE = 7      /* call not allowed in the handle's state       */
+    NEUROSIM_E_STATE = 7,     /* call not allowed in the handle's state       */
+    NEUROSIM_E_IO = 8         /* a file could not be opened, read or written  */
 };
 
 /* Opaque simulator handle for one sensor; owned by the library. */
@@ -374,6 +375,20 @@ int neurosim_interp_gradients(neurosim_interp *h, const float *clips_dev, int32_
  * set_params also resets the optimiser state.  Synchronise. */
 int neurosim_interp_get_params(neurosim_interp *h, float *host, int64_t n);
 int neurosim_interp_set_params(neurosim_interp *h, const float *host, int64_t n);
+
+/* Checkpoints of the network.  save writes the FP32 parameters and, when
+ * with_optimizer != 0, the AdamW moments and step count to the HOST file
+ * `path` (written to path + ".tmp", then renamed over path).  load reads
+ * such a file into a network of any max sizes: the parameters, and the
+ * optimiser state if the file holds it (else the state is reset, as by
+ * set_params).  Layout (little-endian): "NSIMUNT1", uint32 version 1,
+ * uint32 flags (bit 0: moments present), int64 parameter count, int64 step,
+ * the FP32 arrays, then the FNV-1a 64-bit hash of all preceding bytes.
+ * Errors: NEUROSIM_E_IO (open, read, write, rename), NEUROSIM_E_INVALID (not
+ * a checkpoint, other version, other parameter count, truncated, hash
+ * mismatch; the network is then unchanged), NEUROSIM_E_CUDA.  Synchronise. */
+int neurosim_interp_save(neurosim_interp *h, const char *path, int32_t with_optimizer);
+int neurosim_interp_load(neurosim_interp *h, const char *path);
 
 /* Kernels launched by the network so far. */
 int neurosim_interp_launches(neurosim_interp *h, uint64_t *launches);

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libneurosim_evsim.so")
 
 NEUROSIM_OK = 0
 STATUS = {1: "E_INVALID", 2: "E_CUDA", 3: "E_TIME", 4: "E_OVERFLOW", 5: "E_TIMEOUT",
-          6: "E_NOMEM", 7: "E_STATE"}
+          6: "E_NOMEM", 7: "E_STATE", 8: "E_IO"}
 
 # Every exported function of the C ABI, by header section.
 EXPORTS = [
@@ -32,7 +32,8 @@ EXPORTS = [
     "neurosim_evsim_batch_destroy", "neurosim_evsim_autotune", "neurosim_debug_umma_gemm",
     "neurosim_interp_param_count", "neurosim_interp_create", "neurosim_interp_forward",
     "neurosim_interp_train_step", "neurosim_interp_gradients", "neurosim_interp_get_params",
-    "neurosim_interp_set_params", "neurosim_interp_launches", "neurosim_interp_destroy",
+    "neurosim_interp_set_params", "neurosim_interp_save", "neurosim_interp_load",
+    "neurosim_interp_launches", "neurosim_interp_destroy",
     "neurosim_event_f1", "neurosim_log_intensity", "neurosim_time_surface", "neurosim_event_frames",
 ]
 
@@ -173,6 +174,10 @@ def lib():
             L.neurosim_interp_get_params.argtypes = [vp, vp, i64]
             L.neurosim_interp_set_params.restype = C.c_int
             L.neurosim_interp_set_params.argtypes = [vp, vp, i64]
+            L.neurosim_interp_save.restype = C.c_int
+            L.neurosim_interp_save.argtypes = [vp, C.c_char_p, i32]
+            L.neurosim_interp_load.restype = C.c_int
+            L.neurosim_interp_load.argtypes = [vp, C.c_char_p]
             L.neurosim_interp_launches.restype = C.c_int
             L.neurosim_interp_launches.argtypes = [vp, C.POINTER(u64)]
             L.neurosim_interp_destroy.restype = None

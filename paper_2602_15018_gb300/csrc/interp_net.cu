@@ -28,6 +28,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <string>
 #include <vector>
 
 #include "../../include/neurosim_evsim.h"
@@ -821,6 +822,150 @@ int neurosim_interp_set_params(neurosim_interp* h, const float* host, int64_t n)
     ICUDA(cudaMemsetAsync(h->m, 0, (size_t)n * 4, h->stream));
     ICUDA(cudaMemsetAsync(h->v, 0, (size_t)n * 4, h->stream));
     h->step = 0;
+    int rc = pack_all(h);
+    if (rc) return rc;
+    ICUDA(cudaStreamSynchronize(h->stream));
+    return NEUROSIM_OK;
+}
+
+// ---- checkpoints -------------------------------------------------------------------------
+// File layout (little-endian, as written by the host):
+//   0  char[8]  "NSIMUNT1"
+//   8  uint32   format version (1)
+//  12  uint32   flags: bit 0 = the AdamW moments follow the parameters
+//  16  int64    n = parameter count
+//  24  int64    optimiser step count
+//  32  float[n] parameters, then float[n] first and float[n] second moments if flagged
+//  end uint64   FNV-1a 64-bit hash of every byte before it
+namespace {
+
+constexpr char kCkptMagic[8] = {'N', 'S', 'I', 'M', 'U', 'N', 'T', '1'};
+constexpr uint32_t kCkptVersion = 1;
+constexpr size_t kCkptHeader = 32;
+
+uint64_t fnv1a(const unsigned char* p, size_t n)
+{
+    uint64_t x = 0xcbf29ce484222325ull;
+    for (size_t i = 0; i < n; ++i) {
+        x ^= p[i];
+        x *= 0x100000001b3ull;
+    }
+    return x;
+}
+
+bool host_little_endian()
+{
+    const uint32_t one = 1u;
+    unsigned char b;
+    memcpy(&b, &one, 1);
+    return b == 1;
+}
+
+}  // namespace
+
+int neurosim_interp_save(neurosim_interp* h, const char* path, int32_t with_optimizer)
+{
+    if (!h || !path) return fail(NEUROSIM_E_INVALID, "NULL argument");
+    if (!host_little_endian()) return fail(NEUROSIM_E_INVALID, "checkpoints are little-endian only");
+    const int64_t n = h->lay.total;
+    const int arrays = with_optimizer ? 3 : 1;
+    const size_t body = (size_t)arrays * (size_t)n * 4;
+    std::vector<unsigned char> buf;
+    try {
+        buf.resize(kCkptHeader + body + 8);
+    } catch (...) {
+        return fail(NEUROSIM_E_NOMEM, "no host memory for a %zu-byte checkpoint", buf.size());
+    }
+    unsigned char* b = buf.data();
+    const uint32_t flags = with_optimizer ? 1u : 0u;
+    const int64_t step = h->step;
+    memcpy(b, kCkptMagic, 8);
+    memcpy(b + 8, &kCkptVersion, 4);
+    memcpy(b + 12, &flags, 4);
+    memcpy(b + 16, &n, 8);
+    memcpy(b + 24, &step, 8);
+    {
+        IGuard g(h->device);
+        float* src[3] = {h->params, h->m, h->v};
+        for (int a = 0; a < arrays; ++a)
+            ICUDA(cudaMemcpyAsync(b + kCkptHeader + (size_t)a * n * 4, src[a], (size_t)n * 4, cudaMemcpyDeviceToHost,
+                                  h->stream));
+        ICUDA(cudaStreamSynchronize(h->stream));
+    }
+    const uint64_t hash = fnv1a(b, kCkptHeader + body);
+    memcpy(b + kCkptHeader + body, &hash, 8);
+    // write beside the target, then rename: a reader never sees half a file
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "wb");
+    if (!f) return fail(NEUROSIM_E_IO, "cannot open %s for writing", tmp.c_str());
+    const size_t put = fwrite(b, 1, buf.size(), f);
+    const int closed = fclose(f);
+    if (put != buf.size() || closed != 0) {
+        remove(tmp.c_str());
+        return fail(NEUROSIM_E_IO, "short write to %s", tmp.c_str());
+    }
+    if (rename(tmp.c_str(), path) != 0) {
+        remove(tmp.c_str());
+        return fail(NEUROSIM_E_IO, "cannot rename %s to %s", tmp.c_str(), path);
+    }
+    return NEUROSIM_OK;
+}
+
+int neurosim_interp_load(neurosim_interp* h, const char* path)
+{
+    if (!h || !path) return fail(NEUROSIM_E_INVALID, "NULL argument");
+    if (!host_little_endian()) return fail(NEUROSIM_E_INVALID, "checkpoints are little-endian only");
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(NEUROSIM_E_IO, "cannot open %s", path);
+    std::vector<unsigned char> buf;
+    unsigned char chunk[1 << 16];
+    size_t got = 0;
+    bool too_big = false;
+    const int64_t n = h->lay.total;
+    const size_t max_size = kCkptHeader + 3 * (size_t)n * 4 + 8;
+    while ((got = fread(chunk, 1, sizeof chunk, f)) > 0) {
+        if (buf.size() + got > max_size) {
+            too_big = true;
+            break;
+        }
+        buf.insert(buf.end(), chunk, chunk + got);
+    }
+    const bool read_error = ferror(f) != 0;
+    fclose(f);
+    if (read_error) return fail(NEUROSIM_E_IO, "read error on %s", path);
+    if (too_big) return fail(NEUROSIM_E_INVALID, "%s: larger than any checkpoint of this network", path);
+    if (buf.size() < kCkptHeader + 8 || memcmp(buf.data(), kCkptMagic, 8) != 0)
+        return fail(NEUROSIM_E_INVALID, "%s: not an interpolator checkpoint", path);
+    const unsigned char* b = buf.data();
+    uint32_t version = 0, flags = 0;
+    int64_t fn = 0, step = 0;
+    memcpy(&version, b + 8, 4);
+    memcpy(&flags, b + 12, 4);
+    memcpy(&fn, b + 16, 8);
+    memcpy(&step, b + 24, 8);
+    if (version != kCkptVersion) return fail(NEUROSIM_E_INVALID, "%s: format version %u, expected %u", path, version,
+                                             kCkptVersion);
+    if (fn != n) return fail(NEUROSIM_E_INVALID, "%s: %lld parameters, the network has %lld", path, (long long)fn,
+                             (long long)n);
+    if ((flags & ~1u) != 0u || step < 0) return fail(NEUROSIM_E_INVALID, "%s: bad header", path);
+    const int arrays = (flags & 1u) ? 3 : 1;
+    const size_t body = (size_t)arrays * (size_t)n * 4;
+    if (buf.size() != kCkptHeader + body + 8)
+        return fail(NEUROSIM_E_INVALID, "%s: %zu bytes, expected %zu (truncated?)", path, buf.size(),
+                    kCkptHeader + body + 8);
+    uint64_t hash = 0;
+    memcpy(&hash, b + kCkptHeader + body, 8);
+    if (hash != fnv1a(b, kCkptHeader + body)) return fail(NEUROSIM_E_INVALID, "%s: checksum mismatch", path);
+    IGuard g(h->device);
+    float* dst[3] = {h->params, h->m, h->v};
+    for (int a = 0; a < 3; ++a) {
+        if (a < arrays)
+            ICUDA(cudaMemcpyAsync(dst[a], b + kCkptHeader + (size_t)a * n * 4, (size_t)n * 4, cudaMemcpyHostToDevice,
+                                  h->stream));
+        else
+            ICUDA(cudaMemsetAsync(dst[a], 0, (size_t)n * 4, h->stream));
+    }
+    h->step = arrays == 3 ? step : 0;
     int rc = pack_all(h);
     if (rc) return rc;
     ICUDA(cudaStreamSynchronize(h->stream));

@@ -8,6 +8,7 @@ tensors ([3, 3, Cin, Cout], [Cin, 2, 2, Cout], [32, 3] and biases).
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 import torch
@@ -100,6 +101,13 @@ class Interpolator:
     def set_params(self, flat: np.ndarray) -> None:
         flat = np.ascontiguousarray(flat, np.float32)
         check(lib().neurosim_interp_set_params(self._h, C.c_void_p(flat.ctypes.data), self.n_params))
+
+    def save(self, path: str, with_optimizer: bool = True) -> None:
+        """Checkpoint: parameters, and the AdamW state unless with_optimizer is False."""
+        check(lib().neurosim_interp_save(self._h, os.fsencode(path), int(bool(with_optimizer))))
+
+    def load(self, path: str) -> None:
+        check(lib().neurosim_interp_load(self._h, os.fsencode(path)))
 
     def launches(self) -> int:
         n = C.c_uint64(0)

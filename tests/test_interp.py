@@ -9,6 +9,7 @@ a few BF16 ulps (2^-8) relative in norm.  Shapes: batch 2, 16 x 24 (several
 and 1 x 8 x 160, whose full-size 3x3 layers run from halo tiles (rows of 128
 pixels; at width 160 the second tile of a row reaches past the image), and
 1 x 8 x 256, whose half-size 128-channel layers stream their weights.
+Checkpoints are checked against their documented byte layout.
 """
 import numpy as np
 import pytest
@@ -161,3 +162,88 @@ def test_training_beats_linear_interpolation():
     assert np.mean(losses[-10:]) < 0.9 * np.mean(losses[:10]), losses
     assert e1 < 0.9 * e0, (e0, e1)
     net.close()
+
+
+def _fnv1a(b: bytes) -> int:
+    x = 0xcbf29ce484222325
+    for c in b:
+        x = ((x ^ c) * 0x100000001b3) & 0xFFFFFFFFFFFFFFFF
+    return x
+
+
+def test_checkpoint_layout_and_resume(tmp_path):
+    """save/load: the file holds the documented layout (parsed here byte by
+    byte); a network of other max sizes loads it bit-exactly (parameters and
+    forward output); and a resumed AdamW step matches the uninterrupted one,
+    while a parameters-only checkpoint (moments reset) does not."""
+    from paper_2602_15018_gb300 import Interpolator
+    a = _net(_params(21))
+    for it in range(3):
+        a.train_step(torch.from_numpy(_clips(40 + it, 2, 16, 24)).float().cuda(), 1e-3, 1e-4, want_loss=False)
+    full, bare = str(tmp_path / "full.ckpt"), str(tmp_path / "bare.ckpt")
+    a.save(full)
+    a.save(bare, with_optimizer=False)
+    pa = a.get_params()
+    n = pa.size
+    raw = open(full, "rb").read()
+    assert raw[:8] == b"NSIMUNT1" and len(raw) == 32 + 3 * 4 * n + 8
+    version, flags = np.frombuffer(raw[8:16], "<u4")
+    count, step = np.frombuffer(raw[16:32], "<i8")
+    assert (version, flags, count, step) == (1, 1, n, 3)
+    assert np.array_equal(np.frombuffer(raw[32:32 + 4 * n], "<f4"), pa)
+    assert int(np.frombuffer(raw[-8:], "<u8")[0]) == _fnv1a(raw[:-8])
+    assert len(open(bare, "rb").read()) == 32 + 4 * n + 8
+
+    b = Interpolator(1, 32, 32, seed=9)
+    b.load(full)
+    assert np.array_equal(b.get_params(), pa)
+    c = torch.from_numpy(_clips(77, 1, 16, 24)).float().cuda()
+    assert torch.equal(a.forward(c[:, 0].contiguous(), c[:, 4].contiguous()),
+                       b.forward(c[:, 0].contiguous(), c[:, 4].contiguous()))
+    r = Interpolator(2, 16, 24, seed=9)
+    r.load(bare)
+    clips = torch.from_numpy(_clips(50, 2, 16, 24)).float().cuda()
+    b.close()
+    b = Interpolator(2, 16, 24, seed=9)
+    b.load(full)
+    for net in (a, b, r):
+        net.train_step(clips, 1e-3, 1e-4, want_loss=False)
+    pa, pb, pr = a.get_params(), b.get_params(), r.get_params()
+    d_ab, d_ar = np.abs(pa - pb).max(), np.abs(pa - pr).max()
+    assert d_ar > 1e-4 and d_ab < 0.01 * d_ar, (d_ab, d_ar)
+    for net in (a, b, r):
+        net.close()
+
+
+def test_checkpoint_rejects_bad_files(tmp_path):
+    from paper_2602_15018_gb300 import Interpolator
+    from paper_2602_15018_gb300._lib import NeurosimError
+    a = _net(_params(22))
+    path = str(tmp_path / "a.ckpt")
+    a.save(path, with_optimizer=False)
+    raw = bytearray(open(path, "rb").read())
+    b = Interpolator(2, 16, 24, seed=4)
+    p0 = b.get_params()
+
+    def rejects(data, code, what):
+        bad = str(tmp_path / "bad.ckpt")
+        open(bad, "wb").write(bytes(data))
+        with pytest.raises(NeurosimError) as e:
+            b.load(bad)
+        assert e.value.code == code and what in str(e.value), str(e.value)
+        assert np.array_equal(b.get_params(), p0)          # unchanged
+
+    with pytest.raises(NeurosimError) as e:
+        b.load(str(tmp_path / "missing.ckpt"))
+    assert e.value.code == 8
+    rejects(raw[:-100], 1, "truncated")
+    flipped = bytearray(raw)
+    flipped[1000] ^= 0x40
+    rejects(flipped, 1, "checksum")
+    rejects(b"NOTACKPT" + raw[8:], 1, "not an interpolator checkpoint")
+    other = bytearray(raw[:-8])
+    other[16:24] = np.array([12345], "<i8").tobytes()      # another parameter count, valid hash
+    rejects(other + np.array([_fnv1a(bytes(other))], "<u8").tobytes(), 1, "parameters")
+    assert not (tmp_path / "a.ckpt.tmp").exists()
+    a.close()
+    b.close()
