@@ -463,6 +463,9 @@ def run_batch(args):
     la1, _ = batch.counters()
     launches = (la1 - la0) + 5 * args.steps    # graph replays are not counted by the library
     ms, n_events_all = combine_ranks(dist, dev, ms, n_events)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = batch_cpu_baseline(sensors[:6], first[:6], slot0[:6], T)
     px_step = T * npix
     value = job_value(px_step * args.steps, ws, ms)
     ev_step = n_events / max(1, args.steps)
@@ -486,7 +489,7 @@ def run_batch(args):
                          "frac": round(achieved / peak, 4), "traffic": None,
                          "kernel": "whole step (emission + interval sort + clock), graph replay",
                          "peak_source": peak_src},
-            "e2e": None, "cpu_baseline": None,
+            "e2e": None, "cpu_baseline": cpu,
             "clocks": clocks.summary(tw0, tw1),
         }
         print(json.dumps(line), flush=True)
@@ -583,6 +586,10 @@ def run_learned(args):
     tw1 = time.time()
     clocks.stop()
     launches = net.launches() - net_l0 + sum(ev_launches)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        keys0 = sc.render(np.array([0, 4]), device=dev).cpu().numpy()
+        cpu = learned_cpu_baseline(net, [keys0], [CONFIG2_SIM], "one keyframe interval of the HD clip")
     med = lambda xs: float(statistics.median(xs))
     r_all, e_plain = med([x[0] for x in pl]), med([x[1] for x in pl])
     r_keys, u_ms, e_learn = med([x[0] for x in le]), med([x[1] for x in le]), med([x[2] for x in le])
@@ -613,7 +620,7 @@ def run_learned(args):
             "roofline": {"bound": "tensor", "achieved": round(tflops, 1), "peak": peak, "unit": "TFLOP/s",
                          "frac": round(tflops / peak, 4), "traffic": None,
                          "kernel": "U-Net forward, 8 HD intervals (9 tcgen05 GEMMs)", "peak_source": peak_src},
-            "e2e": None, "cpu_baseline": None,
+            "e2e": None, "cpu_baseline": cpu,
             "clocks": clocks.summary(tw0, tw1),
         }
         print(json.dumps(line), flush=True)
@@ -755,6 +762,15 @@ def run_batched_learned(args):
     ms_learn = timed(False, args.steps)
     tw1 = time.time()
     clocks.stop()
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        keys, sims = [], []
+        for gi, ((W, H), n, _) in enumerate(groups):
+            sc = scenes.TextureScene(W, H, seed=args.seed * 7 + gi * 100003 + 1000 * rank, speed=(150.0, 600.0))
+            keys.append(sc.render(np.array([0, 4]), device=dev).cpu().numpy())
+            sims.append({k: v for k, v in sensors[sum(m for _, m, _ in groups[:gi])].items()
+                         if k not in ("width", "height", "input_is_log")})
+        cpu = learned_cpu_baseline(net, keys, sims, "one keyframe interval of one 320x240 and one 1280x720 sensor")
     # renderer stand-in cost: one keyframe set vs four frame sets per interval
     r0 = time.time()
     for gi, ((W, H), n, _) in enumerate(groups):
@@ -791,7 +807,7 @@ def run_batched_learned(args):
                          "frac": round(tflops / peak, 4), "traffic": None,
                          "kernel": "U-Net forward over all sensors of one interval (learned minus plain step)",
                          "peak_source": peak_src},
-            "e2e": None, "cpu_baseline": None,
+            "e2e": None, "cpu_baseline": cpu,
             "clocks": clocks.summary(tw0, tw1),
         }
         print(json.dumps(line), flush=True)
@@ -820,6 +836,85 @@ def cpu_baseline(args, dev):
             "kind": "oracle",
             "sample": f"first {n} frames of the workload ({px} pixel-frames, {len(ev)} events), "
                       f"single-threaded C oracle, {s:.1f} s"}
+
+
+def batch_cpu_baseline(sensors, first, frames, T):
+    """The event oracle (single thread) on a bounded sample of the batched
+    workload: the first `len(first)` sensors over one whole step."""
+    import oracle
+    px, n_ev, s = 0, 0, 0.0
+    for sn, f0, fr in zip(sensors, first, frames):
+        kw = dict(c_pos=sn["c_pos"], c_neg=sn["c_neg"], sigma_c=sn["sigma_c"], c_min=sn["c_min"],
+                  refractory_us=sn["refractory_us"], seed=sn["seed"])
+        sim = oracle.OracleSim(sn["width"], sn["height"], **kw)
+        seq = np.concatenate([f0.cpu().numpy()[None], fr.cpu().numpy()])
+        t0 = time.perf_counter()
+        ev, _ = sim.step(seq, 0, DT)
+        s += time.perf_counter() - t0
+        n_ev += len(ev)
+        px += T * sn["width"] * sn["height"]
+    sizes = ", ".join(f"{sn['width']}x{sn['height']}" for sn in sensors)
+    return {"value": round(px / s / 1e6, 2), "unit": "Mpixel-frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"sensors {sizes} over one {T}-frame step ({px} pixel-frames, {n_ev} events), "
+                      f"single-threaded C oracle, {s:.1f} s"}
+
+
+def learned_cpu_baseline(net, keys, sims, what):
+    """The learned pipeline's oracle on a bounded sample: per sensor, the
+    oracle log of its intensity keyframes [K, H, W] (host), the FP64 U-Net
+    oracle (BF16 storage mirrored) on the trained parameters, and the event
+    oracle on the resulting log sequence.  Runs in a child process with one
+    BLAS / OpenMP thread, so that it uses exactly one core."""
+    import tempfile
+    from paper_2602_15018_gb300.interp import to_dict
+    params = {k: np.asarray(v, np.float64) for k, v in to_dict(net.get_params()).items()}
+    with tempfile.TemporaryDirectory() as tmp:
+        src = os.path.join(tmp, "sample.npz")
+        arrays = {f"keys{i}": np.ascontiguousarray(k, np.float32) for i, k in enumerate(keys)}
+        arrays.update({f"p_{k}": v for k, v in params.items()})
+        np.savez(src, **arrays)
+        with open(os.path.join(tmp, "sims.json"), "w") as f:
+            json.dump(sims, f)
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-learned-sample", tmp],
+                           env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("learned oracle sample failed: " + r.stderr[-2000:])
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    s = res["unet_s"] + res["events_s"]
+    return {"value": round(res["px"] / s / 1e6, 3), "unit": "Mpixel-frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"{what}: {res['px']} pixel-frames, {res['events']} events; FP64 U-Net oracle "
+                      f"{res['unet_s']:.1f} s + C event oracle {res['events_s']:.1f} s, one thread"}
+
+
+def oracle_learned_sample(tmp):
+    """Child of learned_cpu_baseline: time the oracles on the saved sample."""
+    import oracle
+    from oracle import interp_oracle as io
+    z = np.load(os.path.join(tmp, "sample.npz"))
+    with open(os.path.join(tmp, "sims.json")) as f:
+        sims = json.load(f)
+    p = {k[2:]: z[k] for k in z.files if k.startswith("p_")}
+    px, n_ev, t_unet, t_ev = 0, 0, 0.0, 0.0
+    for i, sim_kw in enumerate(sims):
+        keys = z[f"keys{i}"]
+        K, H, W = keys.shape
+        t0 = time.perf_counter()
+        clamped = (np.minimum(np.maximum(keys, np.float32(0)), np.float32(1e6)) + np.float32(1e-3)).astype(np.float32)
+        L = oracle.mylog(clamped)
+        mid, _ = io.forward(p, L[:-1], L[1:], quantize=True)              # [3, K - 1, H, W]
+        seq = np.empty((4 * (K - 1) + 1, H, W), np.float32)
+        seq[0::4] = L
+        for j in range(3):
+            seq[1 + j::4] = mid[j]
+        t1 = time.perf_counter()
+        ev, _ = oracle.OracleSim(W, H, input_is_log=True, **sim_kw).step(seq, 0, DT)
+        t2 = time.perf_counter()
+        t_unet += t1 - t0
+        t_ev += t2 - t1
+        n_ev += len(ev)
+        px += 4 * (K - 1) * H * W
+    print(json.dumps({"px": px, "events": n_ev, "unet_s": t_unet, "events_s": t_ev}), flush=True)
 
 
 # --------------------------------------------------------------------------
@@ -894,7 +989,11 @@ def main():
     ap.add_argument("--train-steps", type=int, default=8000, help="learned workload: training steps")
     ap.add_argument("--frames", type=int, default=0,
                     help="frames per step (default: the workload's); for small profiling cases")
+    ap.add_argument("--oracle-learned-sample", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_learned_sample:
+        oracle_learned_sample(args.oracle_learned_sample)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
