@@ -315,6 +315,22 @@ struct EpiAct {
     int stride, off;
     const float* bias;
     int relu;
+    static constexpr bool kStaged = true;
+    __device__ __forceinline__ bf16* row_ptr(int row) const { return out + (size_t)row * stride + off; }
+    // columns c0 .. c0 + 31 of one pixel as four 16-byte chunks
+    __device__ __forceinline__ void pack32(int c0, const float (&v)[32], uint4 (&o)[4]) const
+    {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float t[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float s = v[8 * q + i] + bias[c0 + 8 * q + i];
+                t[i] = relu ? fmaxf(s, 0.0f) : s;
+            }
+            o[q] = pack8(t);
+        }
+    }
     __device__ __forceinline__ void store(int row, int c0, const float (&v)[8], int) const
     {
         float o[8];

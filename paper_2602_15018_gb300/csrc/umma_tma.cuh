@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "umma.cuh"
 
@@ -195,6 +196,48 @@ __device__ __forceinline__ void drain_row(uint32_t lane_addr, int row, int n_col
                 ep.store(row, c, u, 0);
             }
         }
+    }
+}
+
+// Epilogues that can also hand over 32 finished columns of one pixel as four
+// 16-byte chunks (EP::kStaged, EP::pack32, EP::row_ptr) are drained through
+// a per-warp shared-memory transpose: a plain drain stores 16 B of each of
+// 32 pixels per instruction, half of a 32-byte sector each, while the staged
+// drain stores 8 pixels x 64 contiguous bytes, whole sectors, and halves the
+// L2 write requests.  The 32 rows of a warp must be consecutive pixels.
+template <class EP, class = void>
+struct ep_staged : std::false_type {};
+template <class EP>
+struct ep_staged<EP, std::void_t<decltype(EP::kStaged)>> : std::bool_constant<EP::kStaged> {};
+
+constexpr int kStageU4 = 4 * 32 * 4;   // 4 epilogue warps x 32 pixels x 4 chunks of 16 B
+
+// Drains TMEM columns [0, BN) of the warp's 32 lanes (= pixels row0 .. row0 +
+// 31, of which the first n_valid exist) through stage (128 uint4 of this
+// warp).  n_cols must be a multiple of 32.
+template <int BN, class EP>
+__device__ __forceinline__ void drain_row_staged(uint32_t lane_addr, int row0, int n_valid, int n_cols, const EP& ep,
+                                                 uint4* stage, int lane)
+{
+    static_assert(BN % 32 == 0, "columns");
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        umma::tmem_ld32(lane_addr + (uint32_t)c0, v);
+        if (c0 >= n_cols) continue;                                   // warp-uniform
+        uint4 o[4];
+        ep.pack32(c0, v, o);
+        // chunk q of pixel l at l * 4 + (q ^ ((l >> 1) & 3)): conflict-free both ways
+#pragma unroll
+        for (int q = 0; q < 4; ++q) stage[lane * 4 + (q ^ ((lane >> 1) & 3))] = o[q];
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int px = 8 * i + (lane >> 2), q = lane & 3;
+            const uint4 val = stage[px * 4 + (q ^ ((px >> 1) & 3))];
+            if (px < n_valid) *reinterpret_cast<uint4*>(ep.row_ptr(row0 + px) + c0 + 8 * q) = val;
+        }
+        __syncwarp();
     }
 }
 
@@ -412,6 +455,7 @@ __global__ void __launch_bounds__(kHaloThreads) halo_conv_kernel(const __grid_co
     uint64_t* tempty = bar + 7;     // [2] accumulator drained by the epilogue
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 9);
     __shared__ unsigned int s_fail;
+    __shared__ uint4 s_stage[ep_staged<EP>::value ? kStageU4 : 1];
     const int tiles_x = (g.W + 127) / 128;
     const int per = g.H * tiles_x;
 
@@ -550,10 +594,16 @@ __global__ void __launch_bounds__(kHaloThreads) halo_conv_kernel(const __grid_co
             const int rem = tile - n * per;
             const int y0 = rem / tiles_x;
             const int x0 = (rem - y0 * tiles_x) * 128;
-            const int x = x0 + warp * 32 + lane;
-            const int row = x < g.W ? (n * g.H + y0) * g.W + x : -1;
             const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + b * TC;
-            drain_row<BN>(lane_addr, row, g.n_out, g.ep);
+            if constexpr (ep_staged<EP>::value) {
+                const int xw = x0 + warp * 32;
+                drain_row_staged<BN>(lane_addr, (n * g.H + y0) * g.W + xw, g.W - xw, g.n_out, g.ep,
+                                     s_stage + warp * 128, lane);
+            } else {
+                const int x = x0 + warp * 32 + lane;
+                const int row = x < g.W ? (n * g.H + y0) * g.W + x : -1;
+                drain_row<BN>(lane_addr, row, g.n_out, g.ep);
+            }
             umma::fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
@@ -565,22 +615,48 @@ __global__ void __launch_bounds__(kHaloThreads) halo_conv_kernel(const __grid_co
     if (warp == 0) umma::tmem_dealloc(tmem, 2 * TC);
 }
 
+// CTAs of a persistent kernel that fit on one SM at once: registers (per-warp
+// allocation in units of 256), shared memory (with the per-block reserve),
+// threads, and the SM's 512 TMEM columns.  Computed from the kernel's
+// attributes: the runtime's occupancy query returned 1 for these kernels on
+// GB300 where the SM holds up to 6 of them (the profiler's own limits).
+inline cudaError_t resident_per_sm(const void* fn, int threads, size_t dyn_smem, int tmem_cols, int* per_sm)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0, reserved = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess)
+        return e;
+    const int warps = (threads + 31) / 32;
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+    int n = warp_regs > 0 ? regs_sm / warp_regs / warps : 32;
+    n = std::min(n, (int)((size_t)smem_sm / (dyn_smem + fa.sharedSizeBytes + (size_t)reserved)));
+    n = std::min(n, thr_sm / threads);
+    n = std::min(n, 512 / tmem_cols);
+    n = std::min(n, 32);
+    *per_sm = n;
+    return n >= 1 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
 template <int BN, int SW, int SWA, int CC, class EP>
 cudaError_t launch_halo_conv(const HaloArgs<EP>& g, int num_sms, cudaStream_t stream)
 {
-    if (g.C != CC) return cudaErrorInvalidValue;
+    if (g.C != CC || (ep_staged<EP>::value && g.n_out % 32 != 0)) return cudaErrorInvalidValue;
     const size_t smem = halo_smem_bytes<BN, SW, SWA>(CC);
     cudaError_t e = cudaFuncSetAttribute(halo_conv_kernel<BN, SW, SWA, CC, EP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, halo_conv_kernel<BN, SW, SWA, CC, EP>, kHaloThreads,
-                                                      smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     // resident CTAs must also fit in the SM's 512 TMEM columns (2 accumulators each)
     constexpr int tc = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
-    per_sm = std::min(per_sm, 512 / (2 * tc));
+    int per_sm = 0;
+    e = resident_per_sm(reinterpret_cast<const void*>(halo_conv_kernel<BN, SW, SWA, CC, EP>), kHaloThreads, smem,
+                        2 * tc, &per_sm);
+    if (e != cudaSuccess) return e;
     const int grid = std::min(g.n_tiles, num_sms * per_sm);
     halo_conv_kernel<BN, SW, SWA, CC, EP><<<grid, kHaloThreads, smem, stream>>>(g);
     return cudaGetLastError();
@@ -643,6 +719,7 @@ __global__ void __launch_bounds__(kHaloThreads) halo_conv_stream_kernel(const __
     uint64_t* tempty = tfull + 2;                    // [2] accumulator drained
     uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
     __shared__ unsigned int s_fail;
+    __shared__ uint4 s_stage[ep_staged<EP>::value ? kStageU4 : 1];
     const int tiles_x = (g.W + 127) / 128;
     const int per = g.H * tiles_x;
 
@@ -774,10 +851,16 @@ __global__ void __launch_bounds__(kHaloThreads) halo_conv_stream_kernel(const __
             const int rem = tile - n * per;
             const int y0 = rem / tiles_x;
             const int x0 = (rem - y0 * tiles_x) * 128;
-            const int x = x0 + warp * 32 + lane;
-            const int row = x < g.W ? (n * g.H + y0) * g.W + x : -1;
             const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + b * TC;
-            drain_row<BN>(lane_addr, row, g.n_out, g.ep);
+            if constexpr (ep_staged<EP>::value) {
+                const int xw = x0 + warp * 32;
+                drain_row_staged<BN>(lane_addr, (n * g.H + y0) * g.W + xw, g.W - xw, g.n_out, g.ep,
+                                     s_stage + warp * 128, lane);
+            } else {
+                const int x = x0 + warp * 32 + lane;
+                const int row = x < g.W ? (n * g.H + y0) * g.W + x : -1;
+                drain_row<BN>(lane_addr, row, g.n_out, g.ep);
+            }
             umma::fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
@@ -792,18 +875,16 @@ __global__ void __launch_bounds__(kHaloThreads) halo_conv_stream_kernel(const __
 template <int BN, int CC, class EP>
 cudaError_t launch_halo_conv_stream(const HaloArgs<EP>& g, int num_sms, cudaStream_t stream)
 {
-    if (g.C != CC) return cudaErrorInvalidValue;
+    if (g.C != CC || (ep_staged<EP>::value && g.n_out % 32 != 0)) return cudaErrorInvalidValue;
     constexpr size_t smem = halo_stream_smem_bytes<BN>();
     cudaError_t e = cudaFuncSetAttribute(halo_conv_stream_kernel<BN, CC, EP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, halo_conv_stream_kernel<BN, CC, EP>, kHaloThreads,
-                                                      smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     constexpr int tc = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
-    per_sm = std::min(per_sm, 512 / (2 * tc));
+    int per_sm = 0;
+    e = resident_per_sm(reinterpret_cast<const void*>(halo_conv_stream_kernel<BN, CC, EP>), kHaloThreads, smem,
+                        2 * tc, &per_sm);
+    if (e != cudaSuccess) return e;
     const int grid = std::min(g.n_tiles, num_sms * per_sm);
     halo_conv_stream_kernel<BN, CC, EP><<<grid, kHaloThreads, smem, stream>>>(g);
     return cudaGetLastError();
