@@ -121,6 +121,13 @@ struct DenseA {
         const int m = tile * BM + r;
         return m < M ? m : -1;
     }
+    // rows 32 w .. 32 w + 31 of a tile are pixels row0 .. row0 + 31 (n_valid exist)
+    __device__ __forceinline__ bool warp_rows(int tile, int w, int& row0, int& n_valid) const
+    {
+        row0 = tile * BM + 32 * w;
+        n_valid = M - row0;
+        return true;
+    }
 };
 
 // 3 x 3 convolution with padding 1 over NHWC activations (4-D map: channels
@@ -161,6 +168,17 @@ struct ConvTapA {
         origin(tile, n, x0, y0);
         const int ty = r / TW, x = x0 + (r - ty * TW), y = y0 + ty;
         return (x < W && y < H) ? (n * H + y) * W + x : -1;
+    }
+    // as DenseA::warp_rows; consecutive only when a warp's 32 rows lie in one tile row
+    __device__ __forceinline__ bool warp_rows(int tile, int w, int& row0, int& n_valid) const
+    {
+        if (TW % 32 != 0) return false;
+        int n, x0, y0;
+        origin(tile, n, x0, y0);
+        const int r = 32 * w, ty = r / TW, x = x0 + (r - ty * TW), y = y0 + ty;
+        row0 = (n * H + y) * W + x;
+        n_valid = y < H ? W - x : 0;
+        return true;
     }
 };
 
@@ -297,6 +315,7 @@ __global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ T
     constexpr uint32_t idesc = umma::idesc_bf16_f32(BM, BN, false, false);
 
     __shared__ unsigned int s_fail;
+    __shared__ uint4 s_stage[ep_staged<EP>::value ? kStageU4 : 1];
     if (tid == 0) s_fail = 0u;
     __syncthreads();
     if (tid == 0) {
@@ -334,9 +353,16 @@ __global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ T
     ok = __syncthreads_and(ok && s_fail == 0u);
     if (ok) {
         const int r = warp * 32 + (tid & 31);
-        const int row = g.a.row_of(tile, r);
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-        drain_row<BN>(lane_addr, row, g.N, g.ep);
+        int row0 = 0, n_valid = 0;
+        if constexpr (ep_staged<EP>::value) {
+            if (g.N % 32 == 0 && g.a.warp_rows(tile, warp, row0, n_valid))
+                drain_row_staged<BN>(lane_addr, row0, n_valid, g.N, g.ep, s_stage + warp * 128, tid & 31);
+            else
+                drain_row<BN>(lane_addr, g.a.row_of(tile, r), g.N, g.ep);
+        } else {
+            drain_row<BN>(lane_addr, g.a.row_of(tile, r), g.N, g.ep);
+        }
     } else if (tid == 0) {
         atomicOr(g.err, kErrTimeout);
     }
