@@ -917,4 +917,167 @@ cudaError_t launch_halo_conv_stream(const HaloArgs<EP>& g, int num_sms, cudaStre
 }
 
 
+// ---- persistent GEMM over pixel rows (1x1 and transposed convolutions) -------------------
+// D[128 x BN] per tile of 128 consecutive rows of A ([M][lda] BF16, columns
+// off .. off + K, 2-D map (lda, M), box (bk, 128)); B = the packed weights
+// [BN][K] (box (bk, BN)), loaded once and kept in shared memory.  As the halo
+// kernels: warp 4 loads A tiles into a ring of kPixStages stages, warp 5
+// issues the MMAs into one of two TMEM accumulators, warps 0-3 drain the other
+// one, so a CTA's loads, MMAs and epilogue overlap across tiles.
+constexpr int kPixStages = 3;
+
+template <class EP>
+struct PixArgs {
+    CUtensorMap ta, tb;
+    EP ep;
+    int M, K, off;
+    int n_tiles, n_out;
+    unsigned int* err;
+    uint64_t limit_ns;
+};
+
+template <int BN, int SW>
+__host__ __device__ constexpr size_t pix_smem_bytes(int K)
+{
+    return 1024 + (size_t)((K + bk_of(SW) - 1) / bk_of(SW)) * (BN + kPixStages * BM) * SW + 256;
+}
+
+template <int BN, int SW, class EP>
+__global__ void __launch_bounds__(kHaloThreads) pix_gemm_kernel(const __grid_constant__ PixArgs<EP> g)
+{
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "tcgen05 N for M = 128");
+    constexpr uint32_t TC = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    constexpr int SBK = bk_of(SW);
+    constexpr uint32_t A_BYTES = BM * SW, B_BYTES = BN * SW;
+    constexpr int S = kPixStages;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024u - (umma::smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_kt = (g.K + SBK - 1) / SBK;
+    unsigned char* sB = smem;                                    // n_kt weight tiles
+    unsigned char* sA = smem + (size_t)n_kt * B_BYTES;           // S stages of n_kt tiles
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sA + (size_t)S * n_kt * A_BYTES);
+    uint64_t* bfull = bar;              // weights landed
+    uint64_t* afull = bar + 1;          // [S] A stage landed
+    uint64_t* aempty = afull + S;       // [S] A stage consumed
+    uint64_t* tfull = aempty + S;       // [2] accumulator complete
+    uint64_t* tempty = tfull + 2;       // [2] accumulator drained
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
+    __shared__ unsigned int s_fail;
+
+    if (tid == 0) {
+        s_fail = 0u;
+        umma::mbar_init(bfull, 1);
+        for (int s = 0; s < S; ++s) {
+            umma::mbar_init(&afull[s], 1);
+            umma::mbar_init(&aempty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            umma::mbar_init(&tfull[b], 1);
+            umma::mbar_init(&tempty[b], 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) umma::tmem_alloc(tslot, 2 * TC);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(BM, BN, false, false);
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // producer: the weights once, then the A tiles of this CTA's row tiles
+            uint32_t issued = 0;
+            mbar_expect_tx(bfull, (uint32_t)n_kt * B_BYTES);
+            for (int kt = 0; kt < n_kt; ++kt) tma_load_2d(sB + (size_t)kt * B_BYTES, &g.tb, kt * SBK, 0, bfull);
+            uint32_t i = 0;
+            for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
+                const uint32_t s = i % S, use = i / S;
+                if (i >= (uint32_t)S && !umma::mbar_wait(&aempty[s], (use - 1u) & 1u, g.limit_ns)) {
+                    atomicOr(&s_fail, 1u);
+                    break;
+                }
+                if (*(volatile unsigned int*)&s_fail) break;
+                issued = i + 1;
+                mbar_expect_tx(&afull[s], (uint32_t)n_kt * A_BYTES);
+                for (int kt = 0; kt < n_kt; ++kt)
+                    tma_load_2d(sA + ((size_t)s * n_kt + kt) * A_BYTES, &g.ta, g.off + kt * SBK, tile * BM,
+                                &afull[s]);
+            }
+            if (*(volatile unsigned int*)&s_fail) {
+                // let the copies in flight land before the CTA leaves (bounded)
+                umma::mbar_wait(bfull, 0u, g.limit_ns);
+                for (uint32_t j = issued >= (uint32_t)S ? issued - S : 0; j < issued; ++j)
+                    umma::mbar_wait(&afull[j % S], (j / S) & 1u, g.limit_ns);
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            bool ok = umma::mbar_wait(bfull, 0u, g.limit_ns);
+            uint32_t i = 0;
+            for (int tile = blockIdx.x; ok && tile < g.n_tiles; tile += gridDim.x, ++i) {
+                const uint32_t s = i % S, b = i & 1u;
+                ok = umma::mbar_wait(&afull[s], (i / S) & 1u, g.limit_ns) &&
+                     (i < 2 || umma::mbar_wait(&tempty[b], ((i >> 1) - 1u) & 1u, g.limit_ns));
+                if (!ok || *(volatile unsigned int*)&s_fail) break;
+                umma::fence_after_sync();
+                const uint32_t a0 = umma::smem_u32(sA + (size_t)s * n_kt * A_BYTES), b0 = umma::smem_u32(sB);
+                const uint32_t d = tmem + b * TC;
+                for (int kt = 0; kt < n_kt; ++kt) {
+#pragma unroll
+                    for (int k = 0; k < SBK / 16; ++k)
+                        umma::mma_bf16(d, desc_sw<SW>(a0 + (uint32_t)kt * A_BYTES, k),
+                                       desc_sw<SW>(b0 + (uint32_t)kt * B_BYTES, k), idesc, (kt > 0 || k > 0) ? 1u : 0u);
+                }
+                umma::mma_commit(&aempty[s]);
+                umma::mma_commit(&tfull[b]);
+            }
+            if (!ok) atomicOr(&s_fail, 1u);
+        }
+    } else {
+        // epilogue warps 0-3: TMEM lanes 32 w .. 32 w + 31 = tile rows
+        uint32_t i = 0;
+        for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
+            const uint32_t b = i & 1u;
+            bool ok = umma::mbar_wait(&tfull[b], (i >> 1) & 1u, g.limit_ns);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) atomicOr(&s_fail, 1u);
+                break;
+            }
+            umma::fence_after_sync();
+            const int row = tile * BM + warp * 32 + lane;
+            const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + b * TC;
+            drain_row<BN>(lane_addr, row < g.M ? row : -1, g.n_out, g.ep);
+            umma::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (tid == 0 && s_fail) atomicOr(g.err, kErrTimeout);
+    if (warp == 0) umma::tmem_dealloc(tmem, 2 * TC);
+}
+
+template <int BN, int SW, class EP>
+cudaError_t launch_pix_gemm(const PixArgs<EP>& g, int num_sms, cudaStream_t stream)
+{
+    const size_t smem = pix_smem_bytes<BN, SW>(g.K);
+    if (g.K < 1 || smem > 227u * 1024u) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(pix_gemm_kernel<BN, SW, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    constexpr int tc = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    int per_sm = 0;
+    e = resident_per_sm(reinterpret_cast<const void*>(pix_gemm_kernel<BN, SW, EP>), kHaloThreads, smem, 2 * tc,
+                        &per_sm);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(g.n_tiles, num_sms * per_sm);
+    if (grid < 1) return cudaSuccess;
+    pix_gemm_kernel<BN, SW, EP><<<grid, kHaloThreads, smem, stream>>>(g);
+    return cudaGetLastError();
+}
+
 }  // namespace utma
