@@ -449,6 +449,24 @@ int neurosim_debug_umma_gemm(int32_t mode, int32_t M, int32_t N, int32_t K, cons
  * input_is_log = 0.  Asynchronous on cuda_stream. */
 int neurosim_log_intensity(const float *I_dev, float *L_dev, int64_t n, float log_eps, void *cuda_stream);
 
+/* Sensor bandwidth limit (Sec. 2 of the paper: "bandwidth limitations" are
+ * among the non-idealities the simulator models and the user may turn off;
+ * the paper gives no model).  This library's reading: a first-order low-pass
+ * filter on each pixel's log intensity, one update per frame,
+ *   s_k = s_{k-1} + alpha (L_k - s_{k-1}),  alpha = 1 - exp(-2 pi f_c dt),
+ * in FP32 as d = L - s, s = fma(alpha, d, s).  L_dev: DEVICE log frames
+ * [n_frames][n_pix] FP32; out_dev: DEVICE [n_frames][n_pix], equal to L_dev
+ * (in place) or not overlapping it; state_dev: DEVICE [n_pix] filter levels,
+ * read unless init != 0 (then set from frame 0, which passes unchanged) and
+ * always written back, so that consecutive calls continue one stream.
+ * alpha in (0, 1]; alpha = 1 follows the frames (within the rounding of
+ * L - s).  Feed the output to
+ * the event model with input_is_log = 1.  Asynchronous on cuda_stream.
+ * Errors: NEUROSIM_E_INVALID (sizes, alpha, NULL or partly overlapping
+ * buffers, init with no frame), NEUROSIM_E_CUDA. */
+int neurosim_lowpass_log(const float *L_dev, float *out_dev, int32_t n_frames, int64_t n_pix, float alpha,
+                         float *state_dev, int32_t init, void *cuda_stream);
+
 /* Evaluates the library's FP32 log (the one the event model uses) on n DEVICE
  * floats x_dev into y_dev on cuda_stream; for verification of the log. */
 int neurosim_debug_log(const float *x_dev, float *y_dev, int64_t n, void *cuda_stream);

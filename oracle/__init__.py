@@ -9,6 +9,7 @@ CUDA library never does, and the two share no code.
 
 Functions (each follows the passage and reading named in the C source):
   mylog                 project FP32 log (reading R1)
+  lowpass_log           sensor bandwidth filter on log frames (reading R9)
   splitmix64_at         SplitMix64 output i of a seeded stream (reading R6)
   normal_ih12           Irwin-Hall(12) normal draw (reading R6)
   threshold_maps        per-pixel thresholds max(c_min, C + sigma z) (R6)
@@ -62,6 +63,8 @@ def _configure(L):
     i64pp = C.POINTER(C.POINTER(C.c_int64))
     L.oracle_mylog.restype = C.c_float
     L.oracle_mylog.argtypes = [C.c_float]
+    L.oracle_lowpass_log.restype = C.c_int
+    L.oracle_lowpass_log.argtypes = [f32p, f32p, C.c_int32, C.c_int64, C.c_float, f32p, C.c_int32]
     L.oracle_mylog_batch.restype = None
     L.oracle_mylog_batch.argtypes = [f32p, f32p, C.c_int64]
     L.oracle_mylog_max_ulp.restype = C.c_double
@@ -116,6 +119,22 @@ def _p(a, ct):
 # --------------------------------------------------------------------------
 # log, random draws, thresholds
 # --------------------------------------------------------------------------
+def lowpass_log(L, alpha, state=None, library=None):
+    """Sensor bandwidth filter (reading R9) over log frames L [T, ...]; returns
+    (filtered frames, state).  state None starts the filter at frame 0."""
+    x = np.ascontiguousarray(L, dtype=np.float32)
+    T = x.shape[0]
+    n = int(x[0].size) if T else (0 if state is None else int(np.asarray(state).size))
+    init = state is None
+    st = np.zeros(n, np.float32) if init else np.ascontiguousarray(state, np.float32).reshape(-1).copy()
+    out = np.empty_like(x)
+    rc = (library or lib()).oracle_lowpass_log(_p(x, C.c_float), _p(out, C.c_float), T, n, float(alpha),
+                                               _p(st, C.c_float), int(init))
+    if rc != 0:
+        raise OracleError(_ERR.get(rc, f"error {rc}"))
+    return out, st
+
+
 def mylog(x, library=None) -> np.ndarray:
     x = np.ascontiguousarray(x, dtype=np.float32)
     y = np.empty_like(x)

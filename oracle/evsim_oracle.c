@@ -45,6 +45,13 @@
  *       nothing.
  *   R8  Output order: interval-major; inside one interval ascending by the
  *       packed record (t, y, x, p), OFF (p = 0) before ON (p = 1).
+ *   R9  Sensor bandwidth (Sec. 2 names "bandwidth limitations" among the
+ *       non-idealities, with no model): a first-order low-pass filter on
+ *       each pixel's log intensity, one update per frame, applied before the
+ *       event model: s_k = s_{k-1} + alpha (L_k - s_{k-1}) with
+ *       alpha = 1 - exp(-2 pi f_c dt) for a cutoff f_c; the filter starts at
+ *       the first frame's value.  FP32: d = L - s rounded, then s = fma(alpha,
+ *       d, s) with one rounding (oracle_lowpass_log below).
  *
  * Packed record (64 bits): [63:32] t (us) | [31:17] y | [16:1] x | [0] p.
  *
@@ -458,6 +465,25 @@ int oracle_evsim_step_f64(int32_t W, int32_t H, const float *frames, int32_t T,
         return ORACLE_E_NOMEM;
     }
     finish(&b, events_out, n_events_out, seg_out, n_seg_out);
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sensor bandwidth filter (reading R9).  L, out: [T][n] FP32 (out may be L); */
+/* state: [n], read unless init (then set to frame 0) and written back.       */
+/* ------------------------------------------------------------------------ */
+int oracle_lowpass_log(const float *L, float *out, int32_t T, int64_t n, float alpha, float *state, int32_t init)
+{
+    if (T < 0 || n < 0 || !(alpha > 0.0f && alpha <= 1.0f) || (init && T == 0)) return ORACLE_E_INVALID;
+    for (int64_t i = 0; i < n; ++i) {
+        float s = init ? L[i] : state[i];
+        for (int32_t k = 0; k < T; ++k) {
+            const float d = L[(int64_t)k * n + i] - s;
+            s = fmaf(alpha, d, s);
+            out[(int64_t)k * n + i] = s;
+        }
+        state[i] = s;
+    }
     return ORACLE_OK;
 }
 

@@ -35,6 +35,7 @@ EXPORTS = [
     "neurosim_interp_set_params", "neurosim_interp_save", "neurosim_interp_load",
     "neurosim_interp_launches", "neurosim_interp_destroy",
     "neurosim_event_f1", "neurosim_log_intensity", "neurosim_time_surface", "neurosim_event_frames",
+    "neurosim_lowpass_log",
 ]
 
 
@@ -186,6 +187,8 @@ def lib():
             L.neurosim_time_surface.argtypes = [vp, i32, i32, C.POINTER(i64), vp, i64, i64, C.c_float, vp]
             L.neurosim_event_frames.restype = C.c_int
             L.neurosim_event_frames.argtypes = [vp, i32, i32, vp, i64, i64, i64, i32, vp]
+            L.neurosim_lowpass_log.restype = C.c_int
+            L.neurosim_lowpass_log.argtypes = [vp, vp, i32, i64, C.c_float, vp, i32, vp]
             L.neurosim_log_intensity.restype = C.c_int
             L.neurosim_log_intensity.argtypes = [vp, vp, i64, C.c_float, vp]
             L.neurosim_event_f1.restype = C.c_int

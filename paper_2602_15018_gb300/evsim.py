@@ -8,6 +8,7 @@ supplies device memory and the CUDA stream.
 from __future__ import annotations
 
 import ctypes as C
+import math
 
 import numpy as np
 import torch
@@ -232,6 +233,39 @@ def log_intensity(frames: torch.Tensor, log_eps: float = 1e-3, out: torch.Tensor
     check(lib().neurosim_log_intensity(C.c_void_p(frames.data_ptr()), C.c_void_p(out.data_ptr()), frames.numel(),
                                        float(log_eps), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
     return out
+
+
+def lowpass_alpha(cutoff_hz: float, dt_us: int) -> float:
+    """Per-frame gain of the first-order bandwidth filter, 1 - exp(-2 pi f_c dt)."""
+    if not (cutoff_hz > 0 and dt_us > 0):
+        raise ValueError("cutoff_hz and dt_us must be positive")
+    return float(np.float32(1.0 - math.exp(-2.0 * math.pi * cutoff_hz * dt_us * 1e-6)))
+
+
+def lowpass_log(L: torch.Tensor, alpha: float, state: torch.Tensor | None = None,
+                out: torch.Tensor | None = None):
+    """Sensor bandwidth limit (library kernel): first-order low-pass of the log
+    frames L [T, H, W] (or [T, n]), s <- s + alpha (L - s) per frame.  With
+    state None the filter starts at frame 0; pass the returned state to the
+    next call to continue the stream.  out may be L (in place).  Returns
+    (filtered frames, state)."""
+    if not (L.is_cuda and L.dtype == torch.float32 and L.is_contiguous() and L.dim() >= 2):
+        raise ValueError("L must be a contiguous float32 CUDA tensor [T, ...]")
+    T = L.shape[0]
+    n = L[0].numel()
+    init = state is None
+    if init:
+        state = torch.empty(n, dtype=torch.float32, device=L.device)
+    elif not (state.is_cuda and state.dtype == torch.float32 and state.is_contiguous() and state.numel() == n):
+        raise ValueError("state must be a contiguous float32 CUDA tensor of one frame's size")
+    if out is None:
+        out = torch.empty_like(L)
+    elif not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.shape == L.shape):
+        raise ValueError("out must match L")
+    check(lib().neurosim_lowpass_log(C.c_void_p(L.data_ptr()), C.c_void_p(out.data_ptr()), T, n, float(alpha),
+                                     C.c_void_p(state.data_ptr()), int(init),
+                                     C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return out, state
 
 
 def _ptr_array(tensors):

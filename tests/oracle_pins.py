@@ -8,7 +8,8 @@ when the oracle disagrees with:
   - brute-force time sampling of the linear interpolant (reading R2),
   - the double-precision libm log (reading R1),
   - the published SplitMix64 test vector and Irwin-Hall moments (reading R6),
-  - invariants of the model (reference band, ordering, time range).
+  - invariants of the model (reference band, ordering, time range),
+  - closed forms of the first-order bandwidth filter (reading R9).
 """
 from __future__ import annotations
 
@@ -262,5 +263,45 @@ def pin_uneven_interval(library):
     assert j[m].tolist() == [0, 0, 0, 1, 1] and np.all(p == 1)
 
 
+def pin_lowpass(library):
+    """Sensor bandwidth filter (reading R9): s_k = s_{k-1} + alpha (L_k - s_{k-1}).
+
+    Closed forms: alpha = 1 follows the frames (within two roundings); a constant input stays
+    constant; a unit step reaches 1 - (1 - alpha)^k after k frames, and with
+    alpha = 1 - exp(-2 pi f_c dt) it reaches 1 - 1/e after 1 / (2 pi f_c dt)
+    frames (the time constant of the continuous first-order filter).
+    Invariants: splitting the frames over two calls with the state carried
+    gives the same bits; pixels are independent."""
+    rng = np.random.default_rng(21)
+    L = (rng.standard_normal((12, 3, 5)) * 0.7 - 2.0).astype(np.float32)
+    out, st = oracle.lowpass_log(L, 1.0, library=library)
+    # alpha = 1: fl(s + fl(L - s)) is L up to the rounding of the difference and of the sum
+    prev = np.concatenate([L[:1], out[:-1]])
+    bound = np.spacing(np.abs(L - prev)) / 2 + np.spacing(np.maximum(np.abs(L), np.abs(out))) / 2
+    assert np.all(np.abs(out - L) <= bound) and np.array_equal(st, out[-1].reshape(-1))
+    c = np.full((9, 4), -1.3, np.float32)
+    out, _ = oracle.lowpass_log(c, 0.37, library=library)
+    assert np.array_equal(out, c)
+    n = 20                                            # frames per time constant
+    alpha = np.float32(1.0 - math.exp(-1.0 / n))      # f_c = 1 / (2 pi n dt)
+    step = np.ones((3 * n + 1, 2), np.float32)
+    step[0] = 0.0
+    out, _ = oracle.lowpass_log(step, alpha, library=library)
+    k = np.arange(3 * n + 1)
+    want = 1.0 - (1.0 - np.float64(alpha)) ** k
+    assert np.max(np.abs(out[:, 0] - want)) < 2e-6, np.max(np.abs(out[:, 0] - want))
+    assert abs(out[n, 0] - (1.0 - math.exp(-1.0))) < 4e-6
+    assert np.all(np.diff(out[:, 0]) >= 0) and out[-1, 0] <= 1.0
+    a = np.float32(0.23)
+    full, st_full = oracle.lowpass_log(L, a, library=library)
+    head, st_head = oracle.lowpass_log(L[:5], a, library=library)
+    tail, st_tail = oracle.lowpass_log(L[5:], a, state=st_head, library=library)
+    assert np.array_equal(np.concatenate([head, tail]), full) and np.array_equal(st_tail, st_full)
+    perm = rng.permutation(15)
+    flat = L.reshape(12, 15)
+    pout, _ = oracle.lowpass_log(flat[:, perm], a, library=library)
+    assert np.array_equal(pout, full.reshape(12, 15)[:, perm])
+
+
 ALL_PINS = [pin_ramps, pin_uneven_interval, pin_constant_and_first_frame, pin_refractory, pin_brute_force,
-            pin_threshold_maps, pin_band_and_order, pin_fp64_agreement, pin_step_composition]
+            pin_threshold_maps, pin_band_and_order, pin_fp64_agreement, pin_step_composition, pin_lowpass]

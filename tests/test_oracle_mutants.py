@@ -41,6 +41,11 @@ MUTANTS = [
     ("noise_sign", "vp = c_pos + dp;", "vp = c_pos - dp;"),
     ("first_frame_lprev", "                ref[u] = L;\n                lprev[u] = L;\n                tlast[u] = TLAST_NONE;\n            }\n            *has_prev = 1;\n            *tau_prev = tb;\n            continue;\n        }\n        const int64_t ta = *tau_prev;\n        const int64_t D = tb - ta;\n        const float Df",
      "                ref[u] = L;\n                lprev[u] = 0.0f;\n                tlast[u] = TLAST_NONE;\n            }\n            *has_prev = 1;\n            *tau_prev = tb;\n            continue;\n        }\n        const int64_t ta = *tau_prev;\n        const int64_t D = tb - ta;\n        const float Df"),
+    ("lowpass_sign", "const float d = L[(int64_t)k * n + i] - s;", "const float d = s - L[(int64_t)k * n + i];"),
+    ("lowpass_state_ignored", "float s = init ? L[i] : state[i];", "float s = L[i];"),
+    ("lowpass_starts_at_zero", "float s = init ? L[i] : state[i];", "float s = init ? 0.0f : state[i];"),
+    ("lowpass_state_not_saved", "        state[i] = s;\n    }\n    return ORACLE_OK;", "    }\n    return ORACLE_OK;"),
+    ("lowpass_gain_squared", "s = fmaf(alpha, d, s);", "s = fmaf(alpha * alpha, d, s);"),
 ]
 
 

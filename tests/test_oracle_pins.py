@@ -31,6 +31,10 @@ def test_brute_force(L):
     P.pin_brute_force(L)
 
 
+def test_lowpass_filter(L):
+    P.pin_lowpass(L)
+
+
 def test_log_vs_libm(L):
     P.pin_log(L)
 
