@@ -9,7 +9,7 @@ CUDA library never does, and the two share no code.
 
 Functions (each follows the passage and reading named in the C source):
   mylog                 project FP32 log (reading R1)
-  lowpass_log           sensor bandwidth filter on log frames (reading R9)
+  lowpass_log           sensor bandwidth filter on log frames (reading R13)
   splitmix64_at         SplitMix64 output i of a seeded stream (reading R6)
   normal_ih12           Irwin-Hall(12) normal draw (reading R6)
   threshold_maps        per-pixel thresholds max(c_min, C + sigma z) (R6)
@@ -120,7 +120,7 @@ def _p(a, ct):
 # log, random draws, thresholds
 # --------------------------------------------------------------------------
 def lowpass_log(L, alpha, state=None, library=None):
-    """Sensor bandwidth filter (reading R9) over log frames L [T, ...]; returns
+    """Sensor bandwidth filter (reading R13) over log frames L [T, ...]; returns
     (filtered frames, state).  state None starts the filter at frame 0."""
     x = np.ascontiguousarray(L, dtype=np.float32)
     T = x.shape[0]

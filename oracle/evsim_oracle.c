@@ -21,7 +21,9 @@
  * taken here is listed in the "Readings" block below and is the same reading
  * the CUDA path implements.
  *
- * Readings (the paper is silent on all of these):
+ * Readings (the paper is silent on all of these; R9-R12 concern the step
+ * interface, consumers, batches and the learned interpolator, which this
+ * file does not hold):
  *   R1  L = log(clamp(I, 0, 1e6) + eps) in FP32 with the project's own log
  *       (oracle_mylog below); with input_is_log the frame already holds L and
  *       is clamped to [-32, 32].  NaN intensities clamp to 0 (or to -32 in the
@@ -45,7 +47,7 @@
  *       nothing.
  *   R8  Output order: interval-major; inside one interval ascending by the
  *       packed record (t, y, x, p), OFF (p = 0) before ON (p = 1).
- *   R9  Sensor bandwidth (Sec. 2 names "bandwidth limitations" among the
+ *   R13 Sensor bandwidth (Sec. 2 names "bandwidth limitations" among the
  *       non-idealities, with no model): a first-order low-pass filter on
  *       each pixel's log intensity, one update per frame, applied before the
  *       event model: s_k = s_{k-1} + alpha (L_k - s_{k-1}) with
@@ -469,7 +471,7 @@ int oracle_evsim_step_f64(int32_t W, int32_t H, const float *frames, int32_t T,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Sensor bandwidth filter (reading R9).  L, out: [T][n] FP32 (out may be L); */
+/* Sensor bandwidth filter (reading R13).  L, out: [T][n] FP32 (out may be L); */
 /* state: [n], read unless init (then set to frame 0) and written back.       */
 /* ------------------------------------------------------------------------ */
 int oracle_lowpass_log(const float *L, float *out, int32_t T, int64_t n, float alpha, float *state, int32_t init)

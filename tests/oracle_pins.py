@@ -9,7 +9,7 @@ when the oracle disagrees with:
   - the double-precision libm log (reading R1),
   - the published SplitMix64 test vector and Irwin-Hall moments (reading R6),
   - invariants of the model (reference band, ordering, time range),
-  - closed forms of the first-order bandwidth filter (reading R9).
+  - closed forms of the first-order bandwidth filter (reading R13).
 """
 from __future__ import annotations
 
@@ -264,7 +264,7 @@ def pin_uneven_interval(library):
 
 
 def pin_lowpass(library):
-    """Sensor bandwidth filter (reading R9): s_k = s_{k-1} + alpha (L_k - s_{k-1}).
+    """Sensor bandwidth filter (reading R13): s_k = s_{k-1} + alpha (L_k - s_{k-1}).
 
     Closed forms: alpha = 1 follows the frames (within two roundings); a constant input stays
     constant; a unit step reaches 1 - (1 - alpha)^k after k frames, and with

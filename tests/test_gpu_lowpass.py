@@ -1,4 +1,4 @@
-"""Sensor bandwidth filter on the GPU against the oracle (reading R9), bit for bit.
+"""Sensor bandwidth filter on the GPU against the oracle (reading R13), bit for bit.
 
 Shapes: 23 x 41 pixels (not a multiple of 4: the scalar kernel) and 64 x 48
 (the 128-bit kernel), 37 frames (a ragged tail after the 4-frame groups),
