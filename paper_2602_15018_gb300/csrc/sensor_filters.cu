@@ -92,6 +92,8 @@ extern "C" int neurosim_lowpass_log(const float* L_dev, float* out_dev, int32_t 
         return nsim::report_error(NEUROSIM_E_INVALID, "L_dev and out_dev overlap without being equal");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     constexpr int threads = 256;
+    if ((n_pix + threads - 1) / threads > 0x7FFFFFFFll)
+        return nsim::report_error(NEUROSIM_E_INVALID, "n_pix too large for one launch");
     if (n_pix % 4 == 0 && aligned16(L_dev) && aligned16(out_dev) && aligned16(state_dev)) {
         const int64_t n4 = n_pix / 4;
         lowpass4_kernel<<<(unsigned)((n4 + threads - 1) / threads), threads, 0, st>>>(
