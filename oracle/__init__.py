@@ -257,37 +257,37 @@ class OracleSim:
 # --------------------------------------------------------------------------
 # Consumers and scoring
 # --------------------------------------------------------------------------
-def time_surface(width, height, events, tau_us=10_000.0, S=None, last=None):
+def time_surface(width, height, events, tau_us=10_000.0, S=None, last=None, library=None):
     """Time surface of the supplementary RL section; returns (S[2,H,W], last[2,H,W])."""
     ev = np.ascontiguousarray(events, np.uint64)
     if S is None:
         S = np.zeros((2, height, width), np.float64)
         last = np.full((2, height, width), -1, np.int64)
-    rc = lib().oracle_time_surface(width, height, _p(ev, C.c_uint64), ev.size,
+    rc = (library or lib()).oracle_time_surface(width, height, _p(ev, C.c_uint64), ev.size,
                                    _p(S, C.c_double), _p(last, C.c_int64), float(tau_us))
     if rc:
         raise OracleError("time_surface: bad argument")
     return S, last
 
 
-def event_frames(width, height, events, t_start, win_us, n_win):
+def event_frames(width, height, events, t_start, win_us, n_win, library=None):
     """Per-pixel polarity counts over n_win windows: int32[n_win, 2, H, W]."""
     ev = np.ascontiguousarray(events, np.uint64)
     out = np.zeros((n_win, 2, height, width), np.int32)
-    rc = lib().oracle_event_frames(width, height, _p(ev, C.c_uint64), ev.size, int(t_start),
+    rc = (library or lib()).oracle_event_frames(width, height, _p(ev, C.c_uint64), ev.size, int(t_start),
                                    int(win_us), int(n_win), _p(out, C.c_int32))
     if rc:
         raise OracleError("event_frames: bad argument")
     return out
 
 
-def match_f1(width, height, pred, ref, tol_us=1000):
+def match_f1(width, height, pred, ref, tol_us=1000, library=None):
     """Event F1 and count error of `pred` against `ref` (scoring reading)."""
     a = np.ascontiguousarray(pred, np.uint64)
     b = np.ascontiguousarray(ref, np.uint64)
     counts = np.zeros(4, np.int64)
     scores = np.zeros(4, np.float64)
-    rc = lib().oracle_match_f1(width, height, _p(a, C.c_uint64), a.size, _p(b, C.c_uint64),
+    rc = (library or lib()).oracle_match_f1(width, height, _p(a, C.c_uint64), a.size, _p(b, C.c_uint64),
                                b.size, int(tol_us), _p(counts, C.c_int64),
                                _p(scores, C.c_double))
     if rc:

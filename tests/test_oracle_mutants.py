@@ -11,6 +11,7 @@ import tempfile
 
 import pytest
 
+import consumer_pins as CP
 import oracle
 import oracle_pins as P
 
@@ -49,14 +50,30 @@ MUTANTS = [
 ]
 
 
-def _build_mutant(tmp, name, old, new):
-    src = open(os.path.join(SRC, "evsim_oracle.c")).read()
+# mistakes in the consumers and the scoring (oracle/consumers_oracle.c); none of
+# them writes outside its buffers
+CONSUMER_MUTANTS = [
+    ("surface_decay_sign", "decay = exp(-(double)(t - last[c]) / tau_us);",
+     "decay = exp((double)(t - last[c]) / tau_us);"),
+    ("surface_last_not_updated", "        S[c] = S[c] * decay + 1.0;\n        last[c] = t;",
+     "        S[c] = S[c] * decay + 1.0;"),
+    ("frames_window_from_zero", "const int64_t w = (t - t_start) / win_us;", "const int64_t w = t / win_us;"),
+    ("match_tolerance_strict", "if (llabs(ta - tb) <= tol_us)", "if (llabs(ta - tb) < tol_us)"),
+    ("match_wrong_advance", "else if (ta < tb) ++ii;", "else if (ta > tb) ++ii;"),
+    ("cell_without_polarity", "return (y << 49) | (x << 33) | (p << 32) | t;", "return (y << 49) | (x << 33) | t;"),
+    ("count_error_signed", "cnt_err += llabs((i1 - i) - (j1 - j));", "cnt_err += (i1 - i) - (j1 - j);"),
+]
+
+
+def _build_mutant(tmp, name, old, new, target="evsim_oracle.c"):
+    other = "consumers_oracle.c" if target == "evsim_oracle.c" else "evsim_oracle.c"
+    src = open(os.path.join(SRC, target)).read()
     assert old in src, f"mutation site for {name} not found"
     mutated = src.replace(old, new, 1)
     d = os.path.join(tmp, name)
     os.makedirs(d)
-    open(os.path.join(d, "evsim_oracle.c"), "w").write(mutated)
-    shutil.copy(os.path.join(SRC, "consumers_oracle.c"), d)
+    open(os.path.join(d, target), "w").write(mutated)
+    shutil.copy(os.path.join(SRC, other), d)
     so = os.path.join(d, "lib.so")
     subprocess.check_call(["gcc", *oracle.CFLAGS, "-o", so, os.path.join(d, "evsim_oracle.c"),
                            os.path.join(d, "consumers_oracle.c"), "-lm"])
@@ -84,3 +101,14 @@ def tmpdir_mut():
 def test_mutant_is_caught(tmpdir_mut, name, old, new):
     lib = _build_mutant(tmpdir_mut, name, old, new)
     assert _fails_some_pin(lib), f"planted mistake {name} passed every pin"
+
+
+@pytest.mark.parametrize("name,old,new", CONSUMER_MUTANTS, ids=[m[0] for m in CONSUMER_MUTANTS])
+def test_consumer_mutant_is_caught(tmpdir_mut, name, old, new):
+    lib = _build_mutant(tmpdir_mut, name, old, new, target="consumers_oracle.c")
+    for pin in CP.ALL_CONSUMER_PINS:
+        try:
+            pin(lib)
+        except (AssertionError, oracle.OracleError):
+            return
+    pytest.fail(f"planted mistake {name} passed every consumer pin")
