@@ -93,15 +93,22 @@ typedef struct neurosim_evsim_params {
  * log_eps 1e-3, intensity input.  width/height are left 0 and must be set. */
 void neurosim_evsim_default_params(neurosim_evsim_params *p);
 
-/* Creates a simulator.  cuda_stream is a cudaStream_t (NULL = legacy default
- * stream) on the current device; all device work of the handle is enqueued
+/* Creates a simulator: one event camera of width x height pixels.  Paper:
+ * Sec. 2, paragraph "Neurosim simulates event cameras at multi-kilohertz
+ * rates" (each pixel keeps the level of its last triggered event, compared
+ * against contrast thresholds; noise is a user-disableable non-ideality, here
+ * the per-pixel threshold maps drawn at create).  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream) on the current device; all device work of the handle is enqueued
  * there.  Allocates the per-pixel state, threshold maps and event buffers on
  * the current device.  Returns NEUROSIM_E_INVALID for bad params. */
 int neurosim_evsim_create(const neurosim_evsim_params *p, void *cuda_stream,
                           neurosim_evsim **out);
 
 /* Enqueues one step over n_frames DEVICE frames, FP32 [n_frames][height][width]
- * row-major, frame f at time t0_us + f * dt_us (us).  Asynchronous: returns
+ * row-major, frame f at time t0_us + f * dt_us (us).  Paper: Sec. 2, same
+ * paragraph (every rendered intensity frame updates each pixel's state against
+ * its last event level and yields a variable number of events, gathered with
+ * few global atomics); Sec. 1 for the event tuple (t in us, pixel, polarity).  Asynchronous: returns
  * after enqueueing, without a host synchronisation, and may be captured into a
  * CUDA graph.  The first frame ever initialises the sensor; every later frame
  * closes one interval.  Requires t0_us > the previous frame time (else
@@ -130,7 +137,10 @@ int neurosim_evsim_step_host(neurosim_evsim *h, const float *frames_host, int32_
 int neurosim_evsim_pending(neurosim_evsim *h, uint64_t *n_events, int64_t *n_intervals);
 
 /* Copies the pending events, in output order, into `out` (DEVICE memory if
- * out_is_device, else HOST memory) and clears them.  out_capacity is in
+ * out_is_device, else HOST memory) and clears them.  Paper: Sec. 1 defines
+ * the event as (t, u, p) with integer microsecond timestamps; Sec. 2 (same
+ * paragraph) makes the number of events per frame variable, so the caller
+ * learns the count here.  Records are packed as described at the top.  out_capacity is in
  * records; if it is smaller than the pending count the call returns
  * NEUROSIM_E_OVERFLOW, sets *n_out to the count needed and keeps the events.
  * If seg_offsets is not NULL it receives n_intervals + 1 HOST int64 offsets
@@ -160,7 +170,9 @@ int neurosim_evsim_set_state(neurosim_evsim *h, const float *ref, const float *l
 /* Copies the per-pixel ON/OFF thresholds (HOST, height*width each). */
 int neurosim_evsim_get_thresholds(neurosim_evsim *h, float *c_pos, float *c_neg);
 
-/* Frees all device and host resources of the handle (synchronises first). */
+/* Frees all device and host resources of the handle (synchronises first):
+ * the per-pixel state of Sec. 2's event model, the threshold maps and the
+ * event buffers.  NULL is ignored. */
 void neurosim_evsim_destroy(neurosim_evsim *h);
 
 /* Counters of a handle (all since create; replays after overflow included). */
@@ -442,6 +454,17 @@ int32_t neurosim_abi_version(void);
 int neurosim_debug_umma_gemm(int32_t mode, int32_t M, int32_t N, int32_t K, const void *A,
                              const void *B, float *C, void *cuda_stream);
 
+/* Verification of the bounded device waits (no counterpart in the paper):
+ * every wait of the library's kernels on an mbarrier gives up after a time
+ * limit, records NEUROSIM_E_TIMEOUT and lets the kernel return, so that a
+ * lost arrival cannot hang the GPU.  This launches one warp that waits, with
+ * that same bounded wait and a limit of limit_ns (1 us .. 100 ms), on an
+ * mbarrier that it arrives on itself when arrive != 0 and that nothing
+ * arrives on otherwise.  Returns NEUROSIM_OK when the wait completed and
+ * NEUROSIM_E_TIMEOUT when it gave up (the GPU context stays usable).
+ * Synchronises cuda_stream.  NEUROSIM_E_INVALID for a limit out of range. */
+int neurosim_debug_expiring_wait(int32_t arrive, uint64_t limit_ns, void *cuda_stream);
+
 /* The event model's log intensity of n DEVICE floats (Sec. 2 contrast model,
  * reading: L = log(clamp(I, 0, 1e6) + log_eps) with the library's FP32 log):
  * L_dev[i] = the L the emission kernel computes for I_dev[i].  Feeding these
@@ -467,15 +490,25 @@ int neurosim_log_intensity(const float *I_dev, float *L_dev, int64_t n, float lo
 int neurosim_lowpass_log(const float *L_dev, float *out_dev, int32_t n_frames, int64_t n_pix, float alpha,
                          float *state_dev, int32_t init, void *cuda_stream);
 
+/* Gain of the bandwidth filter above for a cutoff frequency (same reading of
+ * Sec. 2's "bandwidth limitations"): a first-order filter with cutoff f_c
+ * (time constant 1 / (2 pi f_c)) sampled every dt keeps exp(-2 pi f_c dt) of
+ * its level per frame, so *alpha_out = 1 - exp(-2 pi f_c dt), computed on the
+ * host in double and rounded once to FP32.  cutoff_hz > 0 and finite,
+ * dt_us >= 1 (microseconds).  NEUROSIM_E_INVALID for other arguments, a NULL
+ * alpha_out, or a gain that rounds to 0.  Host only; no device work. */
+int neurosim_lowpass_alpha(double cutoff_hz, int32_t dt_us, float *alpha_out);
+
 /* Evaluates the library's FP32 log (the one the event model uses) on n DEVICE
  * floats x_dev into y_dev on cuda_stream; for verification of the log. */
 int neurosim_debug_log(const float *x_dev, float *y_dev, int64_t n, void *cuda_stream);
 
 /* One step of the event model that allocates nothing.  The paper has no
  * counterpart: this is a library convenience for callers that cannot call
- * cudaMalloc (code inside a CUDA graph being captured, real-time loops that
- * must never enter the allocator, hosts that only borrow device buffers).
- * The caller owns every buffer; the library keeps its intermediates (event
+ * cudaMalloc: real-time control loops that must never enter the device
+ * allocator (an allocation can wait on a device-wide synchronisation), and
+ * host programs that only borrow device buffers from another runtime and
+ * have no allocator of their own.  The caller owns every buffer; the library keeps its intermediates (event
  * keys, chunk table, per-interval counts, control block) in one fixed 32 MiB
  * device array compiled into the library (held by every GPU that loads it,
  * until exit).

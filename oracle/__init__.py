@@ -9,11 +9,13 @@ CUDA library never does, and the two share no code.
 
 Functions (each follows the passage and reading named in the C source):
   mylog                 project FP32 log (reading R1)
+  lowpass_alpha         per-frame gain of the bandwidth filter (reading R13)
   lowpass_log           sensor bandwidth filter on log frames (reading R13)
   splitmix64_at         SplitMix64 output i of a seeded stream (reading R6)
   normal_ih12           Irwin-Hall(12) normal draw (reading R6)
   threshold_maps        per-pixel thresholds max(c_min, C + sigma z) (R6)
   OracleSim             stateful FP32-mirrored (or FP64) event simulator
+  banded_step           OracleSim over row bands on several host threads
   time_surface          Eq. for the time surface in the supplementary RL
                         section (S <- S exp(-dt/tau) + 1)
   event_frames          per-pixel polarity histograms over fixed windows
@@ -65,6 +67,8 @@ def _configure(L):
     L.oracle_mylog.argtypes = [C.c_float]
     L.oracle_lowpass_log.restype = C.c_int
     L.oracle_lowpass_log.argtypes = [f32p, f32p, C.c_int32, C.c_int64, C.c_float, f32p, C.c_int32]
+    L.oracle_lowpass_alpha.restype = C.c_float
+    L.oracle_lowpass_alpha.argtypes = [C.c_double, C.c_int32]
     L.oracle_mylog_batch.restype = None
     L.oracle_mylog_batch.argtypes = [f32p, f32p, C.c_int64]
     L.oracle_mylog_max_ulp.restype = C.c_double
@@ -133,6 +137,15 @@ def lowpass_log(L, alpha, state=None, library=None):
     if rc != 0:
         raise OracleError(_ERR.get(rc, f"error {rc}"))
     return out, st
+
+
+def lowpass_alpha(cutoff_hz, dt_us, library=None) -> np.float32:
+    """Per-frame gain of the bandwidth filter (reading R13), 1 - exp(-2 pi f_c dt),
+    rounded once to FP32; raises for f_c <= 0, dt_us < 1 or a gain that rounds to 0."""
+    a = np.float32((library or lib()).oracle_lowpass_alpha(float(cutoff_hz), int(dt_us)))
+    if not a > 0:
+        raise OracleError("invalid cutoff or frame spacing")
+    return a
 
 
 def mylog(x, library=None) -> np.ndarray:
@@ -252,6 +265,45 @@ class OracleSim:
     @property
     def tau(self) -> int:
         return int(self.tau_prev.value)
+
+
+def banded_step(frames, width, height, t0: int, dt: int, c_pos_map, c_neg_map, refractory_us=0,
+                log_eps=1e-3, input_is_log=False, threads=None, library=None):
+    """One step of fresh sensors' oracle (FP32), run band-parallel: the frames'
+    rows are split into bands, each band is simulated by its own OracleSim on
+    its own host thread (the ctypes call releases the interpreter lock), and
+    the bands' records are merged into the output order of reading R8.
+    Pixels are independent in the model, so the result equals one OracleSim
+    over the whole frame (checked in the oracle's tests).  Returns (events,
+    seg_offsets, threads used, final state: dict of ref, lprev (FP32) and
+    tlast (int64, -1 = none) over all pixels)."""
+    from concurrent.futures import ThreadPoolExecutor
+    fr = np.asarray(frames, dtype=np.float32).reshape(-1, height, width)
+    T = fr.shape[0]
+    cp = np.ascontiguousarray(c_pos_map, np.float32).reshape(height, width)
+    cn = np.ascontiguousarray(c_neg_map, np.float32).reshape(height, width)
+    n_thr = max(1, min(int(threads or os.cpu_count() or 1), height))
+    edges = np.linspace(0, height, n_thr + 1).astype(int)
+    L = library or lib()
+
+    def band(b):
+        y0, y1 = int(edges[b]), int(edges[b + 1])
+        sim = OracleSim(width, y1 - y0, c_pos_map=cp[y0:y1], c_neg_map=cn[y0:y1], refractory_us=refractory_us,
+                        log_eps=log_eps, input_is_log=input_is_log, library=L)
+        ev, seg = sim.step(np.ascontiguousarray(fr[:, y0:y1, :]), t0, dt)
+        return ev + (np.uint64(y0) << np.uint64(17)), seg, sim
+
+    with ThreadPoolExecutor(max_workers=n_thr) as ex:
+        parts = list(ex.map(band, range(n_thr)))
+    state = {k: np.concatenate([getattr(sim, k) for _, _, sim in parts]) for k in ("ref", "lprev", "tlast")}
+    parts = [(ev, seg) for ev, seg, _ in parts]
+    n_seg = len(parts[0][1]) - 1
+    rec = np.concatenate([ev for ev, _ in parts]) if parts else np.zeros(0, np.uint64)
+    j = np.concatenate([np.repeat(np.arange(n_seg), np.diff(seg)) for _, seg in parts])
+    order = np.lexsort((rec, j))
+    seg = np.zeros(n_seg + 1, np.int64)
+    seg[1:] = np.cumsum(np.bincount(j, minlength=n_seg))
+    return rec[order], seg, n_thr, state
 
 
 # --------------------------------------------------------------------------

@@ -51,9 +51,10 @@
  *       non-idealities, with no model): a first-order low-pass filter on
  *       each pixel's log intensity, one update per frame, applied before the
  *       event model: s_k = s_{k-1} + alpha (L_k - s_{k-1}) with
- *       alpha = 1 - exp(-2 pi f_c dt) for a cutoff f_c; the filter starts at
- *       the first frame's value.  FP32: d = L - s rounded, then s = fma(alpha,
- *       d, s) with one rounding (oracle_lowpass_log below).
+ *       alpha = 1 - exp(-2 pi f_c dt) for a cutoff f_c (in double, rounded
+ *       once to FP32: oracle_lowpass_alpha); the filter starts at the first
+ *       frame's value.  FP32: d = L - s rounded, then s = fma(alpha, d, s)
+ *       with one rounding (oracle_lowpass_log below).
  *
  * Packed record (64 bits): [63:32] t (us) | [31:17] y | [16:1] x | [0] p.
  *
@@ -487,6 +488,20 @@ int oracle_lowpass_log(const float *L, float *out, int32_t T, int64_t n, float a
         state[i] = s;
     }
     return ORACLE_OK;
+}
+
+/* Per-frame gain of the bandwidth filter (reading R13): the first-order     */
+/* filter with cutoff f_c, time constant 1 / (2 pi f_c), sampled every dt,   */
+/* keeps exp(-2 pi f_c dt) of the old level: alpha = 1 - exp(-2 pi f_c dt),   */
+/* evaluated in double and rounded once to FP32.  dt_us in microseconds.     */
+/* Returns 0 for arguments outside f_c > 0, dt_us >= 1 or a gain that rounds */
+/* to zero.                                                                  */
+float oracle_lowpass_alpha(double cutoff_hz, int32_t dt_us)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    if (!(cutoff_hz > 0.0) || !isfinite(cutoff_hz) || dt_us < 1) return 0.0f;
+    const double keep = exp(-two_pi * cutoff_hz * ((double)dt_us * 1e-6));
+    return (float)(1.0 - keep);
 }
 
 void oracle_free(void *p) { free(p); }

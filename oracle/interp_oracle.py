@@ -36,8 +36,10 @@ v = b2 v + (1 - b2) g^2, w -= lr (m / (1 - b1^t) / (sqrt(v / (1 - b2^t)) + eps)
 
 With quantize=True the oracle rounds what the GPU path stores in BF16 (the
 weights and every activation it writes) to BF16 (round to nearest even), and
-keeps all arithmetic in FP64; the CUDA path then differs only by its FP32
-accumulation order.
+keeps all arithmetic in FP64; with quantize_grads=True (backward) it also
+rounds the activation gradients the GPU path stores in BF16.  The CUDA path
+then differs only by its FP32 accumulation order, and by the rare BF16
+rounding that this order flips.
 
 Parity unpinned against the paper (it has no interpolator); the oracle is
 pinned to mathematics instead: finite differences of the loss, the direct
@@ -192,44 +194,57 @@ def convT2_backward(x, w, gout):
     return gx, gw
 
 
-def backward(p, cache, gout):
+def backward(p, cache, gout, quantize_grads=False):
     """gout: d loss / d out [3, N, H, W].  Returns gradients for every
-    parameter (same keys and shapes as p)."""
+    parameter (same keys and shapes as p).
+
+    With quantize_grads=True the gradients of the activations are rounded to
+    BF16 where the GPU path stores them in BF16: the loss gradient; the
+    gradient of d2; the gradient of the concatenation [u2, e1] after conv8
+    (the e1 half masked by e1 > 0); that of d1; that of [u1, e2] after conv6
+    (the e2 half masked); those of e4 and e3; and the e2 and e1 halves again
+    after the stride-2 layers add their data gradients to them.  Every weight
+    and bias gradient is then computed from those rounded values.  All
+    arithmetic stays FP64."""
+    q = bf16 if quantize_grads else (lambda v: v)
     w, c = cache["w"], cache
     g = {}
-    gr = np.moveaxis(gout, 0, 3)                                       # [N, H, W, 3]
+    gr = q(np.moveaxis(gout, 0, 3))                                    # [N, H, W, 3]
     g["W9"] = c["d2"].reshape(-1, 32).T @ gr.reshape(-1, 3)
     g["b9"] = gr.reshape(-1, 3).sum(0)
-    gd2 = (gr @ w["W9"].T) * (c["d2"] > 0)
+    gd2 = q((gr @ w["W9"].T) * (c["d2"] > 0))
     gcat1, g["W8"] = conv3_backward(c["cat1"], w["W8"], gd2)
     g["b8"] = gd2.reshape(-1, 32).sum(0)
-    gu2, ge1 = gcat1[..., :32], gcat1[..., 32:]
+    gu2 = q(gcat1[..., :32])
+    ge1 = q(gcat1[..., 32:] * (c["e1"] > 0))
     g["b7"] = gu2.reshape(-1, 32).sum(0)
     gd1, g["W7"] = convT2_backward(c["d1"], w["W7"], gu2)
-    gd1 = gd1 * (c["d1"] > 0)
+    gd1 = q(gd1 * (c["d1"] > 0))
     gcat2, g["W6"] = conv3_backward(c["cat2"], w["W6"], gd1)
     g["b6"] = gd1.reshape(-1, 64).sum(0)
-    gu1, ge2 = gcat2[..., :64], gcat2[..., 64:]
+    gu1 = q(gcat2[..., :64])
+    ge2 = q(gcat2[..., 64:] * (c["e2"] > 0))
     g["b5"] = gu1.reshape(-1, 64).sum(0)
     ge4, g["W5"] = convT2_backward(c["e4"], w["W5"], gu1)
-    ge4 = ge4 * (c["e4"] > 0)
+    ge4 = q(ge4 * (c["e4"] > 0))
     ge3, g["W4"] = conv3_backward(c["e3"], w["W4"], ge4)
     g["b4"] = ge4.reshape(-1, 128).sum(0)
-    ge3 = ge3 * (c["e3"] > 0)
+    ge3 = q(ge3 * (c["e3"] > 0))
     ge2b, g["W3"] = conv3_backward(c["e2"], w["W3"], ge3, 2)
     g["b3"] = ge3.reshape(-1, 128).sum(0)
-    ge2 = (ge2 + ge2b) * (c["e2"] > 0)
+    ge2 = q(ge2 + ge2b * (c["e2"] > 0))
     ge1b, g["W2"] = conv3_backward(c["e1"], w["W2"], ge2, 2)
     g["b2"] = ge2.reshape(-1, 64).sum(0)
-    ge1 = (ge1 + ge1b) * (c["e1"] > 0)
+    ge1 = q(ge1 + ge1b * (c["e1"] > 0))
     _, g["W1"] = conv3_backward(c["x"], w["W1"], ge1)
     g["b1"] = ge1.reshape(-1, 32).sum(0)
     return g
 
 
-def loss_and_grads(p, L0, L4, targets, quantize=False):
+def loss_and_grads(p, L0, L4, targets, quantize=False, quantize_grads=False):
     out, cache = forward(p, L0, L4, quantize)
-    return charbonnier(out, targets), backward(p, cache, charbonnier_grad(out, targets)), out
+    g = backward(p, cache, charbonnier_grad(out, targets), quantize_grads)
+    return charbonnier(out, targets), g, out
 
 
 # ---------------------------------------------------------------------------

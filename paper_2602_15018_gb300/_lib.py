@@ -35,7 +35,7 @@ EXPORTS = [
     "neurosim_interp_set_params", "neurosim_interp_save", "neurosim_interp_load",
     "neurosim_interp_launches", "neurosim_interp_destroy",
     "neurosim_event_f1", "neurosim_log_intensity", "neurosim_time_surface", "neurosim_event_frames",
-    "neurosim_lowpass_log",
+    "neurosim_lowpass_log", "neurosim_lowpass_alpha", "neurosim_debug_expiring_wait",
 ]
 
 
@@ -189,6 +189,10 @@ def lib():
             L.neurosim_event_frames.argtypes = [vp, i32, i32, vp, i64, i64, i64, i32, vp]
             L.neurosim_lowpass_log.restype = C.c_int
             L.neurosim_lowpass_log.argtypes = [vp, vp, i32, i64, C.c_float, vp, i32, vp]
+            L.neurosim_debug_expiring_wait.restype = C.c_int
+            L.neurosim_debug_expiring_wait.argtypes = [i32, u64, vp]
+            L.neurosim_lowpass_alpha.restype = C.c_int
+            L.neurosim_lowpass_alpha.argtypes = [C.c_double, i32, C.POINTER(C.c_float)]
             L.neurosim_log_intensity.restype = C.c_int
             L.neurosim_log_intensity.argtypes = [vp, vp, i64, C.c_float, vp]
             L.neurosim_event_f1.restype = C.c_int

@@ -1,9 +1,10 @@
 // One event-generation step that allocates nothing (declared in
 // include/neurosim_evsim.h as neurosim_evsim_step_noalloc).
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA graph that
-// is being captured, real-time loops that must never enter the allocator,
-// and host programs that only borrow a device buffer from another runtime.
+// Some callers cannot call cudaMalloc: real-time control loops that must
+// never enter the device allocator (it can block on a device-wide
+// synchronisation), and host programs that only borrow device buffers from
+// another runtime or framework and have no allocator of their own to call.
 // For them this entry point runs one step of the event model from buffers
 // the caller owns (frames, thresholds, per-pixel state in and out, event
 // records and interval offsets out) and keeps every intermediate — the paged
@@ -13,9 +14,10 @@
 // The array is shared by every call on a device and keeps the last call's
 // contents; the control block is cleared at the start of each call.  Two
 // calls whose work overlaps on the GPU (different streams, no ordering
-// between them) race on the array.  The first call on a device looks up the
-// array's device address and configures the kernels; it should happen before
-// any stream capture.
+// between them) race on the array.  The call synchronises the caller's
+// stream before it returns (it reads the event count back to the host).  The
+// first call on a device looks up the array's device address and configures
+// the kernels; it should happen before any stream capture.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>

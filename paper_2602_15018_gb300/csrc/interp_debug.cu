@@ -74,7 +74,51 @@ int run_tma(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B,
     return NEUROSIM_OK;
 }
 
+// One CTA of 32 threads: thread 0 sets up an mbarrier expecting one arrival
+// and, if `arrive`, arrives on it; then the whole warp waits for the phase
+// with the same bounded wait as the tensor-core kernels (umma::mbar_wait).
+// Nothing else ever arrives, so without `arrive` every wait gives up after
+// limit_ns and the kernel records kErrTimeout and returns.
+__global__ void expiring_wait_kernel(int arrive, uint64_t limit_ns, unsigned int* err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        umma::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (threadIdx.x == 0 && arrive) {
+        uint64_t state;
+        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(umma::smem_u32(&bar)) : "memory");
+        (void)state;
+    }
+    __syncwarp();
+    const bool ok = umma::mbar_wait(&bar, 0, limit_ns);
+    if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) atomicOr(err, nsim::kErrTimeout);
+}
+
 }  // namespace
+
+extern "C" int neurosim_debug_expiring_wait(int32_t arrive, uint64_t limit_ns, void* cuda_stream)
+{
+    if (limit_ns < 1000ull || limit_ns > 100000000ull)
+        return nsim::report_error(NEUROSIM_E_INVALID, "limit_ns must be in [1 us, 100 ms]");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    unsigned int* err = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&err), sizeof(unsigned int), st) != cudaSuccess ||
+        cudaMemsetAsync(err, 0, sizeof(unsigned int), st) != cudaSuccess)
+        return nsim::report_error(NEUROSIM_E_CUDA, "cannot allocate the error word");
+    expiring_wait_kernel<<<1, 32, 0, st>>>(arrive != 0, limit_ns, err);
+    int rc = cudaGetLastError() == cudaSuccess ? NEUROSIM_OK : NEUROSIM_E_CUDA;
+    unsigned int h = 0;
+    if (cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        rc = rc ? rc : NEUROSIM_E_CUDA;
+    cudaFreeAsync(err, st);
+    if (rc) return nsim::report_error(rc, "wait kernel launch failed");
+    if (h & nsim::kErrTimeout) return nsim::report_error(NEUROSIM_E_TIMEOUT, "the bounded mbarrier wait gave up");
+    return NEUROSIM_OK;
+}
 
 extern "C" int neurosim_debug_umma_gemm(int32_t mode, int32_t M, int32_t N, int32_t K, const void* A,
                                         const void* B, float* C, void* cuda_stream)

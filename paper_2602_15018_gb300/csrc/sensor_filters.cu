@@ -78,6 +78,23 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 }  // namespace
 
+// Gain of the filter for a cutoff: a first-order low-pass with cutoff f_c has
+// the time constant 1 / (2 pi f_c); sampled every dt it keeps exp(-2 pi f_c dt)
+// of its old level per frame, so alpha = 1 - exp(-2 pi f_c dt), evaluated on
+// the host in double and rounded once to FP32.
+extern "C" int neurosim_lowpass_alpha(double cutoff_hz, int32_t dt_us, float* alpha_out)
+{
+    if (!alpha_out) return nsim::report_error(NEUROSIM_E_INVALID, "alpha_out is NULL");
+    if (!(cutoff_hz > 0.0) || !std::isfinite(cutoff_hz))
+        return nsim::report_error(NEUROSIM_E_INVALID, "cutoff_hz must be positive and finite");
+    if (dt_us < 1) return nsim::report_error(NEUROSIM_E_INVALID, "dt_us must be >= 1");
+    const double omega_dt = 2.0 * 3.14159265358979323846 * cutoff_hz * ((double)dt_us * 1e-6);
+    const float a = (float)(1.0 - std::exp(-omega_dt));
+    if (!(a > 0.0f)) return nsim::report_error(NEUROSIM_E_INVALID, "cutoff_hz * dt too small: the gain rounds to 0");
+    *alpha_out = a;
+    return NEUROSIM_OK;
+}
+
 extern "C" int neurosim_lowpass_log(const float* L_dev, float* out_dev, int32_t n_frames, int64_t n_pix, float alpha,
                                     float* state_dev, int32_t init, void* cuda_stream)
 {

@@ -8,7 +8,6 @@ supplies device memory and the CUDA stream.
 from __future__ import annotations
 
 import ctypes as C
-import math
 
 import numpy as np
 import torch
@@ -236,10 +235,11 @@ def log_intensity(frames: torch.Tensor, log_eps: float = 1e-3, out: torch.Tensor
 
 
 def lowpass_alpha(cutoff_hz: float, dt_us: int) -> float:
-    """Per-frame gain of the first-order bandwidth filter, 1 - exp(-2 pi f_c dt)."""
-    if not (cutoff_hz > 0 and dt_us > 0):
-        raise ValueError("cutoff_hz and dt_us must be positive")
-    return float(np.float32(1.0 - math.exp(-2.0 * math.pi * cutoff_hz * dt_us * 1e-6)))
+    """Per-frame gain of the first-order bandwidth filter for a cutoff frequency
+    (library call neurosim_lowpass_alpha: 1 - exp(-2 pi f_c dt), FP32)."""
+    a = C.c_float(0.0)
+    check(lib().neurosim_lowpass_alpha(float(cutoff_hz), int(dt_us), C.byref(a)))
+    return float(a.value)
 
 
 def lowpass_log(L: torch.Tensor, alpha: float, state: torch.Tensor | None = None,

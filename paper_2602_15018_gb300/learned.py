@@ -4,45 +4,30 @@ interpolator's intermediate frames, and the exact event model on the result.
 The paper renders every frame for its event camera (Sec. 2, >2700 FPS); here
 keyframes arrive every 4 dt, the U-Net (interp.py) predicts the three log
 frames between them, and the unchanged FP32 event emission runs on the full
-1000 FPS log sequence.  Training clips are 1000 FPS sequences of the seeded
-procedural scenes the plain simulator is benchmarked on.
+1000 FPS log sequence.  The caller supplies the data: training clips of 1000
+FPS log frames from a clip source, and rendered frames to score on.  This
+module renders nothing itself.
 """
 from __future__ import annotations
 
 import math
+from typing import Callable
 
-import numpy as np
 import torch
-
-import scenes
 
 from .evsim import EventSim, event_f1, log_intensity
 from .interp import Interpolator
 
 
-def training_clips(batch: int, size: int, seed: int, speed=(150.0, 300.0), device="cuda") -> torch.Tensor:
-    """[batch, 5, size, size] log frames (1000 FPS): crops of one seeded texture
-    scene of 4 size x 4 size at a random time in a 2 s clip."""
-    rng = np.random.default_rng(seed)
-    big = 4 * size
-    sc = scenes.TextureScene(big, big, seed=int(rng.integers(1 << 30)), speed=speed)
-    t0 = int(rng.integers(0, 2_000_000)) // 1000 * 1000
-    fr = scenes.render_frames(sc, 5, t0_us=t0, dt_us=1000, device=device)
-    lg = log_intensity(fr.contiguous())
-    out = torch.empty((batch, 5, size, size), dtype=torch.float32, device=device)
-    for b in range(batch):
-        y, x = rng.integers(0, big - size + 1, 2)
-        out[b] = lg[:, y:y + size, x:x + size]
-    return out
-
-
-def train(net: Interpolator, steps: int, batch: int = 16, size: int = 256, lr: float = 1e-3,
-          weight_decay: float = 1e-4, seed: int = 10000, speed=(150.0, 300.0), report: int = 0):
-    """AdamW with a cosine learning-rate schedule over `steps` steps; returns
+def train(net: Interpolator, steps: int, clip_source: Callable[[int], torch.Tensor], lr: float = 1e-3,
+          weight_decay: float = 1e-4, report: int = 0):
+    """AdamW with a cosine learning-rate schedule over `steps` steps.
+    clip_source(it) returns step it's clips: DEVICE [batch, 5, H, W] log frames
+    at 1000 FPS (frames 0 and 4 are the keyframes, 1..3 the targets).  Returns
     the losses of the steps it reports (every `report` steps, 0 = none)."""
     losses = []
     for it in range(steps):
-        clips = training_clips(batch, size, seed + it, speed)
+        clips = clip_source(it)
         lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * it / max(1, steps)))
         want = bool(report) and (it % report == 0 or it == steps - 1)
         loss = net.train_step(clips, lr_t, weight_decay, want_loss=want)
@@ -79,18 +64,17 @@ def events_of(frames: torch.Tensor, input_is_log: bool, t0_us: int = 0, dt_us: i
     return ev
 
 
-def evaluate(net: Interpolator, width: int, height: int, n_keys: int, scene_seed: int, tol_us: int = 1000,
-             speed=(150.0, 300.0), **sim) -> dict:
+def evaluate(net: Interpolator, frames: torch.Tensor, tol_us: int = 1000, **sim) -> dict:
     """F1 and count error of the events of the learned path (keyframes every
-    4 ms + predicted frames) and of plain linear interpolation against the
-    plain 1000 FPS path, on one seeded HD-like texture clip."""
-    sc = scenes.TextureScene(width, height, seed=scene_seed, speed=speed)
-    T = 4 * (n_keys - 1) + 1
-    frames = scenes.render_frames(sc, T, device="cuda", chunk=32)
+    4 frames + predicted frames) and of plain linear interpolation against the
+    plain path on all of `frames` (DEVICE intensity frames [4 (K - 1) + 1, H, W]
+    at 1000 FPS)."""
+    T, H, W = frames.shape
+    if (T - 1) % 4 != 0 or T < 5:
+        raise ValueError("frames must hold 4 (K - 1) + 1 frames, K >= 2")
     ref = events_of(frames, False, **sim)
     keys = log_intensity(frames[0::4].contiguous())
-    del frames
-    lin_net = Interpolator(8, height, width, seed=0)          # untrained: r = 0, linear interpolation
+    lin_net = Interpolator(8, H, W, seed=0)          # untrained: r = 0, linear interpolation
     res = {"n_ref": int(len(ref)), "frames": T}
     for name, model in (("learned", net), ("linear", lin_net)):
         seq = interpolate_sequence(model, keys)

@@ -106,5 +106,31 @@ def pin_adamw_first_step(io):
     assert st["t"] == 1
 
 
+def pin_quantized_gradients(io):
+    """Rounding the activation gradients to BF16 (quantize_grads) changes each
+    parameter gradient by no more than a chain of BF16 roundings allows: a few
+    2^-8 relative in norm, far below what a wrong tap or channel would move;
+    and it does change them (the rounding is applied)."""
+    rng = np.random.default_rng(6)
+    p = _rand_params(io, 6)
+    N, H, W = 2, 8, 12
+    L0 = rng.uniform(-4.0, 0.0, (N, H, W))
+    L4 = L0 + rng.normal(0.0, 0.3, (N, H, W))
+    T = rng.uniform(-4.0, 0.0, (3, N, H, W))
+    _, g, _ = io.loss_and_grads(p, L0, L4, T, quantize=True)
+    _, gq, _ = io.loss_and_grads(p, L0, L4, T, quantize=True, quantize_grads=True)
+    moved = 0
+    for k in list(io.SHAPES) + list(io.BIAS):
+        a, b = gq[k].reshape(-1), g[k].reshape(-1)
+        nb = np.linalg.norm(b)
+        if nb == 0:
+            assert np.linalg.norm(a) == 0, k
+            continue
+        rel = np.linalg.norm(a - b) / nb
+        assert rel < 8 * 2.0 ** -8, (k, rel)
+        moved += rel > 0
+    assert moved >= 10
+
+
 ALL_INTERP_PINS = [pin_bf16_rounding, pin_conv3, pin_convT2, pin_untrained_is_linear, pin_gradients,
-                   pin_adamw_first_step]
+                   pin_adamw_first_step, pin_quantized_gradients]

@@ -301,6 +301,38 @@ def pin_lowpass(library):
     flat = L.reshape(12, 15)
     pout, _ = oracle.lowpass_log(flat[:, perm], a, library=library)
     assert np.array_equal(pout, full.reshape(12, 15)[:, perm])
+    pin_lowpass_alpha(library)
+
+
+def pin_lowpass_alpha(library):
+    """Gain of the bandwidth filter from its cutoff (reading R13).
+
+    A first-order filter with cutoff f_c has time constant 1 / (2 pi f_c): a unit step
+    sampled every dt must reach 1 - 1/e after that many frames.  With f_c dt = 1 / (2 pi n)
+    the filter, run with the oracle's own gain, is checked there for several n.  Small
+    f_c dt gives alpha ~ 2 pi f_c dt (first order of the series); a very high cutoff gives a
+    gain that rounds to 1 (the filter follows the frames); doubling dt gives the square of
+    the kept fraction."""
+    for n in (5, 20, 64):
+        fc = 1.0 / (2.0 * math.pi * n * 1e-3)          # dt = 1000 us
+        alpha = oracle.lowpass_alpha(fc, 1000, library=library)
+        step = np.ones((n + 1, 1), np.float32)
+        step[0] = 0.0
+        out, _ = oracle.lowpass_log(step, alpha, library=library)
+        assert abs(out[n, 0] - (1.0 - math.exp(-1.0))) < 4e-6, (n, out[n, 0])
+    x = 2.0 * math.pi * 1.0 * 10e-6                    # f_c = 1 Hz, dt = 10 us
+    a = oracle.lowpass_alpha(1.0, 10, library=library)
+    assert abs(a - x) <= x * x, (a, x)
+    assert oracle.lowpass_alpha(1e9, 1000, library=library) == np.float32(1.0)
+    a1 = np.float64(oracle.lowpass_alpha(37.0, 1000, library=library))
+    a2 = np.float64(oracle.lowpass_alpha(37.0, 2000, library=library))
+    assert abs((1.0 - a2) - (1.0 - a1) ** 2) < 1e-6
+    for bad in ((0.0, 1000), (-5.0, 1000), (10.0, 0), (float("inf"), 1000)):
+        try:
+            oracle.lowpass_alpha(*bad, library=library)
+        except oracle.OracleError:
+            continue
+        raise AssertionError(f"lowpass_alpha{bad} accepted")
 
 
 ALL_PINS = [pin_ramps, pin_uneven_interval, pin_constant_and_first_frame, pin_refractory, pin_brute_force,

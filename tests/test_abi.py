@@ -126,3 +126,21 @@ def test_batch_defaults_and_no_gpu(built):
     rc = L.neurosim_evsim_autotune(C.byref(p), C.c_void_p(16), 1, 1000, 3, None, C.byref(ppt),
                                    C.byref(pf), None)
     assert rc == 1 and b"n_frames" in L.neurosim_last_error()
+
+
+def test_lowpass_gain_matches_the_oracle(built):
+    """The bandwidth filter's gain from a cutoff is computed by the library on
+    the host (no device needed) and must equal the oracle's own, bit for bit;
+    bad arguments are rejected."""
+    import numpy as np
+
+    import oracle
+    from paper_2602_15018_gb300 import _lib
+    L = _lib.lib()
+    a = C.c_float(0.0)
+    for fc, dt in ((40.0, 1000), (400.0, 1000), (1e9, 1000), (1.0, 10), (37.0, 2000), (150.0, 250)):
+        assert L.neurosim_lowpass_alpha(fc, dt, C.byref(a)) == 0
+        assert np.float32(a.value) == oracle.lowpass_alpha(fc, dt), (fc, dt)
+    for fc, dt in ((0.0, 1000), (-1.0, 1000), (10.0, 0), (float("inf"), 1000), (float("nan"), 1000)):
+        assert L.neurosim_lowpass_alpha(fc, dt, C.byref(a)) == 1, (fc, dt)
+    assert L.neurosim_lowpass_alpha(10.0, 1000, None) == 1

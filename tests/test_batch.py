@@ -265,3 +265,74 @@ def test_batch_strided_frames_match_oracle():
             assert np.array_equal(per[i][0], rev), (k, i)
             assert np.array_equal(per[i][1], rseg), (k, i)
     batch.close()
+
+
+def test_batch_at_benchmark_shapes_graph_replay():
+    """24 sensors cycling 346x260 / 640x480 / 1280x720 with the batched
+    benchmark's parameters (C+- from U[0.15, 0.35], sigma 0.03, refractory
+    100 us, texture scenes), 16 frames per step, 3 steps from one captured
+    CUDA graph over two frame slots: every sensor's records, offsets and state
+    equal the oracle's on that sensor alone, bit for bit.  This reaches the
+    descriptor search and the per-sensor chunk tables at several hundred
+    tiles per sensor."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import bench
+    from paper_2602_15018_gb300 import EventSimBatch
+    T, steps, t0 = 16, 3, 0
+    sensors = bench.batch_sensors(seed=3, n=24)
+    frames = []
+    for i, s in enumerate(sensors):
+        sc = scenes.TextureScene(s["width"], s["height"], seed=500 + i, speed=(150.0, 600.0))
+        frames.append(scenes.render_frames(sc, 1 + steps * T, device="cuda", chunk=17).cpu())
+    st = torch.cuda.Stream()
+    batch = EventSimBatch(sensors, frames_per_step=T, dt_us=DT, t0_us=t0, stream=st, max_pending_steps=steps)
+    orcs = []
+    for i, s in enumerate(sensors):
+        cp, cn = batch.thresholds(i)
+        ocp, ocn = oracle.threshold_maps(s["width"], s["height"], s["c_pos"], s["c_neg"], 0.03, 0.01, s["seed"])
+        assert np.array_equal(cp, ocp) and np.array_equal(cn, ocn)
+        orcs.append(oracle.OracleSim(s["width"], s["height"], c_pos_map=cp, c_neg_map=cn, refractory_us=100))
+    bufs = [[torch.empty((T, s["height"], s["width"]), dtype=torch.float32, device="cuda") for s in sensors]
+            for _ in range(2)]
+    with torch.cuda.stream(st):
+        first = [f[0].contiguous().cuda() for f in frames]
+        batch.init(first)
+        batch.set_frames(bufs[0], slot=0)
+        batch.set_frames(bufs[1], slot=1)
+    torch.cuda.synchronize()
+    graphs = []
+    for slot in range(2):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            batch.step(slot=slot)
+        graphs.append(g)
+    for k in range(steps):
+        for i in range(len(sensors)):
+            bufs[k % 2][i].copy_(frames[i][1 + k * T: 1 + (k + 1) * T])
+        torch.cuda.synchronize()
+        graphs[k % 2].replay()
+    torch.cuda.synchronize()
+    ev, seg = batch.drain()
+
+    def run(i):
+        o = orcs[i]
+        o.step(np.ascontiguousarray(frames[i][:1].numpy()), t0, DT)
+        evs, offs = [], [0]
+        for k in range(steps):
+            e, sg = o.step(np.ascontiguousarray(frames[i][1 + k * T: 1 + (k + 1) * T].numpy()),
+                           t0 + (1 + k * T) * DT, DT)
+            evs.append(e)
+            offs.extend((sg[1:] + offs[-1]).tolist())
+        o.step_result = (np.concatenate(evs), np.array(offs, np.int64))
+
+    with ThreadPoolExecutor(max_workers=8) as ex:
+        list(ex.map(run, range(len(sensors))))
+    per = batch.split(ev, seg)
+    total = 0
+    for i, o in enumerate(orcs):
+        _check_stream(batch, i, o, per[i][0], per[i][1], "benchmark shapes")
+        total += len(per[i][0])
+    assert total > 100_000
+    del first
+    batch.close()

@@ -34,9 +34,9 @@ def _frames(seed, T, H, W):
 def test_lowpass_matches_oracle(H, W, cutoff_hz):
     from paper_2602_15018_gb300 import lowpass_alpha, lowpass_log
     T = 37
-    alpha = lowpass_alpha(cutoff_hz, 1000)
+    alpha = lowpass_alpha(cutoff_hz, 1000)            # the library's gain
     L = _frames(int(cutoff_hz) % 1000 + H, T, H, W)
-    want, want_state = oracle.lowpass_log(L, alpha)
+    want, want_state = oracle.lowpass_log(L, oracle.lowpass_alpha(cutoff_hz, 1000))
     Ld = torch.from_numpy(L).cuda()
     got, st = lowpass_log(Ld, alpha)
     assert np.array_equal(got.cpu().numpy(), want)
@@ -55,7 +55,7 @@ def test_filtered_frames_give_the_oracles_events():
     H, W, T = 36, 52, 60
     alpha = lowpass_alpha(150.0, 1000)
     L = _frames(5, T, H, W)
-    filt, _ = oracle.lowpass_log(L, alpha)
+    filt, _ = oracle.lowpass_log(L, oracle.lowpass_alpha(150.0, 1000))
     sim_o = oracle.OracleSim(W, H, c_pos=0.15, c_neg=0.15, sigma_c=0.03, refractory_us=100, input_is_log=True,
                              seed=9)
     ev_o, seg_o = sim_o.step(filt, 0, 1000)

@@ -3,12 +3,16 @@
 The oracle rounds to BF16 exactly what the GPU stores in BF16 (weights and
 activations), so the two differ by FP32 accumulation order and by the BF16
 rounding of gradients the GPU keeps between layers; the tolerances below are
-derived from that: outputs within 1 % of the residual scale, gradients within
-a few BF16 ulps (2^-8) relative in norm.  Shapes: batch 2, 16 x 24 (several
-128-row tiles at full size, ragged tails at the quarter size), and 1 x 8 x 128
-and 1 x 8 x 160, whose full-size 3x3 layers run from halo tiles (rows of 128
-pixels; at width 160 the second tile of a row reaches past the image), and
-1 x 8 x 256, whose half-size 128-channel layers stream their weights.
+derived from that: outputs within 1 % of the residual scale; gradients, against
+the oracle that also rounds the activation gradients the GPU stores in BF16,
+element by element within 2^-9 of the tensor's largest entry plus 2^-6 of the
+entry.  Shapes: batch 2, 16 x 24 (several 128-row tiles at full size, ragged
+tails at the quarter size), and 1 x 8 x 128 and 1 x 8 x 160, whose full-size
+3x3 layers run from halo tiles (rows of 128 pixels; at width 160 the second
+tile of a row reaches past the image), 1 x 8 x 256, whose half-size
+128-channel layers stream their weights, 1 x 8 x 320 (halo tiles past the
+image at 2.5 tiles per row), 1 x 8 x 512 (the quarter-size 128-channel layer
+on the streamed-weight kernel) and 1 x 8 x 1280 (every layer at HD widths).
 Checkpoints are checked against their documented byte layout.
 """
 import numpy as np
@@ -76,7 +80,12 @@ def test_param_roundtrip_and_untrained_is_linear():
     net.close()
 
 
-SHAPES = [(2, 16, 24), (1, 8, 128), (1, 8, 160), (1, 8, 256)]
+# (1, 8, 320): full-size rows of 2.5 halo tiles (the last one past the image),
+# as the 320 x 240 sensors of the batched learned path run them; (1, 8, 512):
+# the quarter-size 128 -> 128 layer (conv4) and its data gradient take the
+# streamed-weight halo kernel (128-pixel rows); (1, 8, 1280): every layer at
+# the widths of an HD frame (conv4 on 320-pixel rows, conv6 on 640).
+SHAPES = [(2, 16, 24), (1, 8, 128), (1, 8, 160), (1, 8, 256), (1, 8, 320), (1, 8, 512), (1, 8, 1280)]
 
 
 @pytest.mark.parametrize("N,H,W", SHAPES)
@@ -95,6 +104,10 @@ def test_forward_matches_oracle(N, H, W):
     net.close()
 
 
+GRAD_ABS = 2.0 ** -9
+GRAD_REL = 2.0 ** -6
+
+
 @pytest.mark.parametrize("N,H,W", SHAPES)
 def test_gradients_match_oracle(N, H, W):
     p = _params(12)
@@ -104,7 +117,7 @@ def test_gradients_match_oracle(N, H, W):
     from paper_2602_15018_gb300.interp import to_dict
     gd = to_dict(g)
     ref_loss, ref_g, _ = io.loss_and_grads(p, clips[:, 0], clips[:, 4], np.moveaxis(clips[:, 1:4], 1, 0),
-                                           quantize=True)
+                                           quantize=True, quantize_grads=True)
     assert abs(loss - ref_loss) <= 1e-3 * ref_loss
     for k in list(io.SHAPES) + list(io.BIAS):
         a, b = np.asarray(gd[k], np.float64).reshape(-1), ref_g[k].reshape(-1)
@@ -112,8 +125,17 @@ def test_gradients_match_oracle(N, H, W):
         if nb == 0:
             assert np.linalg.norm(a) == 0, k
             continue
-        rel = np.linalg.norm(a - b) / nb
-        assert rel < 0.03, (k, rel)
+        # element by element: the oracle rounds to BF16 every activation and
+        # activation gradient the GPU stores in BF16, so the two differ by
+        # FP32 accumulation order (relative ~1e-6) and by the few BF16
+        # roundings that order flips (2^-8 of one stored value each, a small
+        # share of any sum it enters): GRAD_ABS of the tensor's largest entry
+        # plus GRAD_REL of the entry itself
+        bound = GRAD_ABS * np.abs(b).max() + GRAD_REL * np.abs(b)
+        bad = np.abs(a - b) > bound
+        assert not bad.any(), (k, int(bad.sum()), float(np.abs(a - b).max() / np.abs(b).max()))
+        rel = np.linalg.norm(a - b) / nb                    # summary in norm
+        assert rel < 2.0 ** -8, (k, rel)
     net.close()
 
 

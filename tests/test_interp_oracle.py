@@ -25,3 +25,7 @@ def test_gradients_match_finite_differences():
 
 def test_adamw_first_step_closed_form():
     IP.pin_adamw_first_step(io)
+
+
+def test_bf16_rounded_gradients_stay_close():
+    IP.pin_quantized_gradients(io)

@@ -3,7 +3,7 @@
 Each case rewrites one expression of oracle/interp_oracle.py in a temporary
 copy, loads the copy as its own module, and runs the pins of interp_pins.py
 against it: a flipped tap, transposed upsampling taps, a wrong interpolation
-weight, a dropped ReLU mask or skip gradient, a missing loss normalisation,
+weight, a dropped ReLU mask, skip gradient or skip mask, a missing loss normalisation,
 a missing AdamW bias correction, weight decay on biases, truncating BF16."""
 import importlib.util
 import os
@@ -20,8 +20,9 @@ MUTANTS = [
     ("convT2_taps_transposed", "out[:, a::2, b::2, :] = x @ w[:, a, b, :]", "out[:, a::2, b::2, :] = x @ w[:, b, a, :]"),
     ("interp_weight_shifted", "base = np.stack([L0 + (j / 4.0) * (L4 - L0) for j in (1, 2, 3)])",
      "base = np.stack([L0 + (j / 4.0) * (L4 - L0) for j in (0, 1, 2)])"),
-    ("relu_mask_dropped", "gd1 = gd1 * (c[\"d1\"] > 0)", "gd1 = gd1"),
-    ("skip_gradient_dropped", "ge2 = (ge2 + ge2b) * (c[\"e2\"] > 0)", "ge2 = ge2b * (c[\"e2\"] > 0)"),
+    ("relu_mask_dropped", "gd1 = q(gd1 * (c[\"d1\"] > 0))", "gd1 = q(gd1)"),
+    ("skip_gradient_dropped", "ge2 = q(ge2 + ge2b * (c[\"e2\"] > 0))", "ge2 = q(ge2b * (c[\"e2\"] > 0))"),
+    ("skip_mask_dropped", "ge1 = q(gcat1[..., 32:] * (c[\"e1\"] > 0))", "ge1 = q(gcat1[..., 32:])"),
     ("loss_grad_not_averaged", "return d / np.sqrt(d * d + CHARB_EPS * CHARB_EPS) / d.size",
      "return d / np.sqrt(d * d + CHARB_EPS * CHARB_EPS)"),
     ("adam_no_bias_correction", "upd = (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)",

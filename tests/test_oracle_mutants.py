@@ -47,6 +47,9 @@ MUTANTS = [
     ("lowpass_starts_at_zero", "float s = init ? L[i] : state[i];", "float s = init ? 0.0f : state[i];"),
     ("lowpass_state_not_saved", "        state[i] = s;\n    }\n    return ORACLE_OK;", "    }\n    return ORACLE_OK;"),
     ("lowpass_gain_squared", "s = fmaf(alpha, d, s);", "s = fmaf(alpha * alpha, d, s);"),
+    ("lowpass_alpha_no_two_pi", "exp(-two_pi * cutoff_hz", "exp(-cutoff_hz"),
+    ("lowpass_alpha_kept_fraction", "return (float)(1.0 - keep);", "return (float)keep;"),
+    ("lowpass_alpha_dt_in_ms", "((double)dt_us * 1e-6)", "((double)dt_us * 1e-3)"),
 ]
 
 

@@ -92,3 +92,24 @@ def test_intensity_clamp_and_nan(L):
     assert np.array_equal(sim.lprev, Lexp)
     t, x, y, p = oracle.unpack(ev)
     assert set(x[p == 0].tolist()) == {0, 1} and set(x[p == 1].tolist()) == {2}
+
+
+def test_banded_oracle_equals_one_sensor(L):
+    """The band-parallel oracle run (row bands on host threads, merged into the
+    output order) equals one oracle sensor over the whole frame, bit for bit,
+    on a textured scene with noise and refractory; with more bands than rows
+    too."""
+    import scenes
+    W, H, T = 61, 37, 30
+    fr = scenes.render_frames(scenes.TextureScene(W, H, seed=4, speed=(300.0, 600.0)), T).numpy()
+    cp, cn = oracle.threshold_maps(W, H, 0.2, 0.25, 0.03, 0.01, 9, library=L)
+    one = oracle.OracleSim(W, H, c_pos_map=cp, c_neg_map=cn, refractory_us=100, library=L)
+    ev, seg = one.step(fr, 0, 1000)
+    assert len(ev) > 500
+    for threads in (1, 3, 8, 64):
+        bev, bseg, used, st = oracle.banded_step(fr, W, H, 0, 1000, cp, cn, refractory_us=100, threads=threads,
+                                                 library=L)
+        assert used == min(threads, H)
+        assert np.array_equal(bseg, seg) and np.array_equal(bev, ev), threads
+        for k in ("ref", "lprev", "tlast"):
+            assert np.array_equal(st[k], getattr(one, k)), (threads, k)

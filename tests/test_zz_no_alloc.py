@@ -1,13 +1,17 @@
 """The no-allocation step entry point gives the same events as the regular one.
 
 neurosim_evsim_step_noalloc is meant for callers that cannot call cudaMalloc
-(code inside a CUDA graph being captured, real-time loops that must not enter
-the allocator, hosts that only borrow device buffers): every buffer is the
-caller's, and the library's intermediates live in one fixed device array.
-This test runs two consecutive steps through it, carrying the per-pixel state
-in caller-owned buffers, and compares events, interval offsets and state with
+(real-time loops that must not enter the device allocator, hosts that only
+borrow device buffers from another runtime): every buffer is the caller's,
+and the library's intermediates live in one fixed device array.  This test
+runs two consecutive steps through it, carrying the per-pixel state in
+caller-owned buffers, and compares events, interval offsets and state with
 the regular handle API (neurosim_evsim_step + drain) on the same frames; the
-two must agree bit for bit, as every GPU parity test here requires.
+two must agree bit for bit, as every GPU parity test here requires.  It also
+reads the device's free memory (cudaMemGetInfo) around the calls: the second
+call must leave it unchanged, and the first may lower it by no more than the
+fixed array and the code of the module that holds it, which the driver loads
+on first use.
 
 The file name sorts last so that a run stopping at the first failure has run
 every other test already; it also passes on its own in a fresh process.
@@ -68,26 +72,35 @@ def test_noalloc_matches_regular_entry_point_two_calls():
     lp_b = torch.empty_like(ref_a)
     tl_b = torch.empty_like(tl_a)
     cap = 2_000_000
-    events = torch.empty(cap, dtype=torch.int64, device=dev)
+    events = [torch.empty(cap, dtype=torch.int64, device=dev) for _ in range(2)]
+    offs = [torch.empty(T, dtype=torch.int64, device=dev), torch.empty(T + 1, dtype=torch.int64, device=dev)]
+    frames = [fr[s * T:(s + 1) * T].contiguous() for s in range(2)]
     stream = torch.cuda.current_stream().cuda_stream
-    n = C.c_uint64(0)
+    counts = []
     tau = -1
+    torch.cuda.synchronize()
+    free = [torch.cuda.mem_get_info()[0]]
     for s in range(2):
-        frames = fr[s * T:(s + 1) * T].contiguous()
-        n_int = T - 1 if s == 0 else T
-        offs = torch.empty(n_int + 1, dtype=torch.int64, device=dev)
+        n = C.c_uint64(0)
         src = (ref_a, lp_a, tl_a) if s == 1 else (None, None, None)
         dst = (ref_a, lp_a, tl_a) if s == 0 else (ref_b, lp_b, tl_b)
         rc = L.neurosim_evsim_step_noalloc(
-            _ptr(frames), T, W, H, s * T * DT, DT, _ptr(cp_d), _ptr(cn_d), 0.2, 0.25, 100, 1e-3, 0,
+            _ptr(frames[s]), T, W, H, s * T * DT, DT, _ptr(cp_d), _ptr(cn_d), 0.2, 0.25, 100, 1e-3, 0,
             _ptr(src[0]), _ptr(src[1]), _ptr(src[2]), _ptr(dst[0]), _ptr(dst[1]), _ptr(dst[2]),
-            1 if s == 1 else 0, tau, _ptr(events), cap, _ptr(offs), C.byref(n), C.c_void_p(stream))
+            1 if s == 1 else 0, tau, _ptr(events[s]), cap, _ptr(offs[s]), C.byref(n), C.c_void_p(stream))
         _lib.check(rc)
-        got = events[: n.value].cpu().numpy().view(np.uint64)
-        assert n.value == len(ref_ev[s]) > 0
-        assert np.array_equal(got, ref_ev[s]), f"events of call {s} differ"
-        assert np.array_equal(offs.cpu().numpy(), ref_seg[s]), f"offsets of call {s} differ"
+        counts.append(n.value)
+        free.append(torch.cuda.mem_get_info()[0])
         tau = s * T * DT + (T - 1) * DT
+    # nothing allocated: the second call leaves the free memory as it was; the
+    # first may only add the fixed 32 MiB array and its module's code
+    assert free[2] == free[1], f"the second call changed free device memory by {free[1] - free[2]} bytes"
+    assert 0 <= free[0] - free[1] <= (32 << 20) + (16 << 20), f"first call: {free[0] - free[1]} bytes"
+    for s in range(2):
+        got = events[s][: counts[s]].cpu().numpy().view(np.uint64)
+        assert counts[s] == len(ref_ev[s]) > 0
+        assert np.array_equal(got, ref_ev[s]), f"events of call {s} differ"
+        assert np.array_equal(offs[s].cpu().numpy(), ref_seg[s]), f"offsets of call {s} differ"
     assert np.array_equal(ref_b.cpu().numpy(), st["ref"])
     assert np.array_equal(lp_b.cpu().numpy(), st["lprev"])
     assert np.array_equal(tl_b.cpu().numpy().view(np.uint32), st["tlast"])
