@@ -241,6 +241,7 @@ def backward(p, cache, gout, quantize_grads=False):
     return g
 
 
+
 def loss_and_grads(p, L0, L4, targets, quantize=False, quantize_grads=False):
     out, cache = forward(p, L0, L4, quantize)
     g = backward(p, cache, charbonnier_grad(out, targets), quantize_grads)
