@@ -438,6 +438,73 @@ int neurosim_event_frames(int32_t *counts_dev, int32_t width, int32_t height, co
 int neurosim_event_f1(const uint64_t *pred, int64_t n_pred, const uint64_t *ref, int64_t n_ref,
                       int64_t tol_us, int64_t *counts, double *scores);
 
+/* ------------------------------------------------------------------------
+ * Render-fused event simulation.  Sec. 1 of the paper argues that event data
+ * should be produced on the fly, without storing the rendered images.  The
+ * library carries a seeded procedural scene (the scenes of the paper are
+ * rendered by a graphics engine, not available here) that the emission
+ * kernel can render itself, pixel by pixel, in place of reading frames: a
+ * fused step moves no frame bytes through memory.  The same scene can be
+ * rendered to memory by neurosim_render_texture, bit for bit the
+ * intensities the fused step sees.
+ *
+ * Scene: value noise of `octaves` octaves (hashed integer lattice with
+ * smoothstep interpolation, base period `base_period` px, each octave at
+ * half the period and `gain` times the amplitude of the one before; octave
+ * o (from 0) hashes with salt + 0x9E3779B9 (o + 1)), mapped to
+ * [intensity_lo, intensity_hi]; seen through a camera that rotates by
+ * theta(t) = rot_amp / k (cos(rot_phase) - cos(k t + rot_phase)),
+ * k = 2 pi / rot_period (the integral of a rotation rate rot_amp
+ * sin(k t + rot_phase), rad/s), zooms by z(t) = 1 + zoom_amp
+ * sin(2 pi t / zoom_period + zoom_phase) about the image centre and
+ * translates by (vx, vy) t + (offset_x, offset_y): pixel (x, y) sees texture
+ * point R(theta) ((x, y) - centre) / z + centre + (vx, vy) t + offset.
+ * Then n_rects rectangles, drawn in order (the last on top): rectangle i
+ * of size rect_w x rect_h has constant intensity rect_value and its centre
+ * at ((rect_x + rect_vx t) mod (W + rect_w) - rect_w / 2, (rect_y + rect_vy t)
+ * mod (H + rect_h) - rect_h / 2); it covers the pixels strictly within half
+ * its size of the centre.  Times in seconds.  The per-frame camera and
+ * rectangles are evaluated in double, the pixels in FP32.
+ * ---------------------------------------------------------------------- */
+#define NEUROSIM_MAX_RECTS 16
+
+typedef struct neurosim_texture_scene {
+    int32_t width, height;       /* pixels, as a sensor's params               */
+    uint32_t salt;               /* value-noise hash salt                      */
+    int32_t octaves;             /* 1..8                                       */
+    float base_period;           /* px, in [1, 65536]                          */
+    float gain;                  /* amplitude ratio of successive octaves, (0, 1] */
+    float intensity_lo, intensity_hi;  /* noise range, 0 <= lo <= hi <= 1e6   */
+    double vx, vy;               /* camera translation, px/s                   */
+    double offset_x, offset_y;   /* texture offset, px                         */
+    double rot_amp_rad_s, rot_period_s, rot_phase;
+    double zoom_amp, zoom_period_s, zoom_phase;   /* |zoom_amp| < 0.5          */
+    int32_t n_rects;             /* 0..NEUROSIM_MAX_RECTS                      */
+    int32_t reserved;            /* must be zero                               */
+    double rect_x[NEUROSIM_MAX_RECTS], rect_y[NEUROSIM_MAX_RECTS];
+    double rect_w[NEUROSIM_MAX_RECTS], rect_h[NEUROSIM_MAX_RECTS];
+    double rect_vx[NEUROSIM_MAX_RECTS], rect_vy[NEUROSIM_MAX_RECTS];
+    double rect_value[NEUROSIM_MAX_RECTS];
+} neurosim_texture_scene;
+
+/* Renders frames t0_us + f * dt_us, f < n_frames (<= 65535), of the scene
+ * into frames_dev (DEVICE FP32 [n_frames][height][width], caller-owned).
+ * Asynchronous on cuda_stream (allocates its per-frame table there).
+ * NEUROSIM_E_INVALID for a bad scene or a NULL buffer, NEUROSIM_E_TIME for
+ * t0_us < 0 or dt_us < 1. */
+int neurosim_render_texture(const neurosim_texture_scene *scene, float *frames_dev, int32_t n_frames,
+                            int64_t t0_us, int32_t dt_us, void *cuda_stream);
+
+/* As neurosim_evsim_step over the frames neurosim_render_texture would
+ * render for (scene, n_frames, t0_us, dt_us), with the rendering fused into
+ * the emission kernel (Sec. 2 per-frame update on frames produced on the
+ * fly, Sec. 1).  The scene must have the sensor's width and height; it is
+ * copied, so the caller may change it after the call.  Same timing rules,
+ * asynchrony and errors as neurosim_evsim_step; events are identical to
+ * those of neurosim_evsim_step on the rendered frames. */
+int neurosim_evsim_step_texture(neurosim_evsim *h, const neurosim_texture_scene *scene, int32_t n_frames,
+                                int64_t t0_us, int32_t dt_us);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *neurosim_last_error(void);
 

@@ -36,13 +36,32 @@ EXPORTS = [
     "neurosim_interp_launches", "neurosim_interp_destroy",
     "neurosim_event_f1", "neurosim_log_intensity", "neurosim_time_surface", "neurosim_event_frames",
     "neurosim_lowpass_log", "neurosim_lowpass_alpha", "neurosim_debug_expiring_wait",
+    "neurosim_render_texture", "neurosim_evsim_step_texture",
 ]
+
+MAX_RECTS = 16
 
 
 class NeurosimError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
         self.code = code
+
+
+class TextureScene(C.Structure):
+    """Mirror of neurosim_texture_scene."""
+    _fields_ = [
+        ("width", C.c_int32), ("height", C.c_int32), ("salt", C.c_uint32), ("octaves", C.c_int32),
+        ("base_period", C.c_float), ("gain", C.c_float), ("intensity_lo", C.c_float), ("intensity_hi", C.c_float),
+        ("vx", C.c_double), ("vy", C.c_double), ("offset_x", C.c_double), ("offset_y", C.c_double),
+        ("rot_amp_rad_s", C.c_double), ("rot_period_s", C.c_double), ("rot_phase", C.c_double),
+        ("zoom_amp", C.c_double), ("zoom_period_s", C.c_double), ("zoom_phase", C.c_double),
+        ("n_rects", C.c_int32), ("reserved", C.c_int32),
+        ("rect_x", C.c_double * MAX_RECTS), ("rect_y", C.c_double * MAX_RECTS),
+        ("rect_w", C.c_double * MAX_RECTS), ("rect_h", C.c_double * MAX_RECTS),
+        ("rect_vx", C.c_double * MAX_RECTS), ("rect_vy", C.c_double * MAX_RECTS),
+        ("rect_value", C.c_double * MAX_RECTS),
+    ]
 
 
 class Params(C.Structure):
@@ -189,6 +208,10 @@ def lib():
             L.neurosim_event_frames.argtypes = [vp, i32, i32, vp, i64, i64, i64, i32, vp]
             L.neurosim_lowpass_log.restype = C.c_int
             L.neurosim_lowpass_log.argtypes = [vp, vp, i32, i64, C.c_float, vp, i32, vp]
+            L.neurosim_render_texture.restype = C.c_int
+            L.neurosim_render_texture.argtypes = [C.POINTER(TextureScene), vp, i32, i64, i32, vp]
+            L.neurosim_evsim_step_texture.restype = C.c_int
+            L.neurosim_evsim_step_texture.argtypes = [vp, C.POINTER(TextureScene), i32, i64, i32]
             L.neurosim_debug_expiring_wait.restype = C.c_int
             L.neurosim_debug_expiring_wait.argtypes = [i32, u64, vp]
             L.neurosim_lowpass_alpha.restype = C.c_int

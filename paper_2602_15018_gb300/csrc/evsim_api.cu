@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "../../include/neurosim_evsim.h"
@@ -75,6 +76,7 @@ struct StepRec {
     int32_t T;
     int64_t t0;
     int32_t dt;
+    std::shared_ptr<neurosim_texture_scene> scene;   // rendered step: the scene (frames unused)
 };
 
 template <typename T>
@@ -102,6 +104,7 @@ struct neurosim_evsim {
     int W = 0, H = 0, npix = 0, pix_bits = 1;
     int ppt = 16, pf = 2, n_tiles = 0;
     int grid_emit32 = 0, grid_emit64 = 0, sort_smem = 0;
+    int grid_tex32 = 0, grid_tex64 = 0;   // render-fused steps
     int Tmax = 1024;
     int64_t max_pending = 65536;
 
@@ -130,6 +133,7 @@ struct neurosim_evsim {
     Ctl* ctl = nullptr;
 
     float* staging = nullptr;  // device copy of host frames (step_host)
+    void* scene_tab = nullptr; // per-frame scene table of a render-fused step (Tmax rows)
 
     std::vector<StepRec> pending;
     int64_t n_pending_segs = 0;
@@ -192,6 +196,8 @@ void release(neurosim_evsim* h)
     dfree(h->out);
     dfree(h->ctl);
     dfree(h->staging);
+    if (h->scene_tab) cudaFree(h->scene_tab);
+    h->scene_tab = nullptr;
 }
 
 int alloc_event_buffers(neurosim_evsim* h, uint64_t out_cap, size_t key_bytes)
@@ -252,7 +258,8 @@ int check_handle(neurosim_evsim* h)
 }
 
 // Fills the launch descriptor of one step and enqueues it.
-int enqueue_step(neurosim_evsim* h, const float* frames_dev, int32_t T, int64_t t0, int32_t dt)
+int enqueue_step(neurosim_evsim* h, const float* frames_dev, int32_t T, int64_t t0, int32_t dt,
+                 const neurosim_texture_scene* scene = nullptr)
 {
     const bool init = !h->has_w;
     const int32_t D0 = init ? dt : (int32_t)(t0 - h->tau_w);
@@ -293,6 +300,17 @@ int enqueue_step(neurosim_evsim* h, const float* frames_dev, int32_t T, int64_t 
     s.ta0 = ta0;
     s.chunk_base = 0;
     s.out_seg_index = h->n_pending_segs;
+    if (scene) {
+        // render-fused: the per-frame camera and rectangles, then the frames
+        // come from the renderer inside the emission kernel
+        if (!h->scene_tab) CUDA_TRY(cudaMalloc(&h->scene_tab, (size_t)h->Tmax * scene_frame_bytes()));
+        CUDA_TRY(launch_scene_frames(*scene, t0, dt, T, h->scene_tab, h->stream));
+        h->stats.kernel_launches += 1;
+        s.frames = nullptr;
+        s.vec = 0;
+        s.scene_tab = h->scene_tab;
+        s.scene = make_scene_const(*scene);
+    }
 
     L.streams_dev = nullptr;
     L.n_streams = 1;
@@ -304,7 +322,7 @@ int enqueue_step(neurosim_evsim* h, const float* frames_dev, int32_t T, int64_t 
     L.t_bits = t_bits;
     L.ppt = h->ppt;
     L.pf = h->pf;
-    L.grid_emit = key64 ? h->grid_emit64 : h->grid_emit32;
+    L.grid_emit = scene ? (key64 ? h->grid_tex64 : h->grid_tex32) : (key64 ? h->grid_emit64 : h->grid_emit32);
     L.grid_sort = std::max(1, std::min(n_segs, h->sms * 2));
     L.sort_smem = h->sort_smem;
     L.max_tiles = h->n_tiles;
@@ -431,7 +449,7 @@ int resolve(neurosim_evsim* h, Ctl* c)
                 rc = host_frames_for_step(h, s.frames, s.T, &fr);
                 if (rc) return rc;
             }
-            rc = enqueue_step(h, fr, s.T, s.t0, s.dt);
+            rc = enqueue_step(h, fr, s.T, s.t0, s.dt, s.scene.get());
             if (rc) return rc;
             h->pending.push_back(s);
         }
@@ -506,6 +524,12 @@ int neurosim_evsim_create(const neurosim_evsim_params* p, void* cuda_stream, neu
     const int wpc = emit_warps_per_cta(h->ppt);
     h->grid_emit32 = std::min((h->n_tiles + wpc - 1) / wpc, h->sms * bps32);
     h->grid_emit64 = std::min((h->n_tiles + wpc - 1) / wpc, h->sms * bps64);
+    int tps32 = 0, tps64 = 0;
+    if (emit_occupancy(h->ppt, h->pf, 0, &tps32, 1) != cudaSuccess ||
+        emit_occupancy(h->ppt, h->pf, 1, &tps64, 1) != cudaSuccess || tps32 < 1 || tps64 < 1)
+        return bail(fail(NEUROSIM_E_CUDA, "render-fused emission kernel does not fit (ppt %d)", h->ppt));
+    h->grid_tex32 = std::min((h->n_tiles + wpc - 1) / wpc, h->sms * tps32);
+    h->grid_tex64 = std::min((h->n_tiles + wpc - 1) / wpc, h->sms * tps64);
     if (sort_configure(&h->sort_smem) != cudaSuccess)
         return bail(fail(NEUROSIM_E_CUDA, "cannot configure the sort kernel"));
 
@@ -563,7 +587,7 @@ int neurosim_evsim_step(neurosim_evsim* h, const float* frames_dev, int32_t n_fr
     if (!g.ok) return fail(NEUROSIM_E_CUDA, "cannot select the handle's device");
     rc = enqueue_step(h, frames_dev, n_frames, t0_us, dt_us);
     if (rc) return rc;
-    h->pending.push_back(StepRec{frames_dev, false, n_frames, t0_us, dt_us});
+    h->pending.push_back(StepRec{frames_dev, false, n_frames, t0_us, dt_us, nullptr});
     return NEUROSIM_OK;
 }
 
@@ -582,7 +606,27 @@ int neurosim_evsim_step_host(neurosim_evsim* h, const float* frames_host, int32_
     if (rc) return rc;
     rc = enqueue_step(h, fr, n_frames, t0_us, dt_us);
     if (rc) return rc;
-    h->pending.push_back(StepRec{frames_host, true, n_frames, t0_us, dt_us});
+    h->pending.push_back(StepRec{frames_host, true, n_frames, t0_us, dt_us, nullptr});
+    return NEUROSIM_OK;
+}
+
+int neurosim_evsim_step_texture(neurosim_evsim* h, const neurosim_texture_scene* scene, int32_t n_frames,
+                                int64_t t0_us, int32_t dt_us)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    rc = check_scene(scene);
+    if (rc) return rc;
+    if (scene->width != h->W || scene->height != h->H)
+        return fail(NEUROSIM_E_INVALID, "scene is %dx%d, the sensor %dx%d", scene->width, scene->height, h->W, h->H);
+    rc = check_times(h, n_frames, t0_us, dt_us);
+    if (rc || n_frames == 0) return rc;
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(NEUROSIM_E_CUDA, "cannot select the handle's device");
+    auto copy = std::make_shared<neurosim_texture_scene>(*scene);
+    rc = enqueue_step(h, nullptr, n_frames, t0_us, dt_us, copy.get());
+    if (rc) return rc;
+    h->pending.push_back(StepRec{nullptr, false, n_frames, t0_us, dt_us, copy});
     return NEUROSIM_OK;
 }
 

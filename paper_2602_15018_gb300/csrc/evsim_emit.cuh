@@ -408,7 +408,76 @@ __device__ __forceinline__ void interval_of(int64_t ta0, int D0, int dt, int j, 
     Df = (float)(j == 0 ? D0 : dt);
 }
 
-template <int PPT, int WARPS, int PF, typename KeyT>
+// Frame sources of the emission kernel: frames read from memory, or rendered
+// from a texture scene (scene_render.cuh) in place of the read.
+template <int PPT>
+struct MemSource {
+    const float* fp;       // the lane's first pixel in frame 0
+    int64_t fstride;
+    int nvq, vec, lane_left;
+    uint64_t pol;
+    __device__ __forceinline__ void load(float4 (&b)[PPT / 4], int f) const
+    {
+        load_frame<PPT>(b, fp + (int64_t)f * fstride, nvq, vec, lane_left, pol);
+    }
+};
+
+template <int PPT>
+struct TexSource {
+    const SceneFrame* tab;   // row f: camera and rectangles of the step's frame f
+    SceneConst sc;
+    int lane;
+    float y_lo, y_hi;        // rows the warp's tile spans
+    int x0[PPT / 4], y0[PPT / 4];   // pixel of (q, component 0)
+    // Renders the lane's pixels of frame f.  Warp-collective: the rectangles
+    // that can reach the tile's rows are found with one ballot and applied in
+    // rectangle order, as texture_pixel does.
+    __device__ __forceinline__ void load(float4 (&b)[PPT / 4], int f) const
+    {
+        const SceneFrame& fr = tab[f];
+        float4 rk = make_float4(0.f, 0.f, 0.f, 0.f);
+        float vk = 0.0f;
+        bool rel = false;
+        if (lane < sc.n_rects) {
+            rk = fr.rect[lane];
+            vk = fr.rval[lane];
+            // a pixel row y can be covered only if |y - cy| < hh (one row of margin
+            // for the rounding of y - cy)
+            rel = __fadd_rn(__fadd_rn(rk.y, rk.w), 1.0f) > y_lo && __fsub_rn(__fsub_rn(rk.y, rk.w), 1.0f) < y_hi;
+        }
+        uint32_t rmask = __ballot_sync(0xffffffffu, rel);
+#pragma unroll
+        for (int q = 0; q < PPT / 4; ++q) {
+            float v[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                int x = x0[q] + m, y = y0[q];
+                if (x >= sc.W) { x -= sc.W; y += 1; }
+                v[m] = texture_noise(sc, fr, (float)x, (float)y);
+            }
+            b[q] = make_float4(v[0], v[1], v[2], v[3]);
+        }
+        while (rmask) {
+            const int k = __ffs(rmask) - 1;
+            rmask &= rmask - 1u;
+            const float4 r = make_float4(__shfl_sync(0xffffffffu, rk.x, k), __shfl_sync(0xffffffffu, rk.y, k),
+                                         __shfl_sync(0xffffffffu, rk.z, k), __shfl_sync(0xffffffffu, rk.w, k));
+            const float val = __shfl_sync(0xffffffffu, vk, k);
+#pragma unroll
+            for (int q = 0; q < PPT / 4; ++q) {
+                float* c = reinterpret_cast<float*>(&b[q]);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    int x = x0[q] + m, y = y0[q];
+                    if (x >= sc.W) { x -= sc.W; y += 1; }
+                    if (rect_covers(r, (float)x, (float)y)) c[m] = val;
+                }
+            }
+        }
+    }
+};
+
+template <int PPT, int WARPS, int PF, typename KeyT, int SRC>
 __global__ void __launch_bounds__(WARPS * 32) emit_kernel(const __grid_constant__ StepLaunch L)
 {
     (void)PF;   // one pair of frames in flight whatever the prefetch setting
@@ -504,11 +573,32 @@ __global__ void __launch_bounds__(WARPS * 32) emit_kernel(const __grid_constant_
         uint32_t lvalid = init ? 0u : valid;   // lb holds L of the frame before the next one
 
         // frame pipeline: one pair of frames in flight per lane
-        const float* fp = sdp->frames + lane_g;
+        typename std::conditional<SRC == 0, MemSource<PPT>, TexSource<PPT>>::type src;
+        if constexpr (SRC == 0) {
+            src.fp = sdp->frames + lane_g;
+            src.fstride = fstride;
+            src.nvq = nvq;
+            src.vec = vec;
+            src.lane_left = lane_left;
+            src.pol = pol_stream;
+        } else {
+            src.tab = static_cast<const SceneFrame*>(sdp->scene_tab);
+            src.sc = sdp->scene;
+            src.lane = lane;
+            const int W = sdp->scene.W;
+            src.y_lo = (float)(c.g0 / W);
+            src.y_hi = (float)((min(c.g0 + WPX, npix) - 1) / W);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int g = lane_g + q * 128;
+                src.y0[q] = g / W;
+                src.x0[q] = g - src.y0[q] * W;
+            }
+        }
         float4 buf[2][NQ];
 #pragma unroll
         for (int u = 0; u < 2; ++u)
-            if (u < T) load_frame<PPT>(buf[u], fp + (int64_t)u * fstride, nvq, vec, lane_left, pol_stream);
+            if (u < T) src.load(buf[u], u);
         int fs = 0;
         if (init && T > 0) {
             // frame 0 initialises the state; the pairs start at frame 1
@@ -530,7 +620,7 @@ __global__ void __launch_bounds__(WARPS * 32) emit_kernel(const __grid_constant_
             fs = 1;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) buf[0][q] = buf[1][q];
-            if (2 < T) load_frame<PPT>(buf[1], fp + 2 * fstride, nvq, vec, lane_left, pol_stream);
+            if (2 < T) src.load(buf[1], 2);
         }
         __syncwarp();
 
@@ -554,8 +644,8 @@ __global__ void __launch_bounds__(WARPS * 32) emit_kernel(const __grid_constant_
             }
             trig0 &= valid;
             trig1 &= valid;
-            if (f0 + 2 < T) load_frame<PPT>(buf[0], fp + (int64_t)(f0 + 2) * fstride, nvq, vec, lane_left, pol_stream);
-            if (f0 + 3 < T) load_frame<PPT>(buf[1], fp + (int64_t)(f0 + 3) * fstride, nvq, vec, lane_left, pol_stream);
+            if (f0 + 2 < T) src.load(buf[0], f0 + 2);
+            if (f0 + 3 < T) src.load(buf[1], f0 + 3);
             const int j0 = f0 - init;                     // intervals of the pair's frames
             const uint32_t mall = trig0 | trig1;
             if (!__any_sync(0xffffffffu, mall != 0u)) {

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/neurosim_evsim.h"
+
 namespace nsim {
 
 constexpr uint32_t kTlastNone = 0xFFFFFFFFu;   // "no event yet" marker of t_last
@@ -46,6 +48,18 @@ struct DevClock {
     unsigned int sticky;                  // kErr* bits of the failed step, 0 if none
 };
 
+// Constants of a procedural texture scene that every rendered pixel needs
+// (scene_render.cuh).
+struct SceneConst {
+    uint32_t salt;
+    int32_t octaves;
+    float inv_period;      // 1 / base period (px)
+    float gain;            // amplitude ratio of successive octaves
+    float lo, span;        // intensity = lo + span * noise / sum of amplitudes
+    int32_t n_rects;
+    int32_t W;
+};
+
 // One sensor stream inside a step launch.
 struct StreamDesc {
     const float* frames;          // [T][npix] FP32 (device)
@@ -74,6 +88,9 @@ struct StreamDesc {
     int64_t chunk_base;           // chunk-table offset of (segment 0, tile 0)
     int64_t out_seg_index;        // slot of segment 0 in the pending offset array
     int64_t frame_stride;         // floats from one frame to the next (0: npix)
+    const void* scene_tab;        // per-frame SceneFrame table of a rendered step, or
+                                  // nullptr: frames are read from `frames`
+    SceneConst scene;             // constants of the rendered scene
 };
 
 // Everything one step launch needs (passed by value as a __grid_constant__).
@@ -115,6 +132,15 @@ struct StepLaunch {
     cudaEvent_t ev_sorted;          //   after the interval sort
 };
 
+// Per-frame camera and occluder table of a texture scene (scene_render.cuh)
+// for frames t0 + f dt, f < n_frames, into `tab` (device, n_frames rows of
+// scene_frame_bytes()); and the renderer writing FP32 frames [n][H][W].
+size_t scene_frame_bytes();
+cudaError_t launch_scene_frames(const neurosim_texture_scene& sc, int64_t t0_us, int32_t dt_us, int n_frames,
+                                void* tab, cudaStream_t stream);
+SceneConst make_scene_const(const neurosim_texture_scene& sc);
+int check_scene(const neurosim_texture_scene* s);   // NEUROSIM_OK or reports the bad field
+
 // Enqueues emission, segment count, segment scan and segment sort (and, with
 // a device clock, the clock advance); adds the number of kernels launched to
 // *launches.  With a device clock, streams_dev holds two descriptor sets of
@@ -124,7 +150,8 @@ cudaError_t launch_step(const StepLaunch& L, uint64_t* launches);
 // Emission launch geometry helpers (CTA = 64/ppt warps).
 int emit_warps_per_cta(int ppt);
 size_t emit_smem_bytes(int ppt);
-cudaError_t emit_occupancy(int ppt, int pf, int key64, int* blocks_per_sm);
+// src 0: frames read from memory; 1: frames rendered from a texture scene
+cudaError_t emit_occupancy(int ppt, int pf, int key64, int* blocks_per_sm, int src = 0);
 cudaError_t sort_configure(int* smem_bytes);
 
 // Create-time per-pixel thresholds: C+-_u = max(c_min, C+- + sigma * z+-_u).

@@ -36,7 +36,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "evsim_internal.h"
+#include "scene_render.cuh"
 
 namespace nsim {
 namespace {
@@ -565,25 +568,36 @@ __global__ void advance_kernel(DevClock* clk, Ctl* ctl, int n_segs, long long ad
     clk->steps += 1ull;
 }
 
+// A rendered step (scene_tab set) takes the frames from the texture renderer.
 template <int PPT, int PF>
 cudaError_t launch_emit_t(const StepLaunch& L, size_t smem)
 {
     constexpr int WARPS = 64 / PPT;
     // (the dynamic shared-memory attribute was set by emit_occupancy at create
     // time, so that launches stay capturable)
-    if (L.key64)
-        emit_kernel<PPT, WARPS, PF, uint64_t><<<L.grid_emit, WARPS * 32, smem, L.stream>>>(L);
-    else
-        emit_kernel<PPT, WARPS, PF, uint32_t><<<L.grid_emit, WARPS * 32, smem, L.stream>>>(L);
+    const bool tex = L.n_streams == 1 && L.streams_dev == nullptr && L.s0.scene_tab != nullptr;
+    if (tex) {
+        if (L.key64)
+            emit_kernel<PPT, WARPS, PF, uint64_t, 1><<<L.grid_emit, WARPS * 32, smem, L.stream>>>(L);
+        else
+            emit_kernel<PPT, WARPS, PF, uint32_t, 1><<<L.grid_emit, WARPS * 32, smem, L.stream>>>(L);
+    } else if (L.key64) {
+        emit_kernel<PPT, WARPS, PF, uint64_t, 0><<<L.grid_emit, WARPS * 32, smem, L.stream>>>(L);
+    } else {
+        emit_kernel<PPT, WARPS, PF, uint32_t, 0><<<L.grid_emit, WARPS * 32, smem, L.stream>>>(L);
+    }
     return cudaGetLastError();
 }
 
-const void* emit_fn(int ppt, int pf, int key64)
+const void* emit_fn(int ppt, int pf, int key64, int src)
 {
-#define NSIM_PICK(P, F)                                                                    \
-    if (ppt == P && pf == F)                                                               \
-        return key64 ? (const void*)emit_kernel<P, 64 / P, F, uint64_t>                   \
-                     : (const void*)emit_kernel<P, 64 / P, F, uint32_t>;
+#define NSIM_PICK(P, F)                                                                                 \
+    if (ppt == P && pf == F) {                                                                          \
+        if (src) return key64 ? (const void*)emit_kernel<P, 64 / P, F, uint64_t, 1>                    \
+                              : (const void*)emit_kernel<P, 64 / P, F, uint32_t, 1>;                   \
+        return key64 ? (const void*)emit_kernel<P, 64 / P, F, uint64_t, 0>                             \
+                     : (const void*)emit_kernel<P, 64 / P, F, uint32_t, 0>;                            \
+    }
     NSIM_PICK(8, 2) NSIM_PICK(8, 3) NSIM_PICK(16, 2) NSIM_PICK(16, 3)
 #undef NSIM_PICK
     return nullptr;
@@ -599,15 +613,14 @@ size_t emit_smem_bytes(int ppt)
     return (size_t)emit_warps_per_cta(ppt) * per_warp * sizeof(float);
 }
 
-cudaError_t emit_occupancy(int ppt, int pf, int key64, int* blocks_per_sm)
+cudaError_t emit_occupancy(int ppt, int pf, int key64, int* blocks_per_sm, int src)
 {
-    const void* fn = emit_fn(ppt, pf, key64);
+    const void* fn = emit_fn(ppt, pf, key64, src);
     if (!fn) return cudaErrorInvalidValue;
     const size_t smem = emit_smem_bytes(ppt);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, emit_warps_per_cta(ppt) * 32,
-                                                         smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, emit_warps_per_cta(ppt) * 32, smem);
 }
 
 cudaError_t sort_configure(int* smem_bytes)

@@ -12,7 +12,7 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import BatchParams, Params, Stats, check, lib
+from ._lib import MAX_RECTS, BatchParams, Params, Stats, TextureScene, check, lib
 
 
 def _params(width: int, height: int, c_pos: float = 0.2, c_neg: float = 0.2,
@@ -96,6 +96,11 @@ class EventSim:
         check(lib().neurosim_evsim_step(self._h, C.c_void_p(frames.data_ptr()), T, int(t0_us),
                                         int(dt_us)))
         self._keep.append(frames)
+
+    def step_texture(self, scene: TextureScene, n_frames: int, t0_us: int, dt_us: int) -> None:
+        """Render-fused step (library call neurosim_evsim_step_texture): the
+        emission kernel renders the texture scene's frames t0 + f dt itself."""
+        check(lib().neurosim_evsim_step_texture(self._h, C.byref(scene), int(n_frames), int(t0_us), int(dt_us)))
 
     def step_host(self, frames, t0_us: int, dt_us: int) -> None:
         """Step from HOST frames (numpy or CPU tensor, float32, C-contiguous)."""
@@ -499,4 +504,41 @@ def event_frames(events: torch.Tensor, width: int, height: int, t_start_us: int,
                                       C.c_void_p(events.data_ptr() if events.numel() else 0), events.numel(),
                                       int(t_start_us), int(window_us), int(n_windows),
                                       C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return out
+
+
+def texture_scene(width: int, height: int, salt: int, octaves: int = 4, base_period: float = 64.0,
+                  gain: float = 0.5, intensity=(0.02, 1.0), velocity=(0.0, 0.0), offset=(0.0, 0.0),
+                  rotation=(0.0, 1.0, 0.0), zoom=(0.0, 1.0, 0.0), rects=()) -> TextureScene:
+    """A neurosim_texture_scene: rotation = (rate amplitude rad/s, period s,
+    phase), zoom = (amplitude, period s, phase), rects = up to 16 tuples
+    (x, y, w, h, vx, vy, value) in pixels, px/s and intensity."""
+    if len(rects) > MAX_RECTS:
+        raise ValueError(f"at most {MAX_RECTS} rectangles")
+    s = TextureScene()
+    s.width, s.height, s.salt, s.octaves = int(width), int(height), int(salt) & 0xFFFFFFFF, int(octaves)
+    s.base_period, s.gain = float(base_period), float(gain)
+    s.intensity_lo, s.intensity_hi = float(intensity[0]), float(intensity[1])
+    s.vx, s.vy = float(velocity[0]), float(velocity[1])
+    s.offset_x, s.offset_y = float(offset[0]), float(offset[1])
+    s.rot_amp_rad_s, s.rot_period_s, s.rot_phase = (float(v) for v in rotation)
+    s.zoom_amp, s.zoom_period_s, s.zoom_phase = (float(v) for v in zoom)
+    s.n_rects = len(rects)
+    for i, (x, y, w, h, vx, vy, val) in enumerate(rects):
+        s.rect_x[i], s.rect_y[i], s.rect_w[i], s.rect_h[i] = float(x), float(y), float(w), float(h)
+        s.rect_vx[i], s.rect_vy[i], s.rect_value[i] = float(vx), float(vy), float(val)
+    return s
+
+
+def render_texture(scene: TextureScene, n_frames: int, t0_us: int = 0, dt_us: int = 1000,
+                   out: torch.Tensor | None = None) -> torch.Tensor:
+    """Frames t0 + f dt, f < n_frames, of the scene (library renderer) as a
+    CUDA float32 tensor [n_frames, height, width]."""
+    if out is None:
+        out = torch.empty((int(n_frames), scene.height, scene.width), dtype=torch.float32, device="cuda")
+    elif not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+              and out.numel() == int(n_frames) * scene.width * scene.height):
+        raise ValueError("out must be a contiguous float32 CUDA tensor of n_frames frames")
+    check(lib().neurosim_render_texture(C.byref(scene), C.c_void_p(out.data_ptr()), int(n_frames), int(t0_us),
+                                        int(dt_us), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
     return out

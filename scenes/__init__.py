@@ -138,6 +138,17 @@ class TextureScene:
         self.rvx = rs * np.cos(ra)
         self.rvy = rs * np.sin(ra)
 
+    def params(self) -> dict:
+        """The scene as keyword arguments of the library's texture_scene (the
+        same camera, texture and rectangles; its renderer works in FP32)."""
+        rects = [(self.rcx[k], self.rcy[k], self.rw[k], self.rh[k], self.rvx[k], self.rvy[k], self.rval[k])
+                 for k in range(len(self.rw))]
+        return dict(width=self.W, height=self.H, salt=self.salt, octaves=self.octaves,
+                    base_period=self.base_period, gain=0.5, intensity=(0.02, 1.0), velocity=(self.vx, self.vy),
+                    offset=(float(self.off[0]), float(self.off[1])),
+                    rotation=(self.rot_a, self.rot_p, self.rot_ph), zoom=(0.1, self.zoom_p, self.zoom_ph),
+                    rects=rects)
+
     def _theta(self, t: torch.Tensor) -> torch.Tensor:
         k = 2 * math.pi / self.rot_p
         return self.rot_a / k * (math.cos(self.rot_ph) - torch.cos(k * t + self.rot_ph))

@@ -59,7 +59,7 @@ def test_struct_layout_matches_header(built):
     """Offsets of every field of the public structs, C compiler vs ctypes."""
     from paper_2602_15018_gb300 import _lib
     structs = {"neurosim_evsim_params": _lib.Params, "neurosim_evsim_stats": _lib.Stats,
-               "neurosim_evsim_batch_params": _lib.BatchParams}
+               "neurosim_evsim_batch_params": _lib.BatchParams, "neurosim_texture_scene": _lib.TextureScene}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "neurosim_evsim.h"',
              "int main(void) {"]
     for cname, py in structs.items():

@@ -143,6 +143,49 @@ def test_texture_odd_sizes(W, H, ppt, pf):
     g.close()
 
 
+@pytest.mark.parametrize("ppt,win", [(16, 2), (16, 3), (8, 3)])
+def test_exact_paths_crowded_tiles_and_many_events(ppt, win):
+    """Log-domain frames built to reach every path of the emission kernel:
+    quiet tiles, pairs of frames with a few pixels out of their band (one
+    pass of the exact path), pixels with many events in one frame (keys
+    regenerated from the saved state), frames where most pixels of a tile
+    leave their band (more listed pixels than lanes: the general path), a
+    pixel leaving its band again soon after its first events, and a
+    continuing step whose first interval starts from the stored state."""
+    W, H, T = 512, 4, 23
+    rng = np.random.default_rng(ppt * 10 + win)
+    base = rng.uniform(-3.0, 0.0, (H, W))
+    fr = np.repeat(base[None], T, axis=0).astype(np.float64)
+    # row 0: quiet.  row 1: a few pixels drift slowly (single events, retriggers)
+    drift = rng.choice(W, 24, replace=False)
+    fr[:, 1, drift] += np.arange(T)[:, None] * rng.uniform(0.05, 0.3, 24)
+    # row 2: steps of +-3 (about 15 events in one frame) at random frames
+    jump = rng.choice(W, 12, replace=False)
+    at = rng.integers(1, T, 12)
+    for x, f in zip(jump, at):
+        fr[f:, 2, x] += rng.choice([-3.0, 3.0])
+    # row 3: every pixel moves at frames 6..9 (crowded windows)
+    fr[6:10, 3, :] += rng.uniform(-0.6, 0.6, (4, W)).cumsum(axis=0)
+    fr = fr.astype(np.float32)
+    kw = dict(c_pos=0.2, c_neg=0.2, sigma_c=0.02, refractory_us=30, seed=9, input_is_log=True,
+              max_frames_per_step=T, pixels_per_thread=ppt, prefetch_frames=win)
+    g, o = _sims(W, H, **kw)
+    g.step(torch.from_numpy(fr).cuda(), 0, DT)
+    ev, seg = g.drain()
+    rev, rseg = o.step(fr, 0, DT)
+    assert_same(ev, seg, rev, rseg, "crowded tiles")
+    assert len(rev) > 1000
+    _check_state(g, o)
+    # a second, continuing step (the first interval's L_a comes from the state)
+    fr2 = (fr[::-1] + np.float32(0.05)).copy()
+    g.step(torch.from_numpy(fr2).cuda(), T * DT + 700, DT)
+    ev, seg = g.drain()
+    rev, rseg = o.step(fr2, T * DT + 700, DT)
+    assert_same(ev, seg, rev, rseg, "crowded tiles, continuing step")
+    _check_state(g, o)
+    g.close()
+
+
 def test_threshold_maps_match_oracle():
     W, H = 300, 200
     from paper_2602_15018_gb300 import EventSim
