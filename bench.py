@@ -24,6 +24,7 @@ ranks of the timed region use torch.distributed only for timing).
 from __future__ import annotations
 
 import argparse
+import ctypes as C
 import datetime as _dt
 import hashlib
 import json
@@ -97,6 +98,10 @@ WORKLOADS = {
                                  "250 FPS, U-Net predicts 3 log frames per interval, one batched event step of 4 "
                                  "frames per interval; texture scenes up to 600 px/s, C+0.2 C-0.25 sigma0.03 "
                                  "refractory 100us"),
+    "hd_fused": dict(dims=HD, sim=CONFIG2_SIM, render=None,
+                     name="render-fused HD: 1280x720, 2000 frames @1000 FPS per step of the library's texture scene "
+                          "(4-octave value noise, affine camera, 16 occluders) rendered inside the emission kernel; "
+                          "C+0.2 C-0.25 sigma0.03 refractory 100us"),
     "batch": dict(dims=None, sim=None, render=None,
                   name="batched: 256 sensors (346x260 / 640x480 / 1280x720 by index mod 3), "
                        "125 frames @1000 FPS per step (500-frame clips in 4 steps), texture scenes, C+- ~ U[0.15,0.35], "
@@ -375,6 +380,209 @@ def run_ours(args):
         }
         print(json.dumps(line), flush=True)
     sim.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+# Algorithmic operations of one rendered pixel-frame (scene_render.cuh): the
+# camera map (4 FMA) and 4 octaves of 81 operations each (coordinates 2,
+# floor 2, fractions 2, smoothsteps 6, conversions 2, four lattice hashes of
+# 14 integer and conversion operations, interpolation 7, octave updates 4),
+# the normalisation (2) and the emission filter's two compares.
+RENDER_OPS_PER_PX_FRAME = 4 + 4 * 81 + 2 + 2
+
+
+def alu_peak_tops() -> float:
+    """One thread instruction per lane per cycle: SMs x 4 schedulers x 32 lanes
+    x the maximum SM clock (Tops/s)."""
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    mhz = 2070.0
+    try:
+        mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return p.multi_processor_count * 128 * mhz * 1e6 / 1e12
+
+
+def fused_cpu_baseline(gen, n_frames: int = 12):
+    """Render + simulate on the host, for a bounded sample: the seeded scene
+    generator on the CPU (float64 torch, all host threads) for the first
+    frames, then the oracle band-parallel on all host cores."""
+    import oracle
+    W, H = gen.W, gen.H
+    t0 = time.perf_counter()
+    fr = scenes.render_frames(gen, n_frames, device="cpu").numpy()
+    t_render = time.perf_counter() - t0
+    cp, cn = oracle.threshold_maps(W, H, 0.2, 0.25, 0.03, 0.01, CONFIG2_SIM["seed"])
+    t0 = time.perf_counter()
+    ev, _, used, _ = oracle.banded_step(fr, W, H, 0, DT, cp, cn, refractory_us=100, threads=host_cores())
+    t_sim = time.perf_counter() - t0
+    px = n_frames * W * H
+    return {"value": round(px / (t_render + t_sim) / 1e6, 2), "unit": "Mpixel-frames/s", "cores": used,
+            "kind": "oracle",
+            "sample": f"first {n_frames} frames: the scene generator on the host ({t_render:.1f} s, torch float64, "
+                      f"{torch.get_num_threads()} threads) then the C oracle on {used} row bands ({t_sim:.1f} s, "
+                      f"{len(ev)} events)"}
+
+
+def run_fused(args):
+    """Render-fused HD steps: the emission kernel renders the library's texture
+    scene itself (no frame bytes through HBM).  Timed beside the unfused path
+    on the same scene and times: the stand-alone renderer writing the frames
+    to HBM, then the plain step reading them."""
+    from paper_2602_15018_gb300 import EventSim, render_texture, texture_scene
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    W, H, T = HD["W"], HD["H"], args.frames or HD["T"]
+    npix = W * H
+    span = T * DT
+    gen = scenes.TextureScene(W, H, seed=args.seed + rank)
+    ts = texture_scene(**gen.params())
+    sim = EventSim(W, H, **CONFIG2_SIM, max_frames_per_step=T)
+    out = torch.empty(npix * T // 8, dtype=torch.int64, device=dev)
+
+    def drain(s):
+        nonlocal out
+        n, _ = s.pending()
+        if n > out.numel():
+            out = torch.empty(int(n * 1.25), dtype=torch.int64, device=dev)
+        ev, _ = s.drain(to="cuda", out=out)
+        return int(ev.numel())
+
+    k = 0
+    for j in range(args.warmup):
+        sim.step_texture(ts, T, k * span, DT)
+        if (j + 1) % 4 == 0 or j + 1 == args.warmup:
+            drain(sim)
+        k += 1
+    sim.set_profiling(True)
+    st0 = sim.stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tw0 = time.time()
+    e0.record(sim.stream)
+    n_events = 0
+    for j in range(args.steps):
+        sim.step_texture(ts, T, k * span, DT)
+        if (j + 1) % 4 == 0 or j + 1 == args.steps:
+            n_events += drain(sim)
+        k += 1
+    e1.record(sim.stream)
+    torch.cuda.synchronize()
+    tw1 = time.time()
+    if dist:
+        dist.barrier()
+    clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st1 = sim.stats()
+    ms, n_events_all = combine_ranks(dist, dev, ms, n_events)
+    timed = st1["timed_steps"] - st0["timed_steps"]
+    emit_ms = (st1["emit_ms"] - st0["emit_ms"]) / max(1, timed)
+    sort_ms = (st1["sort_ms"] - st0["sort_ms"]) / max(1, timed)
+    launches = int(st1["kernel_launches"] - st0["kernel_launches"])
+    sim.close()
+
+    # unfused: the renderer writes the frames to HBM, the plain step reads them
+    frames = torch.empty((T, H, W), dtype=torch.float32, device=dev)
+    simu = EventSim(W, H, **CONFIG2_SIM, max_frames_per_step=T)
+    cur = torch.cuda.current_stream()
+    n_u = max(1, min(args.steps, 4))
+    ku = 0
+    for _ in range(2):
+        render_texture(ts, T, ku * span, DT, out=frames)
+        simu.step(frames, ku * span, DT)
+        drain(simu)
+        ku += 1
+    torch.cuda.synchronize()
+    rt, stp = 0.0, 0.0
+    for _ in range(n_u):
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(cur)
+        render_texture(ts, T, ku * span, DT, out=frames)
+        b.record(cur)
+        simu.step(frames, ku * span, DT)
+        drain(simu)
+        c.record(cur)
+        torch.cuda.synchronize()
+        rt += a.elapsed_time(b)
+        stp += b.elapsed_time(c)
+        ku += 1
+    simu.close()
+    del frames
+    torch.cuda.empty_cache()
+
+    # end to end through the C ABI: the scene (host struct) in, the events out
+    # to pinned host memory, every step
+    e2e = None
+    if args.e2e_steps > 0:
+        sim2 = EventSim(W, H, **CONFIG2_SIM, max_frames_per_step=T)
+        host_out = torch.empty(max(1 << 20, int(n_events / max(1, args.steps) * 1.5)), dtype=torch.int64).pin_memory()
+        d2h, k2 = 0, 0
+
+        def e2e_step():
+            nonlocal host_out, k2
+            sim2.step_texture(ts, T, k2 * span, DT)
+            k2 += 1
+            n, _ = sim2.pending()
+            if n > host_out.numel():
+                host_out = torch.empty(int(n * 1.25), dtype=torch.int64).pin_memory()
+            ev, _ = sim2.drain(to="cpu", out=host_out)
+            return ev.numel() * 8
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            d2h += e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms, _ = combine_ranks(dist, dev, (time.perf_counter() - t0) * 1e3)
+        e2e = {"value": round(job_value(T * npix * args.e2e_steps, ws, e2e_ms), 1), "unit": "Mpixel-frames/s",
+               "h2d_bytes_per_step": C.sizeof(ts), "d2h_bytes_per_step": int(d2h / args.e2e_steps)}
+        sim2.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = fused_cpu_baseline(gen)
+
+    px = T * npix
+    peak = alu_peak_tops()
+    achieved = RENDER_OPS_PER_PX_FRAME * px / (emit_ms / 1e3) / 1e12
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(job_value(px * args.steps, ws, ms), 1), "unit": "Mpixel-frames/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (the library's seeded texture scene, rendered inside the emission kernel)",
+            "config": {"workload": WORKLOADS["hd_fused"]["name"], "width": W, "height": H, "frames_per_step": T,
+                       "dt_us": DT, "streams_per_gpu": 1,
+                       "parallelism": f"replicas x{ws} (independent sensor streams)",
+                       "l2": "no frames in memory; event buffers only"},
+            "events_per_s": round(n_events_all / (ms / 1e3), 1),
+            "events_per_step": round(n_events / max(1, args.steps), 1),
+            "gpu_launches": launches,
+            "kernel_ms": {"emit_fused": round(emit_ms, 4), "sort": round(sort_ms, 4)},
+            "unfused": {"render_ms": round(rt / n_u, 4), "step_ms": round(stp / n_u, 4),
+                        "value": round(px / ((rt + stp) / n_u / 1e3) / 1e6, 1), "unit": "Mpixel-frames/s",
+                        "frame_bytes_per_step": 4 * px},
+            "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
+                         "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "kernel": "emit_kernel (render-fused)",
+                         "ops_per_px_frame": RENDER_OPS_PER_PX_FRAME,
+                         "peak_source": "SMs x 128 lanes x max SM clock"},
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks.summary(tw0, tw1),
+        }
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
@@ -1040,11 +1248,13 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
-        if args.workload in ("batch", "learned", "batched_learned"):
+        if args.workload in ("batch", "learned", "batched_learned", "hd_fused"):
             ap.error("the reference arm runs the plain workloads only")
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "hd_fused":
+        run_fused(args)
     elif args.workload == "learned":
         run_learned(args)
     elif args.workload == "batched_learned":
