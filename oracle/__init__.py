@@ -11,6 +11,9 @@ Functions (each follows the passage and reading named in the C source):
   mylog                 project FP32 log (reading R1)
   lowpass_alpha         per-frame gain of the bandwidth filter (reading R13)
   lowpass_log           sensor bandwidth filter on log frames (reading R13)
+  leak_log              sensor leak as the drift of the log input (reading R14)
+  shot_noise            shot-noise events per tile and interval (reading R15)
+  merge_events          two event streams merged per interval (reading R8)
   splitmix64_at         SplitMix64 output i of a seeded stream (reading R6)
   normal_ih12           Irwin-Hall(12) normal draw (reading R6)
   threshold_maps        per-pixel thresholds max(c_min, C + sigma z) (R6)
@@ -67,6 +70,14 @@ def _configure(L):
     L.oracle_mylog.argtypes = [C.c_float]
     L.oracle_lowpass_log.restype = C.c_int
     L.oracle_lowpass_log.argtypes = [f32p, f32p, C.c_int32, C.c_int64, C.c_float, f32p, C.c_int32]
+    L.oracle_leak_log.restype = C.c_int
+    L.oracle_leak_log.argtypes = [f32p, f32p, C.c_int32, C.c_int64, C.c_int64, C.c_int32, C.c_int64,
+                                  C.c_double, f32p, C.c_float]
+    L.oracle_shot_noise.restype = C.c_int
+    L.oracle_shot_noise.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_uint64, C.c_int64, C.c_int32,
+                                    C.c_int32, C.c_int32, u64pp, i64p, i64pp]
+    L.oracle_merge_events.restype = C.c_int
+    L.oracle_merge_events.argtypes = [u64p, i64p, u64p, i64p, C.c_int32, u64p, i64p]
     L.oracle_lowpass_alpha.restype = C.c_float
     L.oracle_lowpass_alpha.argtypes = [C.c_double, C.c_int32]
     L.oracle_mylog_batch.restype = None
@@ -146,6 +157,60 @@ def lowpass_alpha(cutoff_hz, dt_us, library=None) -> np.float32:
     if not a > 0:
         raise OracleError("invalid cutoff or frame spacing")
     return a
+
+
+def leak_log(L, t0_us, dt_us, origin_us, rate_hz, cpos=None, cpos_u=0.2, library=None):
+    """Sensor leak (reading R14) on log frames L [T, ...] at t0 + k dt: the log
+    input rises by C+ * rate * (t - origin); cpos: per-pixel ON thresholds."""
+    x = np.ascontiguousarray(L, dtype=np.float32)
+    T = x.shape[0]
+    n = int(x[0].size) if T else 0
+    out = np.empty_like(x)
+    cp = None if cpos is None else np.ascontiguousarray(cpos, np.float32).reshape(-1)
+    rc = (library or lib()).oracle_leak_log(_p(x, C.c_float), _p(out, C.c_float), T, n, int(t0_us), int(dt_us),
+                                            int(origin_us), float(rate_hz),
+                                            None if cp is None else _p(cp, C.c_float), float(cpos_u))
+    if rc != 0:
+        raise OracleError(_ERR.get(rc, f"error {rc}"))
+    return out
+
+
+def shot_noise(width, height, rate_hz, seed, ta0_us, D0_us, dt_us, n_intervals, library=None):
+    """Shot-noise events (reading R15) of n_intervals intervals (the first
+    D0_us long from ta0_us, then dt_us each): (records uint64, offsets int64)."""
+    L = library or lib()
+    evp = C.POINTER(C.c_uint64)()
+    segp = C.POINTER(C.c_int64)()
+    n = C.c_int64(0)
+    rc = L.oracle_shot_noise(int(width), int(height), float(rate_hz), int(seed), int(ta0_us), int(D0_us),
+                             int(dt_us), int(n_intervals), C.byref(evp), C.byref(n), C.byref(segp))
+    if rc != 0:
+        raise OracleError(_ERR.get(rc, f"error {rc}"))
+    try:
+        ev = np.ctypeslib.as_array(evp, shape=(n.value,)).copy() if n.value else np.zeros(0, np.uint64)
+        seg = np.ctypeslib.as_array(segp, shape=(int(n_intervals) + 1,)).copy()
+    finally:
+        L.oracle_free(C.cast(evp, C.c_void_p))
+        L.oracle_free(C.cast(segp, C.c_void_p))
+    return ev, seg
+
+
+def merge_events(a, seg_a, b, seg_b, library=None):
+    """Two interval-structured streams merged per interval in record order (R8)."""
+    a = np.ascontiguousarray(a, np.uint64)
+    b = np.ascontiguousarray(b, np.uint64)
+    sa = np.ascontiguousarray(seg_a, np.int64)
+    sb = np.ascontiguousarray(seg_b, np.int64)
+    if len(sa) != len(sb):
+        raise OracleError("streams have different interval counts")
+    out = np.empty(a.size + b.size, np.uint64)
+    so = np.empty(len(sa), np.int64)
+    rc = (library or lib()).oracle_merge_events(_p(a, C.c_uint64), _p(sa, C.c_int64), _p(b, C.c_uint64),
+                                                _p(sb, C.c_int64), len(sa) - 1, _p(out, C.c_uint64),
+                                                _p(so, C.c_int64))
+    if rc != 0:
+        raise OracleError(_ERR.get(rc, f"error {rc}"))
+    return out, so
 
 
 def mylog(x, library=None) -> np.ndarray:

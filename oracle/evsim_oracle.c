@@ -55,6 +55,29 @@
  *       once to FP32: oracle_lowpass_alpha); the filter starts at the first
  *       frame's value.  FP32: d = L - s rounded, then s = fma(alpha, d, s)
  *       with one rounding (oracle_lowpass_log below).
+ *   R14 Sensor leak (Sec. 2 lists noise among the modelled non-idealities,
+ *       with no model; junction leakage makes a pixel's reference level
+ *       drift): the reference drifts down at C+_u * r per second, which for
+ *       the crossing test L - ref is the same as the log intensity rising by
+ *       delta(t) = C+_u * r * (t - origin).  Applied to log frames before the
+ *       event model: L' = L + delta(t_k), FP32 as
+ *       fl(L + fl(fl(C+_u * fl(r * 1e-6)) * (float)(t_k - origin))), with
+ *       t in microseconds (oracle_leak_log below).  A still pixel then fires
+ *       ON events r times a second.
+ *   R15 Shot noise (same paragraph): spurious events independent of the
+ *       signal and of the pixel state.  For every tile of 64 consecutive
+ *       pixels (row-major; the last may be shorter, `len` pixels) and every
+ *       interval (start ta, length D us), the count is Poisson with mean
+ *       lambda = r * len * D * 1e-6, drawn by inversion: with the 53-bit
+ *       uniform U of SplitMix64 output ((ta * n_tiles + tile) * 32) of the
+ *       noise seed, the count is the least n with U < floor(F(n) * 2^53),
+ *       F the Poisson CDF accumulated in double from exp(-lambda), at most
+ *       15 (the mean is kept at most 4, where more than 15 has probability
+ *       below 1e-6).  Event i uses outputs base + 1 + 2i (pixel tile * 64 +
+ *       floor(hi32 * len / 2^32), time ta + floor(lo32 * D / 2^32)) and
+ *       base + 2 + 2i (polarity: its top bit).  Merged into a stream
+ *       interval by interval in the order of R8 (oracle_shot_noise,
+ *       oracle_merge_events).
  *
  * Packed record (64 bits): [63:32] t (us) | [31:17] y | [16:1] x | [0] p.
  *
@@ -502,6 +525,129 @@ float oracle_lowpass_alpha(double cutoff_hz, int32_t dt_us)
     if (!(cutoff_hz > 0.0) || !isfinite(cutoff_hz) || dt_us < 1) return 0.0f;
     const double keep = exp(-two_pi * cutoff_hz * ((double)dt_us * 1e-6));
     return (float)(1.0 - keep);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sensor leak (reading R14).  L, out: [T][n] FP32 log frames at t0 + k dt  */
+/* (out may be L); cpos: per-pixel ON thresholds [n] or NULL for cpos_u.    */
+/* ------------------------------------------------------------------------ */
+int oracle_leak_log(const float *L, float *out, int32_t T, int64_t n, int64_t t0_us, int32_t dt_us,
+                    int64_t origin_us, double rate_hz, const float *cpos, float cpos_u)
+{
+    if (T < 0 || n < 0 || dt_us < 1 || !(rate_hz >= 0.0) || t0_us < origin_us) return ORACLE_E_INVALID;
+    const float rate_us = (float)(rate_hz * 1e-6);
+    for (int64_t i = 0; i < n; ++i) {
+        const float k = (cpos ? cpos[i] : cpos_u) * rate_us;
+        for (int32_t f = 0; f < T; ++f) {
+            const float s = (float)(t0_us + (int64_t)f * dt_us - origin_us);
+            const float delta = k * s;
+            out[(int64_t)f * n + i] = L[(int64_t)f * n + i] + delta;
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Shot noise (reading R15).                                                */
+/* ------------------------------------------------------------------------ */
+#define SHOT_TILE 64
+#define SHOT_MAX 15
+
+/* thr[n] = floor(F(n) 2^53) for the Poisson CDF F of mean lam, n < SHOT_MAX */
+static void poisson_thresholds(double lam, uint64_t thr[SHOT_MAX])
+{
+    double p = exp(-lam), F = p;
+    for (int k = 0; k < SHOT_MAX; ++k) {
+        double v = F * 9007199254740992.0;   /* 2^53 */
+        thr[k] = v >= 9007199254740992.0 ? (uint64_t)1 << 53 : (uint64_t)v;
+        p = p * lam / (double)(k + 1);
+        F += p;
+    }
+}
+
+int oracle_shot_noise(int32_t W, int32_t H, double rate_hz, uint64_t seed, int64_t ta0_us, int32_t D0_us,
+                      int32_t dt_us, int32_t n_intervals, uint64_t **events_out, int64_t *n_events,
+                      int64_t **seg_out)
+{
+    if (W <= 0 || H <= 0 || W > 65535 || H > 32767 || n_intervals < 0 || !(rate_hz >= 0.0) || D0_us < 1 ||
+        dt_us < 1 || ta0_us < 0)
+        return ORACLE_E_INVALID;
+    if (rate_hz * SHOT_TILE * (double)(D0_us > dt_us ? D0_us : dt_us) * 1e-6 > 4.0) return ORACLE_E_INVALID;
+    const int64_t npix = (int64_t)W * H;
+    const int64_t n_tiles = (npix + SHOT_TILE - 1) / SHOT_TILE;
+    int64_t cap = 1024, n = 0;
+    uint64_t *ev = (uint64_t *)malloc((size_t)cap * sizeof(uint64_t));
+    int64_t *seg = (int64_t *)malloc((size_t)(n_intervals + 1) * sizeof(int64_t));
+    if (!ev || !seg) {
+        free(ev);
+        free(seg);
+        return ORACLE_E_NOMEM;
+    }
+    seg[0] = 0;
+    for (int32_t j = 0; j < n_intervals; ++j) {
+        const int64_t ta = j == 0 ? ta0_us : ta0_us + D0_us + (int64_t)(j - 1) * dt_us;
+        const int32_t D = j == 0 ? D0_us : dt_us;
+        if (ta + D > 0xFFFFFFFFll) {
+            free(ev);
+            free(seg);
+            return ORACLE_E_TIME;
+        }
+        const int64_t start = n;
+        for (int64_t tile = 0; tile < n_tiles; ++tile) {
+            const int64_t len = (tile + 1) * SHOT_TILE <= npix ? SHOT_TILE : npix - tile * SHOT_TILE;
+            uint64_t thr[SHOT_MAX];
+            poisson_thresholds(rate_hz * (double)len * (double)D * 1e-6, thr);
+            const uint64_t base = ((uint64_t)ta * (uint64_t)n_tiles + (uint64_t)tile) * 32u;
+            const uint64_t U = oracle_splitmix64_at(seed, base) >> 11;
+            int count = SHOT_MAX;
+            for (int k = 0; k < SHOT_MAX; ++k)
+                if (U < thr[k]) {
+                    count = k;
+                    break;
+                }
+            for (int i = 0; i < count; ++i) {
+                const uint64_t d1 = oracle_splitmix64_at(seed, base + 1u + 2u * (uint64_t)i);
+                const uint64_t d2 = oracle_splitmix64_at(seed, base + 2u + 2u * (uint64_t)i);
+                const int64_t pix = tile * SHOT_TILE + (int64_t)(((d1 >> 32) * (uint64_t)len) >> 32);
+                const int64_t t = ta + (int64_t)(((d1 & 0xFFFFFFFFull) * (uint64_t)D) >> 32);
+                if (n == cap) {
+                    cap *= 2;
+                    uint64_t *q = (uint64_t *)realloc(ev, (size_t)cap * sizeof(uint64_t));
+                    if (!q) {
+                        free(ev);
+                        free(seg);
+                        return ORACLE_E_NOMEM;
+                    }
+                    ev = q;
+                }
+                ev[n++] = pack(t, (int32_t)(pix % W), (int32_t)(pix / W), (int)(d2 >> 63));
+            }
+        }
+        qsort(ev + start, (size_t)(n - start), sizeof(uint64_t), cmp_u64);
+        seg[j + 1] = n;
+    }
+    *events_out = ev;
+    *n_events = n;
+    *seg_out = seg;
+    return ORACLE_OK;
+}
+
+/* Two interval-structured streams (seg_a, seg_b: n_intervals + 1 offsets)  */
+/* merged interval by interval in record order (R8); out holds both.        */
+int oracle_merge_events(const uint64_t *a, const int64_t *seg_a, const uint64_t *b, const int64_t *seg_b,
+                        int32_t n_intervals, uint64_t *out, int64_t *seg_out)
+{
+    if (n_intervals < 0) return ORACLE_E_INVALID;
+    int64_t o = 0;
+    seg_out[0] = 0;
+    for (int32_t j = 0; j < n_intervals; ++j) {
+        const int64_t start = o;
+        for (int64_t i = seg_a[j]; i < seg_a[j + 1]; ++i) out[o++] = a[i];
+        for (int64_t i = seg_b[j]; i < seg_b[j + 1]; ++i) out[o++] = b[i];
+        qsort(out + start, (size_t)(o - start), sizeof(uint64_t), cmp_u64);
+        seg_out[j + 1] = o;
+    }
+    return ORACLE_OK;
 }
 
 void oracle_free(void *p) { free(p); }

@@ -335,5 +335,103 @@ def pin_lowpass_alpha(library):
         raise AssertionError(f"lowpass_alpha{bad} accepted")
 
 
+def pin_leak(library):
+    """Sensor leak (reading R14): the log input rises by C+ r (t - origin).
+
+    Closed form: a still pixel with C+ = 0.2 and r = 40 Hz fires ON events
+    every 1/r = 25 ms (40 in 1 s), all ON, at k * 25000 us within the model's
+    rounding; the event rate does not depend on the pixel's threshold (the
+    drift scales with C+); r = 0 changes nothing; frames starting later than
+    the origin are the matching frames of a run from the origin."""
+    T, n = 1001, 3
+    L = np.full((T, 1, n), -1.0, np.float32)
+    assert np.array_equal(oracle.leak_log(L, 0, DT, 0, 0.0, cpos_u=0.2, library=library), L)
+    cp = np.array([0.2, 0.4, 0.1], np.float32)
+    out = oracle.leak_log(L, 0, DT, 0, 40.0, cpos=cp, library=library)
+    assert abs(out[-1, 0, 0] - 7.0) < 1e-5 and abs(out[-1, 0, 1] - 15.0) < 1e-5 and abs(out[500, 0, 2] - 1.0) < 1e-5
+    sim = oracle.OracleSim(n, 1, c_pos_map=cp, c_neg_map=cp, input_is_log=True, library=library)
+    ev, _ = sim.step(out, 0, DT)
+    t, x, _, p = oracle.unpack(ev)
+    assert np.all(p == 1)
+    for u in range(n):
+        tu = np.sort(t[x == u]).astype(np.int64)
+        assert len(tu) in (39, 40), (u, len(tu))
+        k = np.arange(1, len(tu) + 1)
+        assert np.all(np.abs(tu - k * 25000) <= 2), (u, np.abs(tu - k * 25000).max())
+    tail = oracle.leak_log(L[:400], 600 * DT, DT, 0, 40.0, cpos=cp, library=library)
+    full = oracle.leak_log(np.full((1000, 1, n), -1.0, np.float32), 0, DT, 0, 40.0, cpos=cp, library=library)
+    assert np.array_equal(tail, full[600:1000])
+
+
+def pin_shot_noise(library):
+    """Shot noise (reading R15), against Poisson statistics and its structure:
+    the count matches the mean rate * pixels * time (4 sigma), counts per
+    tile-interval have variance equal to their mean (Poisson), times are
+    uniform in their interval and independent of the pixel, pixels uniform
+    (also in a ragged last tile), polarities balanced, every interval sorted;
+    an interval's events depend only on its start time (not on how many
+    intervals are drawn); zero rate gives nothing; other seeds other events."""
+    W, H, r, n_int = 37, 83, 40.0, 500          # 3071 px: 47 full tiles and one of 63
+    ev, seg = oracle.shot_noise(W, H, r, 5, 0, 700, DT, n_int, library=library)
+    npix = W * H
+    expect = r * npix * (700 + (n_int - 1) * DT) * 1e-6
+    assert abs(len(ev) - expect) < 4 * np.sqrt(expect), (len(ev), expect)
+    t, x, y, p = oracle.unpack(ev)
+    pix = y.astype(np.int64) * W + x
+    assert np.all((x < W) & (y < H))
+    j = np.repeat(np.arange(n_int), np.diff(seg))
+    ta = np.where(j == 0, 0, 700 + (j - 1) * DT)
+    D = np.where(j == 0, 700, DT)
+    off = t.astype(np.int64) - ta
+    assert np.all((off >= 0) & (off < D))
+    assert abs(np.mean(off[j > 0]) / DT - 0.5) < 0.01
+    assert abs(np.mean(p) - 0.5) < 0.01
+    for jj in range(n_int):
+        e = ev[seg[jj]:seg[jj + 1]]
+        assert np.all(e[1:] >= e[:-1])
+    tile = pix // 64
+    counts = np.bincount((j[j > 0] - 1) * 48 + tile[j > 0], minlength=(n_int - 1) * 48).reshape(n_int - 1, 48)[:, :47]
+    m, v = counts.mean(), counts.var()
+    assert abs(v / m - 1.0) < 0.05, (m, v)
+    per_px = np.bincount(pix, minlength=npix)
+    last = per_px[47 * 64:].mean() / per_px[: 47 * 64].mean()
+    assert abs(last - 1.0) < 0.1, last
+    inner = (pix % 64)[j > 0] / 64.0
+    rho = np.corrcoef(inner, off[j > 0] / DT)[0, 1]
+    assert abs(rho) < 0.03, rho
+    hist = np.bincount(pix % 64, minlength=64)
+    assert hist.min() > 0.8 * hist.mean() and hist.max() < 1.2 * hist.mean()
+    e5, s5 = oracle.shot_noise(W, H, r, 5, 0, 700, DT, 5, library=library)
+    assert np.array_equal(e5, ev[: seg[5]]) and np.array_equal(s5, seg[:6])
+    e_shift, s_shift = oracle.shot_noise(W, H, r, 5, 700 + 4 * DT, DT, DT, 3, library=library)
+    assert np.array_equal(e_shift, ev[seg[5]:seg[8]])
+    z, zs = oracle.shot_noise(W, H, 0.0, 5, 0, 700, DT, 10, library=library)
+    assert len(z) == 0 and np.all(zs == 0)
+    o, _ = oracle.shot_noise(W, H, r, 6, 0, 700, DT, 5, library=library)
+    assert not np.array_equal(o[: min(len(o), len(e5))], e5[: min(len(o), len(e5))])
+    try:
+        oracle.shot_noise(W, H, 100.0, 5, 0, DT, DT, 2, library=library)   # mean 6.4 per tile: refused
+    except oracle.OracleError:
+        pass
+    else:
+        raise AssertionError("a tile mean above 4 was accepted")
+
+
+def pin_merge(library):
+    """Merging interval-structured streams: a permutation of their union,
+    sorted per interval; merging with an empty stream changes nothing."""
+    a, sa = oracle.shot_noise(40, 30, 20.0, 1, 0, DT, DT, 30, library=library)
+    b, sb = oracle.shot_noise(40, 30, 20.0, 2, 0, DT, DT, 30, library=library)
+    m, sm = oracle.merge_events(a, sa, b, sb, library=library)
+    assert np.array_equal(sm, sa + sb)
+    for j in range(30):
+        seg = m[sm[j]:sm[j + 1]]
+        assert np.all(seg[1:] >= seg[:-1])
+        assert np.array_equal(np.sort(seg), np.sort(np.concatenate([a[sa[j]:sa[j + 1]], b[sb[j]:sb[j + 1]]])))
+    e, se = oracle.merge_events(a, sa, np.zeros(0, np.uint64), np.zeros(31, np.int64), library=library)
+    assert np.array_equal(e, a) and np.array_equal(se, sa)
+
+
 ALL_PINS = [pin_ramps, pin_uneven_interval, pin_constant_and_first_frame, pin_refractory, pin_brute_force,
-            pin_threshold_maps, pin_band_and_order, pin_fp64_agreement, pin_step_composition, pin_lowpass]
+            pin_threshold_maps, pin_band_and_order, pin_fp64_agreement, pin_step_composition, pin_lowpass,
+            pin_leak, pin_shot_noise, pin_merge]

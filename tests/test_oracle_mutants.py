@@ -47,6 +47,13 @@ MUTANTS = [
     ("lowpass_starts_at_zero", "float s = init ? L[i] : state[i];", "float s = init ? 0.0f : state[i];"),
     ("lowpass_state_not_saved", "        state[i] = s;\n    }\n    return ORACLE_OK;", "    }\n    return ORACLE_OK;"),
     ("lowpass_gain_squared", "s = fmaf(alpha, d, s);", "s = fmaf(alpha * alpha, d, s);"),
+    ("leak_sign", "out[(int64_t)f * n + i] = L[(int64_t)f * n + i] + delta;",
+     "out[(int64_t)f * n + i] = L[(int64_t)f * n + i] - delta;"),
+    ("leak_without_threshold", "const float k = (cpos ? cpos[i] : cpos_u) * rate_us;", "const float k = rate_us;"),
+    ("shot_always_on", "(int)(d2 >> 63));", "1);"),
+    ("shot_time_from_pixel_bits", "((d1 & 0xFFFFFFFFull) * (uint64_t)D) >> 32", "((d1 >> 32) * (uint64_t)D) >> 32"),
+    ("shot_rate_without_pixels", "rate_hz * (double)len * (double)D * 1e-6", "rate_hz * 64.0 * (double)D * 1e-6 * 0.5"),
+    ("shot_ragged_tile_full", "npix - tile * SHOT_TILE;", "SHOT_TILE;"),
     ("lowpass_alpha_no_two_pi", "exp(-two_pi * cutoff_hz", "exp(-cutoff_hz"),
     ("lowpass_alpha_kept_fraction", "return (float)(1.0 - keep);", "return (float)keep;"),
     ("lowpass_alpha_dt_in_ms", "((double)dt_us * 1e-6)", "((double)dt_us * 1e-3)"),

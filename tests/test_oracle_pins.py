@@ -113,3 +113,15 @@ def test_banded_oracle_equals_one_sensor(L):
         assert np.array_equal(bseg, seg) and np.array_equal(bev, ev), threads
         for k in ("ref", "lprev", "tlast"):
             assert np.array_equal(st[k], getattr(one, k)), (threads, k)
+
+
+def test_leak_closed_form(L):
+    P.pin_leak(L)
+
+
+def test_shot_noise_statistics(L):
+    P.pin_shot_noise(L)
+
+
+def test_merge_streams(L):
+    P.pin_merge(L)
