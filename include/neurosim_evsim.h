@@ -151,6 +151,28 @@ int neurosim_evsim_drain_events(neurosim_evsim *h, uint64_t *out, uint64_t out_c
                                 int32_t out_is_device, uint64_t *n_out, int64_t *seg_offsets,
                                 int64_t seg_capacity, int64_t *n_segs);
 
+/* Zero-copy access to the pending events (Sec. 3 of the paper hands sensor
+ * data to NumPy / PyTorch consumers without copies; this is the in-process
+ * counterpart).  peek resolves a capacity overflow like
+ * neurosim_evsim_pending (synchronises), then sets *events_dev to the
+ * library's DEVICE buffer holding the n_out pending records in output order,
+ * and fills seg_offsets (HOST, nullable, capacity seg_capacity) as drain
+ * does.  The records stay the library's: the pointer is valid until the next
+ * step, drain, release, set_state or destroy of the handle, and the events
+ * stay pending.  release then clears them (and commits the state, as a drain
+ * does) without copying anything. */
+int neurosim_evsim_peek_events(neurosim_evsim *h, const uint64_t **events_dev, uint64_t *n_out,
+                               int64_t *seg_offsets, int64_t seg_capacity, int64_t *n_segs);
+int neurosim_evsim_release_events(neurosim_evsim *h);
+
+/* As peek, returning the records as a DLPack tensor (a DLManagedTensor of the
+ * DLPack v0.8 ABI: 1-D, 64-bit integer holding the record bits, CUDA device
+ * memory of the handle's device, compact), for any DLPack consumer (torch.from_dlpack, CuPy, JAX).
+ * The view aliases the library's buffer with the same validity as peek; the
+ * consumer's call of the tensor's deleter frees the descriptor only.  Wrap
+ * *managed_tensor in a capsule named "dltensor" to hand it over. */
+int neurosim_evsim_events_dlpack(neurosim_evsim *h, void **managed_tensor);
+
 /* Copies the per-pixel state after the last enqueued step into HOST arrays
  * of height*width entries: ref (reference log level), lprev (log intensity of
  * the last frame), tlast (time of the last emitted event, 0xFFFFFFFF = none).
@@ -565,6 +587,52 @@ int neurosim_lowpass_log(const float *L_dev, float *out_dev, int32_t n_frames, i
  * dt_us >= 1 (microseconds).  NEUROSIM_E_INVALID for other arguments, a NULL
  * alpha_out, or a gain that rounds to 0.  Host only; no device work. */
 int neurosim_lowpass_alpha(double cutoff_hz, int32_t dt_us, float *alpha_out);
+
+/* Sensor leak (Sec. 2 of the paper lists noise among the non-idealities the
+ * simulator models and the user may turn off; it gives no model).  This
+ * library's reading: junction leakage makes each pixel's reference level
+ * drift down at C+_u * rate_hz per second, so that a still pixel fires ON
+ * events rate_hz times a second; for the crossing test this equals the log
+ * intensity rising by C+_u * rate_hz * (t - origin_us).  Applied to DEVICE
+ * log frames L_dev [n_frames][n_pix] at t0_us + f * dt_us (t0_us >=
+ * origin_us) into out_dev (= L_dev for in place, or not overlapping it), in
+ * FP32 as fl(L + fl(fl(C+_u * (float)(rate_hz * 1e-6)) * (float)(t -
+ * origin))); c_pos_dev: the sensor's per-pixel ON thresholds [n_pix]
+ * (neurosim_evsim_get_thresholds) or NULL for the uniform c_pos.  Feed the
+ * output to the event model with input_is_log = 1.  Long runs saturate at the
+ * model's clamp of 32 after (32 - L) / (C+ rate) seconds.  Asynchronous.
+ * NEUROSIM_E_INVALID / NEUROSIM_E_TIME for bad arguments. */
+int neurosim_leak_log(const float *L_dev, float *out_dev, int32_t n_frames, int64_t n_pix, int64_t t0_us,
+                      int32_t dt_us, int64_t origin_us, double rate_hz, const float *c_pos_dev, float c_pos,
+                      void *cuda_stream);
+
+/* Shot noise (same passage; this library's reading): spurious events,
+ * independent of the signal and of the pixel state.  For each tile of 64
+ * consecutive pixels (row-major; the last one may be shorter, len pixels)
+ * and each interval (start ta, length D us), the count is Poisson of mean
+ * rate_hz * len * D * 1e-6 (at most 4: NEUROSIM_E_INVALID above), drawn by
+ * inversion of the 53-bit uniform of SplitMix64 output
+ * (ta * n_tiles + tile) * 32 of `seed`, capped at 15; event i takes outputs
+ * base + 1 + 2i (pixel tile * 64 + floor(hi32 * len / 2^32), time
+ * ta + floor(lo32 * D / 2^32)) and base + 2 + 2i (polarity: its top bit).
+ * Intervals: the first from ta0_us, D0_us long, then n_intervals - 1 of
+ * dt_us (a step's intervals).  Writes the records (format of the event
+ * stream, interval-major, ascending per interval) to events_dev (DEVICE,
+ * capacity records) and n_intervals + 1 HOST offsets to seg_offsets;
+ * *n_events gets the count (also when it exceeds capacity:
+ * NEUROSIM_E_OVERFLOW).  At most 8192 events per interval.  Synchronises. */
+int neurosim_shot_noise(int32_t width, int32_t height, double rate_hz, uint64_t seed, int64_t ta0_us,
+                        int32_t D0_us, int32_t dt_us, int32_t n_intervals, uint64_t *events_dev,
+                        uint64_t capacity, int64_t *seg_offsets, uint64_t *n_events, void *cuda_stream);
+
+/* Merges two event streams with the same intervals (DEVICE records, HOST
+ * offsets seg_a / seg_b of n_intervals + 1 entries from 0), each ascending
+ * per interval, into out_dev (DEVICE, seg_a[n] + seg_b[n] records) in the
+ * stream's order, interval by interval; seg_out (HOST, nullable) gets the
+ * merged offsets.  E.g. a drained signal stream and its shot noise.
+ * Synchronises. */
+int neurosim_merge_events(const uint64_t *a_dev, const int64_t *seg_a, const uint64_t *b_dev, const int64_t *seg_b,
+                          int32_t n_intervals, uint64_t *out_dev, int64_t *seg_out, void *cuda_stream);
 
 /* Evaluates the library's FP32 log (the one the event model uses) on n DEVICE
  * floats x_dev into y_dev on cuda_stream; for verification of the log. */

@@ -37,6 +37,8 @@ EXPORTS = [
     "neurosim_event_f1", "neurosim_log_intensity", "neurosim_time_surface", "neurosim_event_frames",
     "neurosim_lowpass_log", "neurosim_lowpass_alpha", "neurosim_debug_expiring_wait",
     "neurosim_render_texture", "neurosim_evsim_step_texture",
+    "neurosim_evsim_peek_events", "neurosim_evsim_release_events", "neurosim_evsim_events_dlpack",
+    "neurosim_leak_log", "neurosim_shot_noise", "neurosim_merge_events",
 ]
 
 MAX_RECTS = 16
@@ -208,6 +210,19 @@ def lib():
             L.neurosim_event_frames.argtypes = [vp, i32, i32, vp, i64, i64, i64, i32, vp]
             L.neurosim_lowpass_log.restype = C.c_int
             L.neurosim_lowpass_log.argtypes = [vp, vp, i32, i64, C.c_float, vp, i32, vp]
+            L.neurosim_leak_log.restype = C.c_int
+            L.neurosim_leak_log.argtypes = [vp, vp, i32, i64, i64, i32, i64, C.c_double, vp, C.c_float, vp]
+            L.neurosim_shot_noise.restype = C.c_int
+            L.neurosim_shot_noise.argtypes = [i32, i32, C.c_double, u64, i64, i32, i32, i32, vp, u64, vp,
+                                              C.POINTER(u64), vp]
+            L.neurosim_merge_events.restype = C.c_int
+            L.neurosim_merge_events.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp]
+            L.neurosim_evsim_peek_events.restype = C.c_int
+            L.neurosim_evsim_peek_events.argtypes = [vp, C.POINTER(vp), C.POINTER(u64), vp, i64, C.POINTER(i64)]
+            L.neurosim_evsim_release_events.restype = C.c_int
+            L.neurosim_evsim_release_events.argtypes = [vp]
+            L.neurosim_evsim_events_dlpack.restype = C.c_int
+            L.neurosim_evsim_events_dlpack.argtypes = [vp, C.POINTER(vp)]
             L.neurosim_render_texture.restype = C.c_int
             L.neurosim_render_texture.argtypes = [C.POINTER(TextureScene), vp, i32, i64, i32, vp]
             L.neurosim_evsim_step_texture.restype = C.c_int

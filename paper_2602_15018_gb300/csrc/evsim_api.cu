@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <string>
 #include <memory>
+#include <new>
 #include <vector>
 
 #include "../../include/neurosim_evsim.h"
@@ -59,6 +60,60 @@ struct DeviceGuard {
         if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
 };
+
+// DLPack exchange format (v0.8 ABI, the layout every DLPack consumer reads):
+// a 1-D 64-bit integer tensor on a CUDA device, owned by its producer.  The
+// struct layouts follow the DLPack specification; the library fills them and
+// the consumer calls `deleter` when it is done with the view.
+struct DLDevice {
+    int32_t device_type;   // 2: CUDA device memory
+    int32_t device_id;
+};
+struct DLDataType {
+    uint8_t code;          // 0: signed integer
+    uint8_t bits;
+    uint16_t lanes;
+};
+struct DLTensor {
+    void* data;
+    DLDevice device;
+    int32_t ndim;
+    DLDataType dtype;
+    int64_t* shape;
+    int64_t* strides;      // NULL: compact row-major
+    uint64_t byte_offset;
+};
+struct DLManagedTensor {
+    DLTensor dl_tensor;
+    void* manager_ctx;
+    void (*deleter)(DLManagedTensor* self);
+};
+struct DLPackBox {         // one allocation: the descriptor and its shape
+    DLManagedTensor t;
+    int64_t shape[1];
+};
+
+void dlpack_delete(DLManagedTensor* self) { delete reinterpret_cast<DLPackBox*>(self); }
+
+// A view of n records at `data` (device `dev`) as int64 (the record bits,
+// as drains to device memory hand them out); the records stay the
+// library's (the deleter frees the descriptor only).
+void* make_dlpack_i64(const uint64_t* data, int64_t n, int dev)
+{
+    DLPackBox* b = new (std::nothrow) DLPackBox;
+    if (!b) return nullptr;
+    b->shape[0] = n;
+    b->t.dl_tensor.data = const_cast<uint64_t*>(data);
+    b->t.dl_tensor.device = DLDevice{2, dev};
+    b->t.dl_tensor.ndim = 1;
+    b->t.dl_tensor.dtype = DLDataType{0, 64, 1};
+    b->t.dl_tensor.shape = b->shape;
+    b->t.dl_tensor.strides = nullptr;
+    b->t.dl_tensor.byte_offset = 0;
+    b->t.manager_ctx = b;
+    b->t.deleter = dlpack_delete;
+    return &b->t;
+}
 
 int bits_of(uint64_t v)  // bits needed to hold v (>= 1)
 {
@@ -682,6 +737,65 @@ int neurosim_evsim_drain_events(neurosim_evsim* h, uint64_t* out, uint64_t out_c
     }
     h->pending.clear();
     h->n_pending_segs = 0;
+    return NEUROSIM_OK;
+}
+
+int neurosim_evsim_peek_events(neurosim_evsim* h, const uint64_t** events_dev, uint64_t* n_out,
+                               int64_t* seg_offsets, int64_t seg_capacity, int64_t* n_segs)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!events_dev) return fail(NEUROSIM_E_INVALID, "events_dev is NULL");
+    DeviceGuard g(h->device);
+    Ctl c;
+    rc = resolve(h, &c);
+    if (rc) return rc;
+    if (seg_offsets && seg_capacity < h->n_pending_segs + 1)
+        return fail(NEUROSIM_E_OVERFLOW, "seg_capacity %lld < %lld", (long long)seg_capacity,
+                    (long long)(h->n_pending_segs + 1));
+    if (seg_offsets) {
+        if (h->n_pending_segs > 0)
+            CUDA_TRY(cudaMemcpyAsync(seg_offsets, h->seg_off, (size_t)h->n_pending_segs * sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        seg_offsets[h->n_pending_segs] = (int64_t)c.run_total;
+    }
+    *events_dev = h->out;
+    if (n_out) *n_out = c.run_total;
+    if (n_segs) *n_segs = h->n_pending_segs;
+    return NEUROSIM_OK;
+}
+
+int neurosim_evsim_release_events(neurosim_evsim* h)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    Ctl c;
+    rc = resolve(h, &c);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->stats.events_drained += c.run_total;
+    if (!h->pending.empty()) {
+        h->cidx = 1 - h->cidx;
+        h->tau_c = h->tau_w;
+        h->has_c = h->has_w;
+    }
+    h->pending.clear();
+    h->n_pending_segs = 0;
+    return NEUROSIM_OK;
+}
+
+int neurosim_evsim_events_dlpack(neurosim_evsim* h, void** managed_tensor)
+{
+    if (!managed_tensor) return fail(NEUROSIM_E_INVALID, "managed_tensor is NULL");
+    const uint64_t* ev = nullptr;
+    uint64_t n = 0;
+    int rc = neurosim_evsim_peek_events(h, &ev, &n, nullptr, 0, nullptr);
+    if (rc) return rc;
+    *managed_tensor = make_dlpack_i64(ev, (int64_t)n, h->device);
+    if (!*managed_tensor) return fail(NEUROSIM_E_NOMEM, "cannot allocate the DLPack descriptor");
     return NEUROSIM_OK;
 }
 

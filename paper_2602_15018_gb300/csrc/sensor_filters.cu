@@ -74,6 +74,21 @@ __global__ void lowpass1_kernel(const float* L, float* out, int T, int64_t n, fl
     state[i] = s;
 }
 
+// Sensor leak: the log input rises by C+_u * r * (t - origin), FP32 as
+// fl(L + fl(fl(C+_u * r_us) * (float)(t - origin))) with r_us = (float)(r 1e-6).
+// One thread per pixel for all frames (4 B read + 4 B written per pixel-frame).
+__global__ void leak_kernel(const float* L, float* out, int T, int64_t n, int64_t t0, int dt, int64_t origin,
+                            float rate_us, const float* cpos, float cpos_u)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float k = __fmul_rn(cpos ? cpos[i] : cpos_u, rate_us);
+    for (int f = 0; f < T; ++f) {
+        const float s = __ll2float_rn(t0 + (int64_t)f * dt - origin);
+        out[(int64_t)f * n + i] = __fadd_rn(L[(int64_t)f * n + i], __fmul_rn(k, s));
+    }
+}
+
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 }  // namespace
@@ -122,5 +137,29 @@ extern "C" int neurosim_lowpass_log(const float* L_dev, float* out_dev, int32_t 
                                                                                            init);
     }
     if (cudaGetLastError() != cudaSuccess) return nsim::report_error(NEUROSIM_E_CUDA, "low-pass launch failed");
+    return NEUROSIM_OK;
+}
+
+extern "C" int neurosim_leak_log(const float* L_dev, float* out_dev, int32_t n_frames, int64_t n_pix, int64_t t0_us,
+                                 int32_t dt_us, int64_t origin_us, double rate_hz, const float* c_pos_dev, float c_pos,
+                                 void* cuda_stream)
+{
+    if (n_frames < 0 || n_pix < 0) return nsim::report_error(NEUROSIM_E_INVALID, "n_frames and n_pix must be >= 0");
+    if (!(rate_hz >= 0.0) || !std::isfinite(rate_hz)) return nsim::report_error(NEUROSIM_E_INVALID, "rate_hz must be >= 0");
+    if (dt_us < 1 || t0_us < origin_us)
+        return nsim::report_error(NEUROSIM_E_TIME, "need dt_us >= 1 and t0_us >= origin_us");
+    if (!c_pos_dev && !(c_pos > 0.0f)) return nsim::report_error(NEUROSIM_E_INVALID, "c_pos must be > 0");
+    if (n_pix == 0 || n_frames == 0) return NEUROSIM_OK;
+    if (!L_dev || !out_dev) return nsim::report_error(NEUROSIM_E_INVALID, "NULL buffer");
+    if (L_dev != out_dev && (const void*)L_dev < (const void*)(out_dev + (size_t)n_frames * n_pix) &&
+        (const void*)out_dev < (const void*)(L_dev + (size_t)n_frames * n_pix))
+        return nsim::report_error(NEUROSIM_E_INVALID, "L_dev and out_dev overlap without being equal");
+    constexpr int threads = 256;
+    if ((n_pix + threads - 1) / threads > 0x7FFFFFFFll)
+        return nsim::report_error(NEUROSIM_E_INVALID, "n_pix too large for one launch");
+    const float rate_us = (float)(rate_hz * 1e-6);
+    leak_kernel<<<(unsigned)((n_pix + threads - 1) / threads), threads, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
+        L_dev, out_dev, n_frames, n_pix, t0_us, dt_us, origin_us, rate_us, c_pos_dev, c_pos);
+    if (cudaGetLastError() != cudaSuccess) return nsim::report_error(NEUROSIM_E_CUDA, "leak launch failed");
     return NEUROSIM_OK;
 }

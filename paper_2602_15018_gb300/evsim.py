@@ -160,6 +160,31 @@ class EventSim:
         self._keep = []
         return ev, seg
 
+    # ------------------------------------------------------------ zero copy
+    def events_view(self):
+        """(events, seg_offsets) without a copy: events is a CUDA int64 tensor
+        (the record bits) aliasing the library's record buffer (through
+        DLPack), valid until the
+        next step, drain, release or close of this simulator; the events stay
+        pending until release()."""
+        p = C.c_void_p()
+        check(lib().neurosim_evsim_events_dlpack(self._h, C.byref(p)))
+        new_capsule = C.pythonapi.PyCapsule_New
+        new_capsule.restype = C.py_object
+        new_capsule.argtypes = [C.c_void_p, C.c_char_p, C.c_void_p]
+        from torch.utils.dlpack import from_dlpack
+        ev = from_dlpack(new_capsule(p, b"dltensor", None))
+        n_ev, n_seg = self.pending()
+        seg = np.zeros(n_seg + 1, np.int64)
+        evp, n_out, n_segs = C.c_void_p(), C.c_uint64(0), C.c_int64(0)
+        check(lib().neurosim_evsim_peek_events(self._h, C.byref(evp), C.byref(n_out),
+                                               C.c_void_p(seg.ctypes.data), seg.size, C.byref(n_segs)))
+        return ev, seg
+
+    def release(self) -> None:
+        """Clears the pending events (after events_view), copying nothing."""
+        check(lib().neurosim_evsim_release_events(self._h))
+
     # ------------------------------------------------------------------ state
     def get_state(self):
         n = self.W * self.H
@@ -542,3 +567,87 @@ def render_texture(scene: TextureScene, n_frames: int, t0_us: int = 0, dt_us: in
     check(lib().neurosim_render_texture(C.byref(scene), C.c_void_p(out.data_ptr()), int(n_frames), int(t0_us),
                                         int(dt_us), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
     return out
+
+
+def drain_into(sims, out: torch.Tensor):
+    """Variable-length batching: drains the sensors `sims` back to back into
+    one preallocated int64 CUDA tensor `out` (device-to-device copies into its
+    slices).  Returns (offsets, segs): sensor i's records are
+    out[offsets[i]:offsets[i + 1]], segs[i] its interval offsets.  Raises if
+    `out` is too small, before draining anything."""
+    if not (out.is_cuda and out.dtype == torch.int64 and out.is_contiguous() and out.dim() == 1):
+        raise ValueError("out must be a contiguous 1-D int64 CUDA tensor")
+    counts = [s.pending()[0] for s in sims]
+    offsets = np.zeros(len(sims) + 1, np.int64)
+    offsets[1:] = np.cumsum(counts)
+    if offsets[-1] > out.numel():
+        raise ValueError(f"out holds {out.numel()} records, the sensors have {int(offsets[-1])} pending")
+    segs = []
+    for i, s in enumerate(sims):
+        view = out[int(offsets[i]):]
+        ev, seg = s.drain(to="cuda", out=view)
+        assert ev.numel() == counts[i]
+        segs.append(seg)
+    return offsets, segs
+
+
+def leak_log(L: torch.Tensor, t0_us: int, dt_us: int, origin_us: int, rate_hz: float,
+             c_pos=0.2, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Sensor leak (library call neurosim_leak_log) on log frames L [T, ...] at
+    t0 + f dt: the log input rises by C+ * rate * (t - origin).  c_pos: a CUDA
+    float32 tensor of per-pixel ON thresholds (one frame's size) or a number.
+    out may be L (in place)."""
+    if not (L.is_cuda and L.dtype == torch.float32 and L.is_contiguous() and L.dim() >= 2):
+        raise ValueError("L must be a contiguous float32 CUDA tensor [T, ...]")
+    T, n = L.shape[0], L[0].numel()
+    cp_ptr, cp_u = None, 0.0
+    if isinstance(c_pos, torch.Tensor):
+        if not (c_pos.is_cuda and c_pos.dtype == torch.float32 and c_pos.is_contiguous() and c_pos.numel() == n):
+            raise ValueError("c_pos must be a contiguous float32 CUDA tensor of one frame's size")
+        cp_ptr = c_pos.data_ptr()
+    else:
+        cp_u = float(c_pos)
+    if out is None:
+        out = torch.empty_like(L)
+    check(lib().neurosim_leak_log(C.c_void_p(L.data_ptr()), C.c_void_p(out.data_ptr()), T, n, int(t0_us), int(dt_us),
+                                  int(origin_us), float(rate_hz), C.c_void_p(cp_ptr), cp_u,
+                                  C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return out
+
+
+def shot_noise(width: int, height: int, rate_hz: float, seed: int, ta0_us: int, D0_us: int, dt_us: int,
+               n_intervals: int):
+    """Shot-noise events (library call neurosim_shot_noise) of a step's
+    intervals: (records as an int64 CUDA tensor, host offsets)."""
+    seg = np.zeros(int(n_intervals) + 1, np.int64)
+    n = C.c_uint64(0)
+    L = lib()
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = L.neurosim_shot_noise(int(width), int(height), float(rate_hz), int(seed), int(ta0_us), int(D0_us),
+                               int(dt_us), int(n_intervals), None, 0, C.c_void_p(seg.ctypes.data), C.byref(n), st)
+    if rc not in (0, 4) or (rc == 4 and n.value == 0):
+        check(rc)
+    out = torch.empty(max(1, n.value), dtype=torch.int64, device="cuda")
+    check(L.neurosim_shot_noise(int(width), int(height), float(rate_hz), int(seed), int(ta0_us), int(D0_us),
+                                int(dt_us), int(n_intervals), C.c_void_p(out.data_ptr()), out.numel(),
+                                C.c_void_p(seg.ctypes.data), C.byref(n), st))
+    return out[: n.value], seg
+
+
+def merge_events(a: torch.Tensor, seg_a, b: torch.Tensor, seg_b):
+    """Two event streams with the same intervals merged per interval in the
+    stream's order (library call neurosim_merge_events): (int64 CUDA tensor,
+    host offsets)."""
+    sa = np.ascontiguousarray(seg_a, np.int64)
+    sb = np.ascontiguousarray(seg_b, np.int64)
+    if len(sa) != len(sb):
+        raise ValueError("the streams have different interval counts")
+    for t in (a, b):
+        if not (t.is_cuda and t.element_size() == 8 and t.is_contiguous()):
+            raise ValueError("events must be contiguous 64-bit CUDA tensors")
+    out = torch.empty(max(1, int(sa[-1] + sb[-1])), dtype=torch.int64, device="cuda")
+    so = np.zeros(len(sa), np.int64)
+    check(lib().neurosim_merge_events(C.c_void_p(a.data_ptr()), C.c_void_p(sa.ctypes.data), C.c_void_p(b.data_ptr()),
+                                      C.c_void_p(sb.ctypes.data), len(sa) - 1, C.c_void_p(out.data_ptr()),
+                                      C.c_void_p(so.ctypes.data), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return out[: int(so[-1])], so
