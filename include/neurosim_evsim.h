@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define NEUROSIM_EVSIM_ABI_VERSION 1
+#define NEUROSIM_EVSIM_ABI_VERSION 2
 
 enum neurosim_status {
     NEUROSIM_OK = 0,
@@ -86,7 +86,10 @@ typedef struct neurosim_evsim_params {
                                     0 = auto.  The emission kernel models the
                                     frames in pairs and keeps one pair in
                                     flight: 2 and 3 behave the same          */
-    int32_t reserved[6];         /* must be zero                               */
+    int32_t ctas_per_sm;         /* emission CTAs resident per SM (each CTA
+                                    holds 64 / pixels_per_thread warps, one
+                                    tile each at a time); 0 = as many as fit */
+    int32_t reserved[5];         /* must be zero                               */
 } neurosim_evsim_params;
 
 /* Fills *p with defaults: C+ = C- = 0.2, sigma 0, c_min 0.01, no refractory,
@@ -255,7 +258,8 @@ typedef struct {
     int32_t frame_slots;         /* frame-buffer sets that can be registered
                                     (0 = 2, at most 16): a renderer fills one
                                     while the steps read another               */
-    int32_t reserved[5];         /* must be zero                                  */
+    int32_t ctas_per_sm;         /* emission CTAs per SM: 0 = as many as fit      */
+    int32_t reserved[4];         /* must be zero                                  */
 } neurosim_evsim_batch_params;
 
 /* Fills *p with defaults (n_streams 1, T 16, dt 1000 us). */
@@ -338,25 +342,27 @@ int neurosim_evsim_batch_counters(neurosim_evsim_batch *b, uint64_t *launches, u
 void neurosim_evsim_batch_destroy(neurosim_evsim_batch *b);
 
 /* ------------------------------------------------------------------------
- * Autotuner: picks the emission tile (pixels_per_thread: 8 or 16) for a
- * workload by timing every variant on the caller's frames (prefetch_frames
- * is reported as 2: the kernel keeps one pair of frames in flight).  The
- * paper has no autotuner (it fixes one thread per pixel).
+ * Autotuner: picks the emission launch shape for a workload by timing every
+ * variant on the caller's frames: the warp tile (pixels_per_thread 8 or 16:
+ * 256 or 512 pixels per warp) times the number of emission CTAs resident per
+ * SM (1 up to what fits).  The paper has no autotuner (it fixes one thread
+ * per pixel).
  *
  * Times `repeats` (>= 1) steps of n_frames frames (DEVICE [T][H][W] FP32 at
  * spacing dt_us) with each variant on a fresh simulator of params p (the
- * params' pixels_per_thread / prefetch_frames are ignored) and keeps the one
- * with the smallest median emission + sort time; all variants produce the
- * same events.  If cache_path is not NULL, a result cached there for this
- * GPU model, width, height and n_frames is returned without timing, and a
- * new result is appended to it (one JSON object per line:
- * {"gpu": ..., "width": W, "height": H, "frames": T, "pixels_per_thread": P,
- *  "prefetch_frames": F, "ms": M}).  *ms_out (nullable) gets the winner's
- * median time.  Returns NEUROSIM_E_INVALID / NEUROSIM_E_CUDA / NEUROSIM_E_NOMEM. */
+ * params' launch fields are ignored) and keeps the one with the smallest
+ * median emission + sort time; all variants produce the same events.  If
+ * cache_path is not NULL, a result cached there for this GPU model, width,
+ * height and n_frames is returned without timing, and a new result is
+ * appended to it (one JSON object per line: {"gpu": ..., "width": W,
+ * "height": H, "frames": T, "pixels_per_thread": P, "ctas_per_sm": C,
+ * "ms": M, "timings": [[P, C, ms], ...]}, every variant timed).  *ms_out
+ * (nullable) gets the winner's median time.  Returns NEUROSIM_E_INVALID /
+ * NEUROSIM_E_CUDA / NEUROSIM_E_NOMEM. */
 int neurosim_evsim_autotune(const neurosim_evsim_params *p, const float *frames_dev,
                             int32_t n_frames, int32_t dt_us, int32_t repeats,
                             const char *cache_path, int32_t *pixels_per_thread,
-                            int32_t *prefetch_frames, double *ms_out);
+                            int32_t *ctas_per_sm, double *ms_out);
 
 /* ------------------------------------------------------------------------
  * Learned interpolator.  The paper has no counterpart (it renders every frame,

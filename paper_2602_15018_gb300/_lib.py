@@ -76,7 +76,7 @@ class Params(C.Structure):
         ("c_pos_map", C.POINTER(C.c_float)), ("c_neg_map", C.POINTER(C.c_float)),
         ("event_capacity", C.c_uint64), ("max_frames_per_step", C.c_int32),
         ("max_pending_intervals", C.c_int32), ("pixels_per_thread", C.c_int32),
-        ("prefetch_frames", C.c_int32), ("reserved", C.c_int32 * 6),
+        ("prefetch_frames", C.c_int32), ("ctas_per_sm", C.c_int32), ("reserved", C.c_int32 * 5),
     ]
 
 
@@ -86,7 +86,7 @@ class BatchParams(C.Structure):
         ("n_streams", C.c_int32), ("frames_per_step", C.c_int32), ("dt_us", C.c_int32),
         ("max_pending_steps", C.c_int32), ("t0_us", C.c_int64), ("event_capacity", C.c_uint64),
         ("pixels_per_thread", C.c_int32), ("prefetch_frames", C.c_int32),
-        ("frame_slots", C.c_int32), ("reserved", C.c_int32 * 5),
+        ("frame_slots", C.c_int32), ("ctas_per_sm", C.c_int32), ("reserved", C.c_int32 * 4),
     ]
 
 

@@ -299,7 +299,8 @@ int validate(const neurosim_evsim_params* p)
         return fail(NEUROSIM_E_INVALID, "pixels_per_thread must be 0, 8 or 16");
     if (p->prefetch_frames != 0 && p->prefetch_frames != 2 && p->prefetch_frames != 3)
         return fail(NEUROSIM_E_INVALID, "prefetch_frames must be 0, 2 or 3");
-    for (int i = 0; i < 6; ++i)
+    if (p->ctas_per_sm < 0 || p->ctas_per_sm > 64) return fail(NEUROSIM_E_INVALID, "ctas_per_sm must be in [0, 64]");
+    for (int i = 0; i < 5; ++i)
         if (p->reserved[i] != 0) return fail(NEUROSIM_E_INVALID, "reserved fields must be zero");
     return NEUROSIM_OK;
 }
@@ -577,6 +578,10 @@ int neurosim_evsim_create(const neurosim_evsim_params* p, void* cuda_stream, neu
         return bail(fail(NEUROSIM_E_CUDA, "emission kernel does not fit (ppt %d, prefetch %d)",
                          h->ppt, h->pf));
     const int wpc = emit_warps_per_cta(h->ppt);
+    if (p->ctas_per_sm > 0) {          // the caller's (or the autotuner's) launch shape
+        bps32 = std::min(bps32, p->ctas_per_sm);
+        bps64 = std::min(bps64, p->ctas_per_sm);
+    }
     h->grid_emit32 = std::min((h->n_tiles + wpc - 1) / wpc, h->sms * bps32);
     h->grid_emit64 = std::min((h->n_tiles + wpc - 1) / wpc, h->sms * bps64);
     int tps32 = 0, tps64 = 0;

@@ -29,11 +29,21 @@ int fail(int code, const char* fmt, ...)
 }
 
 struct Variant {
-    int ppt, pf;
+    int ppt, ctas;     // pixels per lane (warp tile 32 * ppt) and emission CTAs per SM
 };
-// The emission kernel keeps one pair of frames in flight for either prefetch
-// setting, so only the tile size is swept.
-constexpr Variant kVariants[] = {{8, 2}, {16, 2}};
+
+// The launch shapes to time: both warp tiles, each with 1 up to as many
+// CTAs per SM as fit (the occupancy of the kernel with 32-bit keys).
+int variants(std::vector<Variant>* out)
+{
+    out->clear();
+    for (int ppt : {8, 16}) {
+        int bps = 0;
+        if (nsim::emit_occupancy(ppt, 2, 0, &bps) != cudaSuccess || bps < 1) return NEUROSIM_E_CUDA;
+        for (int c = 1; c <= bps; ++c) out->push_back(Variant{ppt, c});
+    }
+    return NEUROSIM_OK;
+}
 
 // Value of "key": in one JSON line (number or string); false if absent.
 bool json_field(const std::string& line, const char* key, std::string* out)
@@ -55,26 +65,24 @@ bool json_field(const std::string& line, const char* key, std::string* out)
     return true;
 }
 
-bool cache_lookup(const char* path, const std::string& gpu, int W, int H, int T, int* ppt, int* pf, double* ms)
+bool cache_lookup(const char* path, const std::string& gpu, int W, int H, int T, int* ppt, int* ctas, double* ms)
 {
     FILE* f = fopen(path, "r");
     if (!f) return false;
     bool found = false;
-    char buf[1024];
-    while (fgets(buf, sizeof buf, f)) {
-        const std::string line(buf);
-        std::string g, w, h, t, p, q, m;
+    std::vector<char> buf(1 << 16);
+    while (fgets(buf.data(), (int)buf.size(), f)) {
+        const std::string line(buf.data());
+        std::string g, w, h, t, p, c, m;
         if (!json_field(line, "gpu", &g) || !json_field(line, "width", &w) || !json_field(line, "height", &h) ||
             !json_field(line, "frames", &t) || !json_field(line, "pixels_per_thread", &p) ||
-            !json_field(line, "prefetch_frames", &q))
+            !json_field(line, "ctas_per_sm", &c))
             continue;
         if (g != gpu || atoi(w.c_str()) != W || atoi(h.c_str()) != H || atoi(t.c_str()) != T) continue;
-        const int pv = atoi(p.c_str()), qv = atoi(q.c_str());
-        bool ok = false;
-        for (const Variant& v : kVariants) ok |= (v.ppt == pv && v.pf == qv);
-        if (!ok) continue;
+        const int pv = atoi(p.c_str()), cv = atoi(c.c_str());
+        if ((pv != 8 && pv != 16) || cv < 1 || cv > 64) continue;
         *ppt = pv;
-        *pf = qv;
+        *ctas = cv;
         *ms = json_field(line, "ms", &m) ? atof(m.c_str()) : 0.0;
         found = true;   // the last matching line wins
     }
@@ -128,9 +136,9 @@ int time_variant(const neurosim_evsim_params* p, const float* frames, int T, int
 
 extern "C" int neurosim_evsim_autotune(const neurosim_evsim_params* p, const float* frames_dev, int32_t n_frames,
                                        int32_t dt_us, int32_t repeats, const char* cache_path,
-                                       int32_t* pixels_per_thread, int32_t* prefetch_frames, double* ms_out)
+                                       int32_t* pixels_per_thread, int32_t* ctas_per_sm, double* ms_out)
 {
-    if (!p || !frames_dev || !pixels_per_thread || !prefetch_frames)
+    if (!p || !frames_dev || !pixels_per_thread || !ctas_per_sm)
         return fail(NEUROSIM_E_INVALID, "params, frames_dev and the outputs must not be NULL");
     if (n_frames < 2) return fail(NEUROSIM_E_INVALID, "n_frames must be >= 2");
     if (repeats < 1 || repeats > 100) return fail(NEUROSIM_E_INVALID, "repeats must be in [1, 100]");
@@ -143,46 +151,53 @@ extern "C" int neurosim_evsim_autotune(const neurosim_evsim_params* p, const flo
         return fail(NEUROSIM_E_CUDA, "no CUDA device");
     const std::string gpu(prop.name);
     double best_ms = 0.0;
-    int best_ppt = 0, best_pf = 0;
-    if (cache_path && cache_lookup(cache_path, gpu, p->width, p->height, n_frames, &best_ppt, &best_pf, &best_ms)) {
+    int best_ppt = 0, best_ctas = 0;
+    if (cache_path && cache_lookup(cache_path, gpu, p->width, p->height, n_frames, &best_ppt, &best_ctas, &best_ms)) {
         *pixels_per_thread = best_ppt;
-        *prefetch_frames = best_pf;
+        *ctas_per_sm = best_ctas;
         if (ms_out) *ms_out = best_ms;
         return NEUROSIM_OK;
     }
+    std::vector<Variant> vs;
+    if (variants(&vs) != NEUROSIM_OK) return fail(NEUROSIM_E_CUDA, "cannot query the emission kernel's occupancy");
     cudaStream_t st = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
         return fail(NEUROSIM_E_CUDA, "cannot create a stream");
     uint64_t* buf = nullptr;
     uint64_t cap = 0;
     int rc = NEUROSIM_OK;
-    for (const Variant& v : kVariants) {
+    std::string timings;
+    for (const Variant& v : vs) {
         neurosim_evsim_params q = *p;
         q.pixels_per_thread = v.ppt;
-        q.prefetch_frames = v.pf;
+        q.prefetch_frames = 0;
+        q.ctas_per_sm = v.ctas;
         q.max_frames_per_step = std::max(q.max_frames_per_step, n_frames);
         double ms = 0.0;
         rc = time_variant(&q, frames_dev, n_frames, dt_us, repeats, st, &buf, &cap, &ms);
         if (rc) break;
+        char item[64];
+        snprintf(item, sizeof item, "%s[%d, %d, %.4f]", timings.empty() ? "" : ", ", v.ppt, v.ctas, ms);
+        timings += item;
         if (best_ppt == 0 || ms < best_ms) {
             best_ms = ms;
             best_ppt = v.ppt;
-            best_pf = v.pf;
+            best_ctas = v.ctas;
         }
     }
     if (buf) cudaFree(buf);
     cudaStreamDestroy(st);
     if (rc) return rc;
     *pixels_per_thread = best_ppt;
-    *prefetch_frames = best_pf;
+    *ctas_per_sm = best_ctas;
     if (ms_out) *ms_out = best_ms;
     if (cache_path) {
         FILE* f = fopen(cache_path, "a");
         if (f) {
             fprintf(f,
                     "{\"gpu\": \"%s\", \"width\": %d, \"height\": %d, \"frames\": %d, \"pixels_per_thread\": %d, "
-                    "\"prefetch_frames\": %d, \"ms\": %.4f}\n",
-                    gpu.c_str(), p->width, p->height, n_frames, best_ppt, best_pf, best_ms);
+                    "\"ctas_per_sm\": %d, \"ms\": %.4f, \"timings\": [%s]}\n",
+                    gpu.c_str(), p->width, p->height, n_frames, best_ppt, best_ctas, best_ms, timings.c_str());
             fclose(f);
         }
     }

@@ -280,7 +280,8 @@ int neurosim_evsim_batch_create(const neurosim_evsim_params* streams, const neur
     if (bp->prefetch_frames != 0 && bp->prefetch_frames != 2 && bp->prefetch_frames != 3)
         return fail(NEUROSIM_E_INVALID, "prefetch_frames must be 0, 2 or 3");
     if (bp->frame_slots < 0 || bp->frame_slots > 16) return fail(NEUROSIM_E_INVALID, "frame_slots must be in [0, 16]");
-    for (int i = 0; i < 5; ++i)
+    if (bp->ctas_per_sm < 0 || bp->ctas_per_sm > 64) return fail(NEUROSIM_E_INVALID, "ctas_per_sm must be in [0, 64]");
+    for (int i = 0; i < 4; ++i)
         if (bp->reserved[i] != 0) return fail(NEUROSIM_E_INVALID, "reserved fields must be zero");
     for (int i = 0; i < bp->n_streams; ++i) {
         const int rc = validate_stream_params(&streams[i]);
@@ -365,7 +366,9 @@ int neurosim_evsim_batch_create(const neurosim_evsim_params* streams, const neur
     if (emit_occupancy(b->ppt, b->pf, 1, &bps64) != cudaSuccess || bps64 < 1)
         return bail(fail(NEUROSIM_E_CUDA, "emission kernel does not fit (ppt %d, prefetch %d)", b->ppt, b->pf));
     const int wpc = emit_warps_per_cta(b->ppt);
-    b->grid_emit = std::min((b->n_items + wpc - 1) / wpc, b->sms * (b->key64 ? bps64 : bps));
+    int per_sm = b->key64 ? bps64 : bps;
+    if (bp->ctas_per_sm > 0) per_sm = std::min(per_sm, bp->ctas_per_sm);
+    b->grid_emit = std::min((b->n_items + wpc - 1) / wpc, b->sms * per_sm);
     if (sort_configure(&b->sort_smem) != cudaSuccess)
         return bail(fail(NEUROSIM_E_CUDA, "cannot configure the sort kernel"));
 

@@ -52,7 +52,7 @@ class EventSim:
                  log_eps: float = 1e-3, input_is_log: bool = False, seed: int = 0,
                  c_pos_map=None, c_neg_map=None, event_capacity: int = 0,
                  max_frames_per_step: int = 0, max_pending_intervals: int = 0,
-                 pixels_per_thread: int = 0, prefetch_frames: int = 0,
+                 pixels_per_thread: int = 0, prefetch_frames: int = 0, ctas_per_sm: int = 0,
                  stream: torch.cuda.Stream | None = None, device=None):
         L = lib()
         self.W, self.H = int(width), int(height)
@@ -78,6 +78,7 @@ class EventSim:
         p.max_pending_intervals = int(max_pending_intervals)
         p.pixels_per_thread = int(pixels_per_thread)
         p.prefetch_frames = int(prefetch_frames)
+        p.ctas_per_sm = int(ctas_per_sm)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream()
             h = C.c_void_p()
@@ -322,7 +323,7 @@ class EventSimBatch:
 
     def __init__(self, sensors, frames_per_step: int, dt_us: int = 1000, t0_us: int = 0,
                  event_capacity: int = 0, max_pending_steps: int = 0,
-                 pixels_per_thread: int = 0, prefetch_frames: int = 0, frame_slots: int = 0,
+                 pixels_per_thread: int = 0, prefetch_frames: int = 0, frame_slots: int = 0, ctas_per_sm: int = 0,
                  stream: torch.cuda.Stream | None = None):
         L = lib()
         keep = []
@@ -340,6 +341,7 @@ class EventSimBatch:
         bp.max_pending_steps = int(max_pending_steps)
         bp.pixels_per_thread = int(pixels_per_thread)
         bp.prefetch_frames = int(prefetch_frames)
+        bp.ctas_per_sm = int(ctas_per_sm)
         bp.frame_slots = int(frame_slots)
         self.T = int(frames_per_step)
         self.n = len(sensors)
@@ -466,21 +468,22 @@ class EventSimBatch:
 
 def autotune(frames: torch.Tensor, dt_us: int = 1000, repeats: int = 5, cache_path: str | None = None,
              **sensor):
-    """Times every emission launch shape on `frames` [T, H, W] (FP32, CUDA) for
-    one sensor (EventSim's keywords) and returns (pixels_per_thread,
-    prefetch_frames, median_ms); `cache_path` is a JSON-lines cache keyed by
-    GPU model, width, height and T."""
+    """Times every emission launch shape (warp tile x CTAs per SM) on `frames`
+    [T, H, W] (FP32, CUDA) for one sensor (EventSim's keywords), the median of
+    `repeats` steps each, and returns (pixels_per_thread, ctas_per_sm,
+    median_ms) of the fastest; `cache_path` is a JSON-lines cache keyed by GPU
+    model, width, height and T that also lists every variant's time."""
     H, W = frames.shape[-2], frames.shape[-1]
     if not (frames.is_cuda and frames.dtype == torch.float32 and frames.is_contiguous()):
         raise ValueError("frames must be a contiguous float32 CUDA tensor [T, H, W]")
     keep = []
     p = _params(W, H, keep=keep, **sensor)
-    ppt, pf, ms = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
+    ppt, ctas, ms = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
     T = frames.numel() // (H * W)
     check(lib().neurosim_evsim_autotune(C.byref(p), C.c_void_p(frames.data_ptr()), T, int(dt_us),
                                         int(repeats), cache_path.encode() if cache_path else None,
-                                        C.byref(ppt), C.byref(pf), C.byref(ms)))
-    return int(ppt.value), int(pf.value), float(ms.value)
+                                        C.byref(ppt), C.byref(ctas), C.byref(ms)))
+    return int(ppt.value), int(ctas.value), float(ms.value)
 
 
 def event_f1(pred, ref, tol_us: int = 1000) -> dict:

@@ -48,7 +48,7 @@ def test_library_exports_every_declared_symbol(built):
 def test_abi_version_and_defaults(built):
     from paper_2602_15018_gb300 import _lib
     L = _lib.lib()
-    assert L.neurosim_abi_version() == 1
+    assert L.neurosim_abi_version() == 2
     p = _lib.Params()
     L.neurosim_evsim_default_params(C.byref(p))
     assert abs(p.c_pos - 0.2) < 1e-7 and abs(p.c_min - 0.01) < 1e-7 and p.width == 0
@@ -109,7 +109,7 @@ def test_batch_defaults_and_no_gpu(built):
     L.neurosim_evsim_batch_default_params(C.byref(bp))
     assert bp.n_streams == 1 and bp.frames_per_step == 16 and bp.dt_us == 1000
     assert bp.t0_us == 0 and bp.event_capacity == 0 and bp.frame_slots == 0
-    assert list(bp.reserved) == [0] * 5
+    assert list(bp.reserved) == [0] * 4 and bp.ctas_per_sm == 0
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
     p = _lib.Params()

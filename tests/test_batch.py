@@ -210,24 +210,33 @@ def test_batch_pending_capacity_is_enforced():
     batch.close()
 
 
-def test_autotune_picks_a_variant_and_caches_it(tmp_path):
+def test_autotune_picks_the_fastest_timed_variant_and_caches_it(tmp_path):
+    """The tuner times every launch shape (warp tile 256 or 512 pixels x 1 up
+    to the resident CTAs per SM), keeps the one with the smallest median
+    time, caches it with every variant's time, and the picked shape computes
+    the default shape's events."""
+    import json
+
     from paper_2602_15018_gb300 import EventSim, autotune
     W, H, T = 320, 180, 40
     fr = scenes.render_frames(scenes.TextureScene(W, H, seed=9), T).cuda()
     cache = str(tmp_path / "tune.jsonl")
-    ppt, pf, ms = autotune(fr, dt_us=DT, repeats=3, cache_path=cache, c_pos=0.2, c_neg=0.25,
-                           sigma_c=0.03, refractory_us=100, seed=1)
-    assert (ppt, pf) in {(8, 2), (8, 3), (16, 2), (16, 3)} and ms > 0
+    kw = dict(c_pos=0.2, c_neg=0.25, sigma_c=0.03, refractory_us=100, seed=1)
+    ppt, ctas, ms = autotune(fr, dt_us=DT, repeats=5, cache_path=cache, **kw)
     lines = open(cache).read().strip().split("\n")
-    assert len(lines) == 1 and f'"pixels_per_thread": {ppt}' in lines[0]
-    again = autotune(fr, dt_us=DT, repeats=3, cache_path=cache, c_pos=0.2, c_neg=0.25,
-                     sigma_c=0.03, refractory_us=100, seed=1)
-    assert again[:2] == (ppt, pf) and len(open(cache).read().strip().split("\n")) == 1
-    # the picked variant computes the same events as the default one
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    timings = rec["timings"]
+    shapes = {(p, c) for p, c, _ in timings}
+    assert {(8, 1), (16, 1)} <= shapes and len(shapes) == len(timings) >= 4
+    fastest = min(timings, key=lambda v: v[2])
+    assert (ppt, ctas) == (fastest[0], fastest[1]) == (rec["pixels_per_thread"], rec["ctas_per_sm"])
+    assert abs(ms - fastest[2]) < 1e-3 and ms > 0
+    again = autotune(fr, dt_us=DT, repeats=5, cache_path=cache, **kw)
+    assert again[:2] == (ppt, ctas) and len(open(cache).read().strip().split("\n")) == 1
     res = []
-    for kw in (dict(), dict(pixels_per_thread=ppt, prefetch_frames=pf)):
-        sim = EventSim(W, H, c_pos=0.2, c_neg=0.25, sigma_c=0.03, refractory_us=100, seed=1,
-                       max_frames_per_step=T, **kw)
+    for shape in (dict(), dict(pixels_per_thread=ppt, ctas_per_sm=ctas)):
+        sim = EventSim(W, H, max_frames_per_step=T, **kw, **shape)
         sim.step(fr, 0, DT)
         res.append(sim.drain())
         sim.close()
