@@ -347,6 +347,13 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, dev)
 
+    secondary = None
+    if rank == 0 and ws == 1 and args.workload == "hd" and not args.frames and not args.no_secondary:
+        sim.close()
+        sim = None
+        torch.cuda.empty_cache()
+        secondary = run_secondary()
+
     if rank == 0:
         clk = clocks.summary(tw0, tw1)
         line = {
@@ -378,8 +385,11 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "clocks": clk,
         }
+        if secondary is not None:
+            line["secondary"] = secondary
         print(json.dumps(line), flush=True)
-    sim.close()
+    if sim is not None:
+        sim.close()
     if dist:
         dist.destroy_process_group()
 
@@ -1070,6 +1080,42 @@ def _oracle_sample_frames(args, dev):
     return fr.cpu().numpy(), n
 
 
+SECONDARY = (
+    ("batch", ["--steps", "4"]),
+    ("learned", ["--steps", "2", "--train-steps", "1000"]),
+    ("batched_learned", ["--steps", "2", "--train-steps", "1000"]),
+)
+SECONDARY_KEYS = ("value", "unit", "ms_per_step", "events_per_s", "f1", "f1_linear", "count_err",
+                  "count_err_linear", "plain_value", "e2e_speedup_vs_plain", "e2e_speedup_vs_plain_with_render",
+                  "roofline", "clocks", "gpu_launches")
+
+
+def run_secondary():
+    """The batched and learned workloads, each in a child process after the
+    headline measurement (short: 4 batched steps; the interpolator trained for
+    1000 steps), so that one default run records the plain, batched and learned
+    paths side by side.  A failure is recorded, not raised."""
+    res = {}
+    for name, extra in SECONDARY:
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", name, "--warmup", "3", "--no-cpu-baseline",
+               "--no-secondary", *extra]
+        t0 = time.time()
+        try:
+            p = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+            lines = [ln for ln in p.stdout.strip().splitlines() if ln.startswith("{")]
+            if p.returncode != 0 or not lines:
+                res[name] = {"error": f"exit {p.returncode}: {(p.stderr or p.stdout)[-300:]}"}
+                continue
+            d = json.loads(lines[-1])
+            res[name] = {k: d[k] for k in SECONDARY_KEYS if k in d}
+            res[name]["config"] = d.get("config", {}).get("workload")
+            res[name]["args"] = " ".join(extra)
+        except (subprocess.TimeoutExpired, OSError, ValueError) as e:
+            res[name] = {"error": str(e)[-300:]}
+        res[name]["wall_s"] = round(time.time() - t0, 1)
+    return res
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -1250,6 +1296,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-frames", type=int, default=480)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="default workload: skip the batched and learned child runs")
     ap.add_argument("--keys", type=int, default=126, help="learned workload: keyframes per clip")
     ap.add_argument("--bl-small", type=int, default=1024, help="batched_learned: 320x240 sensors")
     ap.add_argument("--bl-big", type=int, default=64, help="batched_learned: 1280x720 sensors")
