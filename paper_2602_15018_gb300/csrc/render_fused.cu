@@ -70,12 +70,20 @@ __global__ void render_kernel(const SceneFrame* __restrict__ tab, SceneConst sc,
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (i >= npix) return;
     const SceneFrame& fr = tab[f];
-    float v[4];
+    float xs[4], ys[4], v[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const int64_t g = i + m;
         const int y = (int)(g / sc.W), x = (int)(g - (int64_t)y * sc.W);
-        v[m] = (g < npix) ? texture_pixel(sc, fr, (float)x, (float)y) : 0.0f;
+        xs[m] = (float)x;
+        ys[m] = (float)y;
+    }
+    texture_noise4(sc, fr, xs, ys, v);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        for (int k = 0; k < sc.n_rects; ++k)
+            if (rect_covers(fr.rect[k], xs[m], ys[m])) v[m] = fr.rval[k];
+        if (i + m >= npix) v[m] = 0.0f;
     }
     float* dst = out + (int64_t)f * npix + i;
     if (vec && i + 4 <= npix) {
