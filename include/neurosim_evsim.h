@@ -544,8 +544,11 @@ int32_t neurosim_abi_version(void);
  * with BF16 DEVICE operands; modes 0-3 gather the operands with CUDA cores:
  * bit 0: A stored [K][M] (else [M][K]), bit 1: B stored [K][N] (else
  * [N][K]); modes 4 and 5 load A [M][K] and B [N][K] with TMA into 128- or
- * 64-byte-swizzled tiles (16-byte-aligned operands).  16 <= N <= 256, N % 16 == 0, K % 8 == 0,
- * M % 8 == 0 when A is stored [K][M].  Synchronises cuda_stream. */
+ * 64-byte-swizzled tiles (16-byte-aligned operands); mode 6 loads A [K][M]
+ * and B [K][N] with TMA as MN-major tiles (the weight-gradient GEMM over
+ * pixels, K split over CTAs and summed with atomics).  16 <= N <= 256,
+ * N % 16 == 0, K % 8 == 0, M % 8 == 0 when A is stored [K][M].
+ * Synchronises cuda_stream. */
 int neurosim_debug_umma_gemm(int32_t mode, int32_t M, int32_t N, int32_t K, const void *A,
                              const void *B, float *C, void *cuda_stream);
 

@@ -9,6 +9,7 @@
 #include "evsim_internal.h"
 #include "umma_gemm.cuh"
 #include "umma_tma.cuh"
+#include "umma_mn.cuh"
 
 namespace {
 
@@ -74,6 +75,31 @@ int run_tma(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B,
     return NEUROSIM_OK;
 }
 
+// MN-major TMA GEMM over "pixels": A stored [K][M] and B stored [K][N] are
+// viewed as one image row of K pixels with M (N) channels; C is zeroed and
+// the K-slice partial tiles are added into it.
+template <int BN>
+int run_mn(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, unsigned int* err,
+           cudaStream_t st)
+{
+    umn::MnArgs<BN> g;
+    g.a = umn::MnOp{umn::kPix, M, 0, 1, M, umn::pick_sw(M)};
+    g.b = umn::MnOp{umn::kPix, N, 0, 1, N, umn::pick_sw(N)};
+    if (!umn::encode_op(&g.ta, A, M, K, 1, 1, g.a) || !umn::encode_op(&g.tb, B, N, K, 1, 1, g.b))
+        return NEUROSIM_E_CUDA;
+    const int xb = (K + umn::KT - 1) / umn::KT;
+    g.geom = umn::MnGeom{1, K, xb, xb};
+    g.M = M;
+    g.N = N;
+    g.dw = C;
+    g.err = err;
+    g.limit_ns = 2000000000ull;
+    if (cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(float), st) != cudaSuccess) return NEUROSIM_E_CUDA;
+    // a few K slices, so that the partial tiles are really added
+    if (umn::launch_mn_gemm<BN>(g, 3 * ((M + umn::BM - 1) / umn::BM), st) != cudaSuccess) return NEUROSIM_E_CUDA;
+    return NEUROSIM_OK;
+}
+
 // One CTA of 32 threads: thread 0 sets up an mbarrier expecting one arrival
 // and, if `arrive`, arrives on it; then the whole warp waits for the phase
 // with the same bounded wait as the tensor-core kernels (umma::mbar_wait).
@@ -124,10 +150,10 @@ extern "C" int neurosim_debug_umma_gemm(int32_t mode, int32_t M, int32_t N, int3
                                         const void* B, float* C, void* cuda_stream)
 {
     if (!A || !B || !C) return nsim::report_error(NEUROSIM_E_INVALID, "NULL operand");
-    if (mode < 0 || mode > 5) return nsim::report_error(NEUROSIM_E_INVALID, "mode must be in [0, 5]");
+    if (mode < 0 || mode > 6) return nsim::report_error(NEUROSIM_E_INVALID, "mode must be in [0, 6]");
     if (mode >= 4 && (reinterpret_cast<uintptr_t>(A) & 15u || reinterpret_cast<uintptr_t>(B) & 15u))
         return nsim::report_error(NEUROSIM_E_INVALID, "TMA operands must be 16-byte aligned");
-    const bool amn = mode < 4 && (mode & 1), bmn = mode < 4 && (mode & 2);
+    const bool amn = (mode < 4 && (mode & 1)) || mode == 6, bmn = (mode < 4 && (mode & 2)) || mode == 6;
     if (M < 1 || N < 16 || N > 256 || N % 16 || K < 8 || K % 8 || (amn && M % 8) || (bmn && N % 8))
         return nsim::report_error(NEUROSIM_E_INVALID,
                                   "need M >= 1, 16 <= N <= 256 with N % 16 == 0, K % 8 == 0, MN-major rows % 8 == 0");
@@ -138,7 +164,11 @@ extern "C" int neurosim_debug_umma_gemm(int32_t mode, int32_t M, int32_t N, int3
         return nsim::report_error(NEUROSIM_E_CUDA, "cannot allocate the error word");
     const auto* a = static_cast<const __nv_bfloat16*>(A);
     const auto* b = static_cast<const __nv_bfloat16*>(B);
-    int rc = mode == 4 ? (N <= 64 ? run_tma<64, 128>(M, N, K, a, b, C, err, st) : run_tma<256, 128>(M, N, K, a, b, C, err, st))
+    int rc = mode == 6 ? (N <= 16 ? run_mn<16>(M, N, K, a, b, C, err, st)
+                          : N <= 32 ? run_mn<32>(M, N, K, a, b, C, err, st)
+                          : N <= 64 ? run_mn<64>(M, N, K, a, b, C, err, st)
+                          : N <= 128 ? run_mn<128>(M, N, K, a, b, C, err, st) : run_mn<256>(M, N, K, a, b, C, err, st))
+             : mode == 4 ? (N <= 64 ? run_tma<64, 128>(M, N, K, a, b, C, err, st) : run_tma<256, 128>(M, N, K, a, b, C, err, st))
              : mode == 5 ? (N <= 64 ? run_tma<64, 64>(M, N, K, a, b, C, err, st) : run_tma<256, 64>(M, N, K, a, b, C, err, st))
              : N <= 64 ? dispatch<64>(mode, M, N, K, a, b, C, err, st)
                        : dispatch<256>(mode, M, N, K, a, b, C, err, st);

@@ -34,6 +34,7 @@
 #include "../../include/neurosim_evsim.h"
 #include "evsim_internal.h"
 #include "interp_layers.cuh"
+#include "umma_mn.cuh"
 #include "umma_tma.cuh"
 
 using namespace interp;
@@ -565,6 +566,55 @@ int forward(neurosim_interp* h, const Shape& s, const float* L0, const float* L4
     return NEUROSIM_OK;
 }
 
+// ---- weight gradients over pixels with TMA-loaded MN-major operands ------------------
+template <int BN>
+int dw_mn_bn(neurosim_interp* h, const Act& xa, const umn::MnOp& a, const Act& xb, const umn::MnOp& b, int Ho, int Wo,
+             float* dw, int M, int N, bool* done)
+{
+    umn::MnArgs<BN> g;
+    g.a = a;
+    g.b = b;
+    if (!umn::encode_op(&g.ta, xa.p, xa.stride, xa.W, xa.H, xa.N, a) ||
+        !umn::encode_op(&g.tb, xb.p, xb.stride, xb.W, xb.H, xb.N, b))
+        return NEUROSIM_OK;                       // not done: the gather form runs instead
+    const int runs = (Wo + umn::KT - 1) / umn::KT;
+    g.geom = umn::MnGeom{Ho, Wo, runs, xa.N * Ho * runs};
+    g.M = M;
+    g.N = N;
+    g.dw = dw;
+    g.err = h->err;
+    g.limit_ns = 2000000000ull;
+    h->launches += 1;
+    // one wave: two CTAs per SM fit with up to 64 gradient columns
+    ICUDA(umn::launch_mn_gemm<BN>(g, (BN <= 64 ? 2 : 1) * h->sms, h->stream));
+    *done = true;
+    return NEUROSIM_OK;
+}
+
+// dw[M x N] += sum over the pixel grid (batch, Ho, Wo) of A(m, p) B(n, p): A
+// is operand kind akind over the view xa (aC channels per tap, stride as),
+// B kind bkind over xb (bC channels).  Pixel runs narrower than 64 take the
+// gather GEMM `fallback` instead.
+template <class Fallback>
+int weight_grad(neurosim_interp* h, Act xa, int akind, int aC, int as, Act xb, int bkind, int bC, int Ho, int Wo,
+                float* dw, int M, int N, Fallback&& fallback)
+{
+    bool done = false;
+    int rc = NEUROSIM_OK;
+    if (Wo >= umn::KT && N % 16 == 0 && N <= 256) {
+        const umn::MnOp a{akind, aC, xa.off, as, M, umn::pick_sw(aC)};
+        const umn::MnOp b{bkind, bC, xb.off, 1, N, umn::pick_sw(bC)};
+        rc = N <= 16 ? dw_mn_bn<16>(h, xa, a, xb, b, Ho, Wo, dw, M, N, &done)
+             : N <= 32 ? dw_mn_bn<32>(h, xa, a, xb, b, Ho, Wo, dw, M, N, &done)
+             : N <= 64 ? dw_mn_bn<64>(h, xa, a, xb, b, Ho, Wo, dw, M, N, &done)
+             : N <= 128 ? dw_mn_bn<128>(h, xa, a, xb, b, Ho, Wo, dw, M, N, &done)
+                        : dw_mn_bn<256>(h, xa, a, xb, b, Ho, Wo, dw, M, N, &done);
+    }
+    if (rc || done) return rc;
+    ICUDA(fallback());
+    return NEUROSIM_OK;
+}
+
 int bias_grad(neurosim_interp* h, const bf16* g, int rows, int stride, int off, int C, int layer)
 {
     const int G = 256 / C;
@@ -585,54 +635,98 @@ int backward(neurosim_interp* h, const Shape& s)
     int rc;
     ICUDA(cudaMemsetAsync(G, 0, (size_t)L.total * sizeof(float), h->stream));
     // ---- final 1x1: W9, b9, d(d2)
-    ICUDA(gemm(h, PixMN{act(h->d2, N, H, W, 32, 0), 32, s.P}, PixMN{act(h->gr, N, H, W, 16, 0), 16, s.P},
-               EpiDW{G + L.w_off[8], 16}, 32, 16, s.P, true));
+    if ((rc = weight_grad(h, act(h->d2, N, H, W, 32, 0), umn::kPix, 32, 1, act(h->gr, N, H, W, 16, 0), umn::kPix, 16, H,
+                          W, G + L.w_off[8], 32, 16, [&] {
+                              return gemm(h, PixMN{act(h->d2, N, H, W, 32, 0), 32, s.P},
+                                          PixMN{act(h->gr, N, H, W, 16, 0), 16, s.P}, EpiDW{G + L.w_off[8], 16}, 32,
+                                          16, s.P, true);
+                          })))
+        return rc;
     if ((rc = bias_grad(h, h->gr, s.P, 16, 0, 16, 8))) return rc;
     ICUDA(gemm(h, PixK{act(h->gr, N, H, W, 16, 0), s.P}, ugemm::DenseK{h->wb[8], 32, 16},
                EpiGrad{h->gd2, 32, 0, h->d2, 32, 0, 0, 0}, s.P, 32, 16, false));
     // ---- conv8 (cat1 -> d2): W8, b8, d(cat1) (u2 linear, e1 masked)
-    ICUDA(gemm(h, Im2colMN{act(h->cat1, N, H, W, 64, 0), 64, H, W, 1, 576, s.P}, PixMN{act(h->gd2, N, H, W, 32, 0), 32, s.P},
-               EpiDW{G + L.w_off[7], 32}, 576, 32, s.P, true));
+    if ((rc = weight_grad(h, act(h->cat1, N, H, W, 64, 0), umn::kConv3, 64, 1, act(h->gd2, N, H, W, 32, 0), umn::kPix,
+                          32, H, W, G + L.w_off[7], 576, 32, [&] {
+                              return gemm(h, Im2colMN{act(h->cat1, N, H, W, 64, 0), 64, H, W, 1, 576, s.P},
+                                          PixMN{act(h->gd2, N, H, W, 32, 0), 32, s.P}, EpiDW{G + L.w_off[7], 32}, 576,
+                                          32, s.P, true);
+                          })))
+        return rc;
     if ((rc = bias_grad(h, h->gd2, s.P, 32, 0, 32, 7))) return rc;
     ICUDA(conv_tma(h, h->gd2, 32, 0, 32, 1, N, H, W, h->wb[7], 64, EpiGrad{h->gcat1, 64, 0, h->cat1, 64, 0, 32, 0}));
     // ---- convT2 (d1 -> u2): W7, b7, d(d1)
-    ICUDA(gemm(h, PixMN{act(h->d1, N, H2, W2, 64, 0), 64, s.P2}, S2DMN{act(h->gcat1, N, H, W, 64, 0), 32, H2, W2, 128, s.P2},
-               EpiDW{G + L.w_off[6], 128}, 64, 128, s.P2, true));
+    if ((rc = weight_grad(h, act(h->d1, N, H2, W2, 64, 0), umn::kPix, 64, 1, act(h->gcat1, N, H, W, 64, 0), umn::kS2D,
+                          32, H2, W2, G + L.w_off[6], 64, 128, [&] {
+                              return gemm(h, PixMN{act(h->d1, N, H2, W2, 64, 0), 64, s.P2},
+                                          S2DMN{act(h->gcat1, N, H, W, 64, 0), 32, H2, W2, 128, s.P2},
+                                          EpiDW{G + L.w_off[6], 128}, 64, 128, s.P2, true);
+                          })))
+        return rc;
     if ((rc = bias_grad(h, h->gcat1, s.P, 64, 0, 32, 6))) return rc;
     ICUDA(gemm(h, s2dk(act(h->gcat1, N, H, W, 64, 0), 32, H2, W2, s.P2), ugemm::DenseK{h->wb[6], 64, 128},
                EpiGrad{h->gd1, 64, 0, h->d1, 64, 0, 0, 0}, s.P2, 64, 128, false));
     // ---- conv6 (cat2 -> d1): W6, b6, d(cat2) (u1 linear, e2 masked)
-    ICUDA(gemm(h, Im2colMN{act(h->cat2, N, H2, W2, 128, 0), 128, H2, W2, 1, 1152, s.P2},
-               PixMN{act(h->gd1, N, H2, W2, 64, 0), 64, s.P2}, EpiDW{G + L.w_off[5], 64}, 1152, 64, s.P2, true));
+    if ((rc = weight_grad(h, act(h->cat2, N, H2, W2, 128, 0), umn::kConv3, 128, 1, act(h->gd1, N, H2, W2, 64, 0),
+                          umn::kPix, 64, H2, W2, G + L.w_off[5], 1152, 64, [&] {
+                              return gemm(h, Im2colMN{act(h->cat2, N, H2, W2, 128, 0), 128, H2, W2, 1, 1152, s.P2},
+                                          PixMN{act(h->gd1, N, H2, W2, 64, 0), 64, s.P2}, EpiDW{G + L.w_off[5], 64},
+                                          1152, 64, s.P2, true);
+                          })))
+        return rc;
     if ((rc = bias_grad(h, h->gd1, s.P2, 64, 0, 64, 5))) return rc;
     ICUDA(conv_tma(h, h->gd1, 64, 0, 64, 1, N, H2, W2, h->wb[5], 128, EpiGrad{h->gcat2, 128, 0, h->cat2, 128, 0, 64, 0}));
     // ---- convT1 (e4 -> u1): W5, b5, d(e4)
-    ICUDA(gemm(h, PixMN{act(h->e4, N, H4, W4, 128, 0), 128, s.P4},
-               S2DMN{act(h->gcat2, N, H2, W2, 128, 0), 64, H4, W4, 256, s.P4}, EpiDW{G + L.w_off[4], 256}, 128, 256,
-               s.P4, true));
+    if ((rc = weight_grad(h, act(h->e4, N, H4, W4, 128, 0), umn::kPix, 128, 1, act(h->gcat2, N, H2, W2, 128, 0),
+                          umn::kS2D, 64, H4, W4, G + L.w_off[4], 128, 256, [&] {
+                              return gemm(h, PixMN{act(h->e4, N, H4, W4, 128, 0), 128, s.P4},
+                                          S2DMN{act(h->gcat2, N, H2, W2, 128, 0), 64, H4, W4, 256, s.P4},
+                                          EpiDW{G + L.w_off[4], 256}, 128, 256, s.P4, true);
+                          })))
+        return rc;
     if ((rc = bias_grad(h, h->gcat2, s.P2, 128, 0, 64, 4))) return rc;
     ICUDA(gemm(h, s2dk(act(h->gcat2, N, H2, W2, 128, 0), 64, H4, W4, s.P4), ugemm::DenseK{h->wb[4], 128, 256},
                EpiGrad{h->ge4, 128, 0, h->e4, 128, 0, 0, 0}, s.P4, 128, 256, false));
     // ---- conv4 (e3 -> e4): W4, b4, d(e3)
-    ICUDA(gemm(h, Im2colMN{act(h->e3, N, H4, W4, 128, 0), 128, H4, W4, 1, 1152, s.P4},
-               PixMN{act(h->ge4, N, H4, W4, 128, 0), 128, s.P4}, EpiDW{G + L.w_off[3], 128}, 1152, 128, s.P4, true));
+    if ((rc = weight_grad(h, act(h->e3, N, H4, W4, 128, 0), umn::kConv3, 128, 1, act(h->ge4, N, H4, W4, 128, 0),
+                          umn::kPix, 128, H4, W4, G + L.w_off[3], 1152, 128, [&] {
+                              return gemm(h, Im2colMN{act(h->e3, N, H4, W4, 128, 0), 128, H4, W4, 1, 1152, s.P4},
+                                          PixMN{act(h->ge4, N, H4, W4, 128, 0), 128, s.P4},
+                                          EpiDW{G + L.w_off[3], 128}, 1152, 128, s.P4, true);
+                          })))
+        return rc;
     if ((rc = bias_grad(h, h->ge4, s.P4, 128, 0, 128, 3))) return rc;
     ICUDA(conv_tma(h, h->ge4, 128, 0, 128, 1, N, H4, W4, h->wb[3], 128, EpiGrad{h->ge3, 128, 0, h->e3, 128, 0, 0, 0}));
     // ---- conv3 (e2 -> e3, stride 2): W3, b3, d(e2) added into d(cat2)[:, 64:128]
-    ICUDA(gemm(h, Im2colMN{act(h->cat2, N, H2, W2, 128, 64), 64, H4, W4, 2, 576, s.P4},
-               PixMN{act(h->ge3, N, H4, W4, 128, 0), 128, s.P4}, EpiDW{G + L.w_off[2], 128}, 576, 128, s.P4, true));
+    if ((rc = weight_grad(h, act(h->cat2, N, H2, W2, 128, 64), umn::kConv3, 64, 2, act(h->ge3, N, H4, W4, 128, 0),
+                          umn::kPix, 128, H4, W4, G + L.w_off[2], 576, 128, [&] {
+                              return gemm(h, Im2colMN{act(h->cat2, N, H2, W2, 128, 64), 64, H4, W4, 2, 576, s.P4},
+                                          PixMN{act(h->ge3, N, H4, W4, 128, 0), 128, s.P4},
+                                          EpiDW{G + L.w_off[2], 128}, 576, 128, s.P4, true);
+                          })))
+        return rc;
     if ((rc = bias_grad(h, h->ge3, s.P4, 128, 0, 128, 2))) return rc;
     ICUDA(gemm(h, conv3tk(act(h->ge3, N, H4, W4, 128, 0), 128, H2, W2, 2, s.P2), ugemm::DenseK{h->wb[2], 64, 1152},
                EpiGrad{h->gcat2, 128, 64, h->cat2, 128, 64, 0, 1}, s.P2, 64, 1152, false));
     // ---- conv2 (e1 -> e2, stride 2): W2, b2, d(e1) added into d(cat1)[:, 32:64]
-    ICUDA(gemm(h, Im2colMN{act(h->cat1, N, H, W, 64, 32), 32, H2, W2, 2, 288, s.P2},
-               PixMN{act(h->gcat2, N, H2, W2, 128, 64), 64, s.P2}, EpiDW{G + L.w_off[1], 64}, 288, 64, s.P2, true));
+    if ((rc = weight_grad(h, act(h->cat1, N, H, W, 64, 32), umn::kConv3, 32, 2, act(h->gcat2, N, H2, W2, 128, 64),
+                          umn::kPix, 64, H2, W2, G + L.w_off[1], 288, 64, [&] {
+                              return gemm(h, Im2colMN{act(h->cat1, N, H, W, 64, 32), 32, H2, W2, 2, 288, s.P2},
+                                          PixMN{act(h->gcat2, N, H2, W2, 128, 64), 64, s.P2},
+                                          EpiDW{G + L.w_off[1], 64}, 288, 64, s.P2, true);
+                          })))
+        return rc;
     if ((rc = bias_grad(h, h->gcat2, s.P2, 128, 64, 64, 1))) return rc;
     ICUDA(gemm(h, conv3tk(act(h->gcat2, N, H2, W2, 128, 64), 64, H, W, 2, s.P), ugemm::DenseK{h->wb[1], 32, 576},
                EpiGrad{h->gcat1, 64, 32, h->cat1, 64, 32, 0, 1}, s.P, 32, 576, false));
     // ---- conv1 (x -> e1): W1, b1
-    ICUDA(gemm(h, Im2colMN{act(h->x0, N, H, W, 8, 0), 8, H, W, 1, 72, s.P}, PixMN{act(h->gcat1, N, H, W, 64, 32), 32, s.P},
-               EpiDW{G + L.w_off[0], 32}, 72, 32, s.P, true));
+    if ((rc = weight_grad(h, act(h->x0, N, H, W, 8, 0), umn::kConv3, 8, 1, act(h->gcat1, N, H, W, 64, 32), umn::kPix, 32,
+                          H, W, G + L.w_off[0], 72, 32, [&] {
+                              return gemm(h, Im2colMN{act(h->x0, N, H, W, 8, 0), 8, H, W, 1, 72, s.P},
+                                          PixMN{act(h->gcat1, N, H, W, 64, 32), 32, s.P}, EpiDW{G + L.w_off[0], 32},
+                                          72, 32, s.P, true);
+                          })))
+        return rc;
     if ((rc = bias_grad(h, h->gcat1, s.P, 64, 32, 32, 0))) return rc;
     return NEUROSIM_OK;
 }

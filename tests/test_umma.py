@@ -29,14 +29,14 @@ def _gemm(mode, A, B, M, N, K):
     return c.cpu()
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (304, 256, 200), (77, 48, 136)])
-@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (304, 256, 200), (77, 48, 136), (96, 32, 192), (64, 16, 136)])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4, 5, 6])
 def test_gemm_layouts(mode, M, N, K):
     g = torch.Generator().manual_seed(M * 1000 + N * 10 + K + mode)
     A = torch.randn(M, K, generator=g).to(torch.bfloat16).float()
     B = torch.randn(N, K, generator=g).to(torch.bfloat16).float()
     ref = (A.double() @ B.double().T).float()
-    a_mn, b_mn = mode in (1, 3), mode in (2, 3)     # modes 4 and 5 (TMA) are K-major
+    a_mn, b_mn = mode in (1, 3, 6), mode in (2, 3, 6)     # modes 4 and 5 (TMA) are K-major
     a_in = A.T.contiguous() if a_mn else A
     b_in = B.T.contiguous() if b_mn else B
     if (a_mn and M % 8) or (b_mn and N % 8):
