@@ -367,6 +367,65 @@ cudaError_t conv_tma_bn(neurosim_interp* h, const bf16* buf, int cstride, int of
     return utma::launch_tma_gemm<BN, SW>(g, N * tx * ty, h->stream);
 }
 
+// Data gradient of a 3x3 stride-2 convolution: g (Cout channels at `off` of
+// rows of `cstride`, Ho x Wo per image) through the packed backward weights
+// [cin][tap * Cout + o] into the input-size epilogue, as four tcgen05 GEMMs,
+// one per parity class of the input pixels (ParityTapA): every product is
+// one of the convolution's, none is a zero of the stride.
+template <int BN, class EP>
+cudaError_t conv_s2_dgrad_bn(neurosim_interp* h, const bf16* g, int cstride, int off, int Cout, int N, int Ho, int Wo,
+                             const bf16* wpacked, int n_out, const EP& ep)
+{
+    constexpr int SW = 128, BKS = utma::bk_of(SW);
+    if (Cout % BKS) return cudaErrorInvalidValue;
+    int TW = 128, TH = 1;
+    pick_tile(Wo, Ho, &TW, &TH);
+    const int tx = (Wo + TW - 1) / TW, ty = (Ho + TH - 1) / TH;
+    utma::TmaArgs<utma::ParityTapA, EP> a;
+    const cuuint64_t dims[4] = {(cuuint64_t)cstride, (cuuint64_t)Wo, (cuuint64_t)Ho, (cuuint64_t)N};
+    const cuuint64_t strides[3] = {(cuuint64_t)cstride * 2u, (cuuint64_t)Wo * cstride * 2u,
+                                   (cuuint64_t)Ho * Wo * cstride * 2u};
+    const cuuint32_t box[4] = {(cuuint32_t)BKS, (cuuint32_t)TW, (cuuint32_t)TH, 1u};
+    if (!utma::encode_tiled(&a.ta, 4, g, dims, strides, box, SW) ||
+        !utma::encode_kmajor(&a.tb, wpacked, n_out, 9 * Cout, BN, SW))
+        return cudaErrorInvalidValue;
+    a.ep = ep;
+    a.N = n_out;
+    a.err = h->err;
+    a.limit_ns = 2000000000ull;
+    for (int py = 0; py < 2; ++py)
+        for (int px = 0; px < 2; ++px) {
+            utma::ParityTapA& L = a.a;
+            L = utma::ParityTapA{};
+            L.Cout = Cout;
+            L.off = off;
+            L.Wo = Wo;
+            L.Ho = Ho;
+            L.N = N;
+            L.py = py;
+            L.px = px;
+            L.TW = TW;
+            L.TH = TH;
+            L.tiles_x = tx;
+            L.tiles_y = ty;
+            L.bk = BKS;
+            // taps of the class: dy = 1 (oy 0) for py = 0; dy = 0 (oy 1), 2 (oy 0) for py = 1
+            const int ndy = py ? 2 : 1, ndx = px ? 2 : 1;
+            for (int i = 0; i < ndy; ++i)
+                for (int j = 0; j < ndx; ++j) {
+                    const int dy = py ? 2 * i : 1, dx = px ? 2 * j : 1;
+                    L.tap[L.ntaps] = 3 * dy + dx;
+                    L.oy[L.ntaps] = (py && dy == 0) ? 1 : 0;
+                    L.ox[L.ntaps] = (px && dx == 0) ? 1 : 0;
+                    ++L.ntaps;
+                }
+            h->launches += 1;
+            const cudaError_t e = utma::launch_tma_gemm<BN, SW>(a, N * tx * ty, h->stream);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
 // out = conv3x3 (stride 1) of the view [off, off + C) of `buf` from halo
 // tiles of 128-pixel rows (W >= 128; C 8 (forward), 32 with a 64-byte swizzle
 // of the weights, or 64 with a 128-byte swizzle).
@@ -706,8 +765,8 @@ int backward(neurosim_interp* h, const Shape& s)
                           })))
         return rc;
     if ((rc = bias_grad(h, h->ge3, s.P4, 128, 0, 128, 2))) return rc;
-    ICUDA(gemm(h, conv3tk(act(h->ge3, N, H4, W4, 128, 0), 128, H2, W2, 2, s.P2), ugemm::DenseK{h->wb[2], 64, 1152},
-               EpiGrad{h->gcat2, 128, 64, h->cat2, 128, 64, 0, 1}, s.P2, 64, 1152, false));
+    ICUDA((conv_s2_dgrad_bn<64>(h, h->ge3, 128, 0, 128, N, H4, W4, h->wb[2], 64,
+                                EpiGrad{h->gcat2, 128, 64, h->cat2, 128, 64, 0, 1})));
     // ---- conv2 (e1 -> e2, stride 2): W2, b2, d(e1) added into d(cat1)[:, 32:64]
     if ((rc = weight_grad(h, act(h->cat1, N, H, W, 64, 32), umn::kConv3, 32, 2, act(h->gcat2, N, H2, W2, 128, 64),
                           umn::kPix, 64, H2, W2, G + L.w_off[1], 288, 64, [&] {
@@ -717,8 +776,8 @@ int backward(neurosim_interp* h, const Shape& s)
                           })))
         return rc;
     if ((rc = bias_grad(h, h->gcat2, s.P2, 128, 64, 64, 1))) return rc;
-    ICUDA(gemm(h, conv3tk(act(h->gcat2, N, H2, W2, 128, 64), 64, H, W, 2, s.P), ugemm::DenseK{h->wb[1], 32, 576},
-               EpiGrad{h->gcat1, 64, 32, h->cat1, 64, 32, 0, 1}, s.P, 32, 576, false));
+    ICUDA((conv_s2_dgrad_bn<32>(h, h->gcat2, 128, 64, 64, N, H2, W2, h->wb[1], 32,
+                                EpiGrad{h->gcat1, 64, 32, h->cat1, 64, 32, 0, 1})));
     // ---- conv1 (x -> e1): W1, b1
     if ((rc = weight_grad(h, act(h->x0, N, H, W, 8, 0), umn::kConv3, 8, 1, act(h->gcat1, N, H, W, 64, 32), umn::kPix, 32,
                           H, W, G + L.w_off[0], 72, 32, [&] {

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <utility>
 
 #include "umma.cuh"
 
@@ -182,6 +183,64 @@ struct ConvTapA {
     }
 };
 
+// Data gradient of a 3 x 3 stride-2 convolution with padding 1, for the
+// input pixels of one parity class (py, px).  Input pixel (2a + py, 2b + px)
+// receives tap (dy, dx) of the output gradient at (a + oy, b + ox): for py = 0
+// only dy = 1 (oy = 0), for py = 1 dy = 0 (oy = 1) and dy = 2 (oy = 0); the
+// same along x.  So the classes hold 1, 2, 2 and 4 of the 9 taps and no
+// product is a structural zero.  Output tile = TW x TH pixels (a, b) of the
+// gradient's grid; K tile = (class tap t, bk-channel chunk).  4-D map of the
+// gradient (channels of the buffer, Wo, Ho, N), box bk x TW x TH x 1; B (the
+// packed [cin][tap * Cout + o] weights) is read at column tap * Cout + chunk.
+struct ParityTapA {
+    int Cout, off;        // gradient channels and their offset in the buffer
+    int Wo, Ho, N;        // gradient grid (the convolution's output)
+    int py, px;           // parity class of the input pixels written
+    int TW, TH, tiles_x, tiles_y;
+    int bk;
+    int ntaps;
+    int tap[4], ox[4], oy[4];
+    __host__ __device__ __forceinline__ int n_kt() const { return ntaps * (Cout / bk); }
+    __device__ __forceinline__ void origin(int tile, int& n, int& x0, int& y0) const
+    {
+        const int per = tiles_x * tiles_y;
+        n = tile / per;
+        const int rem = tile - n * per;
+        const int ty = rem / tiles_x;
+        y0 = ty * TH;
+        x0 = (rem - ty * tiles_x) * TW;
+    }
+    __device__ __forceinline__ void load(void* dst, const CUtensorMap* map, int tile, int kt, uint64_t* mbar) const
+    {
+        int n, x0, y0;
+        origin(tile, n, x0, y0);
+        const int cc = Cout / bk;
+        const int t = kt / cc, c = kt - t * cc;
+        tma_load_4d(dst, map, off + c * bk, x0 + ox[t], y0 + oy[t], n, mbar);
+    }
+    __device__ __forceinline__ int b_col(int kt) const
+    {
+        const int cc = Cout / bk;
+        const int t = kt / cc, c = kt - t * cc;
+        return tap[t] * Cout + c * bk;
+    }
+    __device__ __forceinline__ int row_of(int tile, int r) const
+    {
+        int n, x0, y0;
+        origin(tile, n, x0, y0);
+        const int ty = r / TW, b = x0 + (r - ty * TW), a = y0 + ty;
+        return (a < Ho && b < Wo) ? (n * 2 * Ho + 2 * a + py) * (2 * Wo) + 2 * b + px : -1;
+    }
+    __device__ __forceinline__ bool warp_rows(int, int, int&, int&) const { return false; }
+};
+
+// B column of K tile kt: the loader's b_col where it has one, else kt x the
+// stage's K.
+template <class AL, class = void>
+struct al_bcol : std::false_type {};
+template <class AL>
+struct al_bcol<AL, std::void_t<decltype(std::declval<const AL&>().b_col(0))>> : std::true_type {};
+
 // Epilogue of one accumulator row: 32 columns per TMEM load (one wait), then
 // the epilogue functor on 8 columns at a time, unrolled so that the global
 // loads some functors make (masks, accumulation) are in flight together.
@@ -329,7 +388,10 @@ __global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ T
             }
             mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
             g.a.load(sA + s * A_BYTES, &g.ta, tile, kt, &full[s]);
-            tma_load_2d(sB + s * B_BYTES, &g.tb, kt * SBK, 0, &full[s]);
+            if constexpr (al_bcol<AL>::value)
+                tma_load_2d(sB + s * B_BYTES, &g.tb, g.a.b_col(kt), 0, &full[s]);
+            else
+                tma_load_2d(sB + s * B_BYTES, &g.tb, kt * SBK, 0, &full[s]);
         }
     } else if (tid == 32) {
         // MMA issuer
