@@ -7,10 +7,11 @@
 //
 //   forward   conv 3x3 (stride 1 or 2):  D[pixel][cout] = im2col(x) * W
 //             convT 2x2 stride 2:        D[in pixel][(a, b, cout)] = x * W
-//   backward  data of conv:  D[in pixel][cin]  = "transposed im2col"(dy) * W^T
-//             data of convT: D[in pixel][cin]  = space-to-depth(dy) * W^T
+//   backward  data of the final 1x1 layer: D[pixel][cin] = dy * W^T
 //             weights:       D[(tap, cin)][cout] = sum over pixels (split over
-//                            the grid's y dimension, FP32 atomics)
+//                            the grid's y dimension, FP32 atomics), where the
+//                            pixel runs are too short for the TMA form
+// (the other data gradients run on TMA-fed kernels: umma_tma.cuh)
 #pragma once
 
 #include <cuda_bf16.h>
@@ -94,60 +95,6 @@ struct Conv3K {
     }
 };
 
-// data gradient of a conv 3x3 of stride s: row (n, y, x) at the conv's input
-// size, k = tap * C + c reads dy(n, (y + 1 - dy) / s, (x + 1 - dx) / s, c)
-// where the division is exact (else zero).
-struct Conv3TK {
-    static constexpr bool MN = false;
-    Act g;              // gradient of the conv's output (size Ho x Wo)
-    int C, Hi, Wi, s, M;
-    int cshift;
-    template <int R>
-    struct Rows {
-        int nH[kRowsPerThread(R)];     // n * Ho, or -1 for rows past M
-        int y1[kRowsPerThread(R)];     // y + 1
-        int x1[kRowsPerThread(R)];     // x + 1
-    };
-    template <int R>
-    __device__ __forceinline__ void prep(Rows<R>& rw, int r0, int tid) const
-    {
-        const int hw = Hi * Wi;
-#pragma unroll
-        for (int j = 0; j < kRowsPerThread(R); ++j) {
-            const int m = r0 + (tid >> 3) + 16 * j;
-            if (m < M) {
-                const int n = m / hw, rem = m - n * hw, y = rem / Wi, xx = rem - y * Wi;
-                rw.nH[j] = n * g.H;
-                rw.y1[j] = y + 1;
-                rw.x1[j] = xx + 1;
-            } else {
-                rw.nH[j] = -1;
-                rw.y1[j] = rw.x1[j] = 0;
-            }
-        }
-    }
-    template <int R>
-    __device__ __forceinline__ void gather(unsigned char* tile, const Rows<R>& rw, int, int k0, int kn, int tid) const
-    {
-        const int kc = tid & 7, k = k0 + kc * 8;
-        const int tap = k >> cshift, c = k & (C - 1);
-        const int dy = tap / 3, dx = tap - 3 * dy;
-        const bool kok = kc * 8 < kn;
-        const int smask = s - 1, sshift = s == 2 ? 1 : 0;
-#pragma unroll
-        for (int j = 0; j < kRowsPerThread(R); ++j) {
-            const int r = (tid >> 3) + 16 * j;
-            const int ty = rw.y1[j] - dy, tx = rw.x1[j] - dx;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (kok && rw.nH[j] >= 0 && ty >= 0 && tx >= 0 && !(ty & smask) && !(tx & smask)) {
-                const int yo = ty >> sshift, xo = tx >> sshift;
-                if (yo < g.H && xo < g.W) v = ld16(g.p + ((size_t)(rw.nH[j] + yo) * g.W + xo) * g.stride + g.off + c);
-            }
-            st_chunk(tile, kmajor_chunk(r, kc * 8), v);
-        }
-    }
-};
-
 // 1x1: row = pixel, k = channel.
 struct PixK {
     static constexpr bool MN = false;
@@ -164,49 +111,6 @@ struct PixK {
             const int r = (tid >> 3) + 16 * j, m = r0 + r;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if (kok && m < M) v = ld16(x.p + (size_t)m * x.stride + x.off + k0 + kc * 8);
-            st_chunk(tile, kmajor_chunk(r, kc * 8), v);
-        }
-    }
-};
-
-// data gradient of a convT 2x2 stride 2: row (n, y, x) at the low size,
-// k = (2a + b) * C + c reads g(n, 2y + a, 2x + b, c).
-struct S2DK {
-    static constexpr bool MN = false;
-    Act g;              // full-size gradient
-    int C, Hl, Wl, M;
-    int cshift;
-    template <int R>
-    struct Rows {
-        int pix[kRowsPerThread(R)];    // full-size pixel index of (n, 2y, 2x), or -1 past M
-    };
-    template <int R>
-    __device__ __forceinline__ void prep(Rows<R>& rw, int r0, int tid) const
-    {
-        const int hw = Hl * Wl;
-#pragma unroll
-        for (int j = 0; j < kRowsPerThread(R); ++j) {
-            const int m = r0 + (tid >> 3) + 16 * j;
-            if (m < M) {
-                const int n = m / hw, rem = m - n * hw, y = rem / Wl, xx = rem - y * Wl;
-                rw.pix[j] = (n * g.H + 2 * y) * g.W + 2 * xx;
-            } else {
-                rw.pix[j] = -1;
-            }
-        }
-    }
-    template <int R>
-    __device__ __forceinline__ void gather(unsigned char* tile, const Rows<R>& rw, int, int k0, int kn, int tid) const
-    {
-        const int kc = tid & 7, k = k0 + kc * 8;
-        const int ab = k >> cshift, c = k & (C - 1);
-        const int dpix = (ab >> 1) * g.W + (ab & 1);
-        const bool kok = kc * 8 < kn;
-#pragma unroll
-        for (int j = 0; j < kRowsPerThread(R); ++j) {
-            const int r = (tid >> 3) + 16 * j;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (kok && rw.pix[j] >= 0) v = ld16(g.p + (size_t)(rw.pix[j] + dpix) * g.stride + g.off + c);
             st_chunk(tile, kmajor_chunk(r, kc * 8), v);
         }
     }

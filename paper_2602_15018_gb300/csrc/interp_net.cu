@@ -367,6 +367,38 @@ cudaError_t conv_tma_bn(neurosim_interp* h, const bf16* buf, int cstride, int of
     return utma::launch_tma_gemm<BN, SW>(g, N * tx * ty, h->stream);
 }
 
+// Data gradient of a 2x2 stride-2 transposed convolution: g (Cout channels at
+// `off` of rows of `cstride`, 2H x 2W per image) through the packed backward
+// weights [cin][ab * Cout + o] into the low-resolution epilogue (H x W), one
+// TMA GEMM over the four sub-positions (S2DTapA).  Cout: 32 (64-byte swizzle)
+// or a multiple of 64.
+template <int BN, int SW, class EP>
+cudaError_t convt_dgrad_bn(neurosim_interp* h, const bf16* g, int cstride, int off, int Cout, int N, int H, int W,
+                           const bf16* wpacked, int n_out, const EP& ep)
+{
+    constexpr int BKS = utma::bk_of(SW);
+    if (Cout % BKS) return cudaErrorInvalidValue;
+    int TW = 128, TH = 1;
+    pick_tile(W, H, &TW, &TH);
+    utma::TmaArgs<utma::S2DTapA, EP> a;
+    const cuuint64_t dims[4] = {(cuuint64_t)cstride, (cuuint64_t)(2 * W), (cuuint64_t)(2 * H), (cuuint64_t)N};
+    const cuuint64_t strides[3] = {(cuuint64_t)cstride * 2u, (cuuint64_t)(2 * W) * cstride * 2u,
+                                   (cuuint64_t)(4 * H * W) * cstride * 2u};
+    const cuuint32_t box[4] = {(cuuint32_t)BKS, (cuuint32_t)(2 * TW), (cuuint32_t)(2 * TH), 1u};
+    const cuuint32_t estr[4] = {1u, 2u, 2u, 1u};
+    if (!utma::encode_tiled(&a.ta, 4, g, dims, strides, box, SW, estr) ||
+        !utma::encode_kmajor(&a.tb, wpacked, n_out, 4 * Cout, BN, SW))
+        return cudaErrorInvalidValue;
+    const int tx = (W + TW - 1) / TW, ty = (H + TH - 1) / TH;
+    a.a = utma::S2DTapA{Cout, off, W, H, N, TW, TH, tx, ty, BKS};
+    a.ep = ep;
+    a.N = n_out;
+    a.err = h->err;
+    a.limit_ns = 2000000000ull;
+    h->launches += 1;
+    return utma::launch_tma_gemm<BN, SW>(a, N * tx * ty, h->stream);
+}
+
 // Data gradient of a 3x3 stride-2 convolution: g (Cout channels at `off` of
 // rows of `cstride`, Ho x Wo per image) through the packed backward weights
 // [cin][tap * Cout + o] into the input-size epilogue, as four tcgen05 GEMMs,
@@ -574,8 +606,6 @@ int log2i(int c)
     return k;
 }
 Conv3K conv3k(Act x, int C, int Ho, int Wo, int s, int M) { return Conv3K{x, C, Ho, Wo, s, M, log2i(C)}; }
-Conv3TK conv3tk(Act g, int C, int Hi, int Wi, int s, int M) { return Conv3TK{g, C, Hi, Wi, s, M, log2i(C)}; }
-S2DK s2dk(Act g, int C, int Hl, int Wl, int M) { return S2DK{g, C, Hl, Wl, M, log2i(C)}; }
 
 const float* bias_of(const neurosim_interp* h, int l) { return h->params + h->lay.b_off[l]; }
 
@@ -723,8 +753,8 @@ int backward(neurosim_interp* h, const Shape& s)
                           })))
         return rc;
     if ((rc = bias_grad(h, h->gcat1, s.P, 64, 0, 32, 6))) return rc;
-    ICUDA(gemm(h, s2dk(act(h->gcat1, N, H, W, 64, 0), 32, H2, W2, s.P2), ugemm::DenseK{h->wb[6], 64, 128},
-               EpiGrad{h->gd1, 64, 0, h->d1, 64, 0, 0, 0}, s.P2, 64, 128, false));
+    ICUDA((convt_dgrad_bn<64, 64>(h, h->gcat1, 64, 0, 32, N, H2, W2, h->wb[6], 64,
+                                  EpiGrad{h->gd1, 64, 0, h->d1, 64, 0, 0, 0})));
     // ---- conv6 (cat2 -> d1): W6, b6, d(cat2) (u1 linear, e2 masked)
     if ((rc = weight_grad(h, act(h->cat2, N, H2, W2, 128, 0), umn::kConv3, 128, 1, act(h->gd1, N, H2, W2, 64, 0),
                           umn::kPix, 64, H2, W2, G + L.w_off[5], 1152, 64, [&] {
@@ -744,8 +774,8 @@ int backward(neurosim_interp* h, const Shape& s)
                           })))
         return rc;
     if ((rc = bias_grad(h, h->gcat2, s.P2, 128, 0, 64, 4))) return rc;
-    ICUDA(gemm(h, s2dk(act(h->gcat2, N, H2, W2, 128, 0), 64, H4, W4, s.P4), ugemm::DenseK{h->wb[4], 128, 256},
-               EpiGrad{h->ge4, 128, 0, h->e4, 128, 0, 0, 0}, s.P4, 128, 256, false));
+    ICUDA((convt_dgrad_bn<128, 128>(h, h->gcat2, 128, 0, 64, N, H4, W4, h->wb[4], 128,
+                                    EpiGrad{h->ge4, 128, 0, h->e4, 128, 0, 0, 0})));
     // ---- conv4 (e3 -> e4): W4, b4, d(e3)
     if ((rc = weight_grad(h, act(h->e3, N, H4, W4, 128, 0), umn::kConv3, 128, 1, act(h->ge4, N, H4, W4, 128, 0),
                           umn::kPix, 128, H4, W4, G + L.w_off[3], 1152, 128, [&] {

@@ -183,6 +183,55 @@ struct ConvTapA {
     }
 };
 
+// Data gradient of a 2 x 2 stride-2 transposed convolution: low-resolution
+// pixel (y, x) takes sub-position (a, b) of the output gradient at
+// (2y + a, 2x + b).  Output tile = TW x TH low-resolution pixels of one image;
+// K tile = (sub-position ab = 2a + b, bk-channel chunk) of the gradient view
+// [off, off + Cout).  4-D map of the gradient (channels of the buffer, 2 W,
+// 2 H, N), box bk x 2 TW x 2 TH x 1 with traversal stride 2 in W and H, so
+// that one box holds TW x TH pixels.  B is the packed [cin][ab * Cout + o].
+struct S2DTapA {
+    int Cout, off;
+    int W, H, N;          // low-resolution size (the data gradient's)
+    int TW, TH, tiles_x, tiles_y;
+    int bk;
+    __host__ __device__ __forceinline__ int n_kt() const { return 4 * (Cout / bk); }
+    __device__ __forceinline__ void origin(int tile, int& n, int& x0, int& y0) const
+    {
+        const int per = tiles_x * tiles_y;
+        n = tile / per;
+        const int rem = tile - n * per;
+        const int ty = rem / tiles_x;
+        y0 = ty * TH;
+        x0 = (rem - ty * tiles_x) * TW;
+    }
+    __device__ __forceinline__ void load(void* dst, const CUtensorMap* map, int tile, int kt, uint64_t* mbar) const
+    {
+        int n, x0, y0;
+        origin(tile, n, x0, y0);
+        const int cc = Cout / bk;
+        const int ab = kt / cc, c = off + (kt - ab * cc) * bk;
+        tma_load_4d(dst, map, c, 2 * x0 + (ab & 1), 2 * y0 + (ab >> 1), n, mbar);
+    }
+    __device__ __forceinline__ int row_of(int tile, int r) const
+    {
+        int n, x0, y0;
+        origin(tile, n, x0, y0);
+        const int ty = r / TW, x = x0 + (r - ty * TW), y = y0 + ty;
+        return (x < W && y < H) ? (n * H + y) * W + x : -1;
+    }
+    __device__ __forceinline__ bool warp_rows(int tile, int w, int& row0, int& n_valid) const
+    {
+        if (TW % 32 != 0) return false;
+        int n, x0, y0;
+        origin(tile, n, x0, y0);
+        const int r = 32 * w, ty = r / TW, x = x0 + (r - ty * TW), y = y0 + ty;
+        row0 = (n * H + y) * W + x;
+        n_valid = y < H ? W - x : 0;
+        return true;
+    }
+};
+
 // Data gradient of a 3 x 3 stride-2 convolution with padding 1, for the
 // input pixels of one parity class (py, px).  Input pixel (2a + py, 2b + px)
 // receives tap (dy, dx) of the output gradient at (a + oy, b + ox): for py = 0
