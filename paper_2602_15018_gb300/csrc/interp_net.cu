@@ -680,6 +680,31 @@ int dw_mn_bn(neurosim_interp* h, const Act& xa, const umn::MnOp& a, const Act& x
     return NEUROSIM_OK;
 }
 
+// The halo form for 3x3 stride-1 convolutions over 64-channel parts with up
+// to 64 gradient columns: all 9 taps of a part from one halo per pixel run.
+template <int BN>
+int dw_halo_bn(neurosim_interp* h, const Act& xa, int C, const Act& xb, const umn::MnOp& b, int Ho, int Wo, float* dw,
+               int N, bool* done)
+{
+    umn::MnHaloArgs<BN> g;
+    if (!umn::encode_halo(&g.ta, xa.p, xa.stride, xa.W, xa.H, xa.N) ||
+        !umn::encode_op(&g.tb, xb.p, xb.stride, xb.W, xb.H, xb.N, b))
+        return NEUROSIM_OK;
+    const int runs = (Wo + umn::KT - 1) / umn::KT;
+    g.C = C;
+    g.off = xa.off;
+    g.b = b;
+    g.geom = umn::MnGeom{Ho, Wo, runs, xa.N * Ho * runs};
+    g.N = N;
+    g.dw = dw;
+    g.err = h->err;
+    g.limit_ns = 2000000000ull;
+    h->launches += 1;
+    ICUDA(umn::launch_mn_halo<BN>(g, h->sms, h->stream));
+    *done = true;
+    return NEUROSIM_OK;
+}
+
 // dw[M x N] += sum over the pixel grid (batch, Ho, Wo) of A(m, p) B(n, p): A
 // is operand kind akind over the view xa (aC channels per tap, stride as),
 // B kind bkind over xb (bC channels).  Pixel runs narrower than 64 take the
@@ -693,6 +718,10 @@ int weight_grad(neurosim_interp* h, Act xa, int akind, int aC, int as, Act xb, i
     if (Wo >= umn::KT && N % 16 == 0 && N <= 256) {
         const umn::MnOp a{akind, aC, xa.off, as, M, umn::pick_sw(aC)};
         const umn::MnOp b{bkind, bC, xb.off, 1, N, umn::pick_sw(bC)};
+        if (akind == umn::kConv3 && as == 1 && aC % 64 == 0 && bkind == umn::kPix && N <= 64)
+            rc = N <= 32 ? dw_halo_bn<32>(h, xa, aC, xb, b, Ho, Wo, dw, N, &done)
+                         : dw_halo_bn<64>(h, xa, aC, xb, b, Ho, Wo, dw, N, &done);
+        if (rc || done) return rc;
         rc = N <= 16 ? dw_mn_bn<16>(h, xa, a, xb, b, Ho, Wo, dw, M, N, &done)
              : N <= 32 ? dw_mn_bn<32>(h, xa, a, xb, b, Ho, Wo, dw, M, N, &done)
              : N <= 64 ? dw_mn_bn<64>(h, xa, a, xb, b, Ho, Wo, dw, M, N, &done)

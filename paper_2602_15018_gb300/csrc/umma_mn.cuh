@@ -213,7 +213,16 @@ __global__ void __launch_bounds__(128) mn_gemm_kernel(const __grid_constant__ Mn
             }
         }
     } else if (tid == 32) {
-        // MMA issuer
+        // MMA issuer: the descriptors of stage 0, once; a stage adds its
+        // offset to the start-address field (no carry: shared addresses are
+        // below 256 KB)
+        const uint32_t base = umma::smem_u32(smem);
+        uint64_t da[KT / 16], db[KT / 16];
+#pragma unroll
+        for (int k = 0; k < KT / 16; ++k) {
+            da[k] = desc_mn(base, g.a.sw, k);
+            db[k] = desc_mn(base + A_BYTES, g.b.sw, k);
+        }
         for (int i = 0; i < n_kt; ++i) {
             const int s = i % ns;
             if (!umma::mbar_wait(&full[s], (uint32_t)((i / ns) & 1), g.limit_ns)) {
@@ -221,11 +230,10 @@ __global__ void __launch_bounds__(128) mn_gemm_kernel(const __grid_constant__ Mn
                 break;
             }
             umma::fence_after_sync();
-            const uint32_t a0 = umma::smem_u32(smem + (size_t)s * STAGE), b0 = a0 + A_BYTES;
+            const uint64_t off = (uint64_t)(((uint32_t)s * STAGE) >> 4);
 #pragma unroll
             for (int k = 0; k < KT / 16; ++k)
-                umma::mma_bf16(tmem, desc_mn(a0, g.a.sw, k), desc_mn(b0, g.b.sw, k), idesc,
-                               (i > 0 || k > 0) ? 1u : 0u);
+                umma::mma_bf16(tmem, da[k] + off, db[k] + off, idesc, (i > 0 || k > 0) ? 1u : 0u);
             umma::mma_commit(&empty[s]);
         }
         umma::mma_commit(done);
@@ -288,6 +296,204 @@ cudaError_t launch_mn_gemm(MnArgs<BN>& g, int ctas, cudaStream_t stream)
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)mt, (unsigned)(splits > 0 ? splits : 1));
     mn_gemm_kernel<BN><<<grid, 128, mn_smem_bytes<BN>(ns), stream>>>(g);
+    return cudaGetLastError();
+}
+
+}  // namespace umn
+
+namespace umn {
+
+// ---- weight gradient of a 3x3 stride-1 convolution from a halo -----------------------
+// D rows (tap, c) for one 64-channel part cp of the input view, all 9 taps,
+// against B = the output gradient (BN <= 64 channels, pixel boxes).  Per K
+// tile (64 output pixels of row y) one TMA box brings the input rows
+// y - 1 .. y + 1, pixels x0 - 1 .. x0 + 70, 64 channels: 3 x 72 rows of
+// 128 bytes, 128-byte swizzle.  The operand of tap (dy, dx) is that halo
+// from row dy * 72 + dx on: an MN-major operand whose 8-pixel groups are
+// 1024 B apart, starting inside a swizzle atom (the tensor core swizzles by
+// address, as the TMA wrote it).  Taps are paired into M = 128 MMAs: the
+// second tap is the second MN atom, at a leading byte offset equal to the
+// distance between the two taps' first rows.  Tap 8 pairs with the halo
+// shifted one more pixel, whose rows the epilogue drops.  Five FP32
+// accumulators of BN columns stay in TMEM for the CTA's whole K slice.
+constexpr int kHaloRows = 72;                       // pixels x0 - 1 .. x0 + 70 of a halo row
+constexpr uint32_t kHaloBytes = 3u * kHaloRows * 128u;
+
+template <int BN>
+struct MnHaloArgs {
+    CUtensorMap ta, tb;
+    int C, off;            // input view: C channels (multiple of 64) at `off`
+    MnOp b;                // output gradient (kPix), rows = BN
+    MnGeom geom;
+    int N;                 // gradient columns (<= BN)
+    int kt_per_split;
+    float* dw;             // [(tap, c)][N]
+    unsigned int* err;
+    uint64_t limit_ns;
+};
+
+template <int BN>
+__host__ __device__ constexpr size_t mn_halo_stage_bytes()
+{
+    return (size_t)kHaloBytes + (size_t)BN * KT * 2;
+}
+
+template <int BN>
+__host__ __device__ constexpr size_t mn_halo_smem_bytes(int ns = STAGES)
+{
+    return 1024 + (size_t)ns * mn_halo_stage_bytes<BN>() + 256 + 8192;
+}
+
+__device__ __forceinline__ uint32_t tap_row(int t) { return (uint32_t)((t / 3) * kHaloRows + t % 3); }
+
+template <int BN>
+__global__ void __launch_bounds__(128) mn_halo_kernel(const __grid_constant__ MnHaloArgs<BN> g)
+{
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 64, "five accumulators of BN columns in 512 TMEM columns");
+    constexpr uint32_t TCOLS = 5 * BN <= 256 ? 256 : 512;
+    constexpr uint32_t STAGE = (uint32_t)mn_halo_stage_bytes<BN>();
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024u - (umma::smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int cp = blockIdx.x;                   // 64-channel part of the input view
+    const int kb = blockIdx.y * g.kt_per_split;
+    const int ke = min(g.geom.n_kt, kb + g.kt_per_split);
+    const int n_kt = ke > kb ? ke - kb : 0;
+    if (n_kt == 0) return;
+    const int ns = n_kt < STAGES ? n_kt : STAGES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)ns * STAGE);
+    uint64_t* empty = full + ns;
+    uint64_t* done = empty + ns;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ unsigned int s_fail;
+
+    if (tid == 0) {
+        for (int s = 0; s < ns; ++s) {
+            umma::mbar_init(&full[s], 1);
+            umma::mbar_init(&empty[s], 1);
+        }
+        umma::mbar_init(done, 1);
+        s_fail = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) umma::tmem_alloc(tslot, TCOLS);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(BM, BN, true, true);
+
+    if (tid == 0) {
+        const int nbp = (BN + g.b.cb() - 1) / g.b.cb();
+        const uint32_t pb = g.b.part_bytes();
+        const int nb = (g.b.rows + g.b.cb() - 1) / g.b.cb() < nbp ? (g.b.rows + g.b.cb() - 1) / g.b.cb() : nbp;
+        const uint32_t bytes = kHaloBytes + (uint32_t)nb * pb;
+        int xb = kb % g.geom.xblocks, y = (kb / g.geom.xblocks) % g.geom.Ho, n = kb / g.geom.xblocks / g.geom.Ho;
+        for (int i = 0; i < n_kt; ++i) {
+            const int s = i % ns;
+            if (i >= ns && !umma::mbar_wait(&empty[s], (uint32_t)((i / ns - 1) & 1), g.limit_ns)) {
+                atomicOr(&s_fail, 1u);
+                break;
+            }
+            unsigned char* st = smem + (size_t)s * STAGE;
+            utma::mbar_expect_tx(&full[s], bytes);
+            const int x0 = xb * KT;
+            utma::tma_load_4d(st, &g.ta, g.off + cp * 64, x0 - 1, y - 1, n, &full[s]);
+            for (int j = 0; j < nb; ++j)
+                utma::tma_load_4d(st + kHaloBytes + (size_t)j * pb, &g.tb, g.b.off + j * g.b.cb(), x0, y, n, &full[s]);
+            if (++xb == g.geom.xblocks) {
+                xb = 0;
+                if (++y == g.geom.Ho) {
+                    y = 0;
+                    ++n;
+                }
+            }
+        }
+    } else if (tid == 32) {
+        // MMA issuer: every descriptor is a stage-0 descriptor plus constants
+        // (start address >> 4 in bits 0-13, leading byte offset >> 4 in bits
+        // 16-29), so that issuing an MMA costs a 64-bit add
+        const uint32_t base = umma::smem_u32(smem);
+        const uint64_t dh = umma::smem_desc(base, 0u, 1024u) | ((uint64_t)2u << 61);
+        uint64_t db[KT / 16];
+#pragma unroll
+        for (int k = 0; k < KT / 16; ++k) db[k] = desc_mn(base + kHaloBytes, g.b.sw, k);
+        for (int i = 0; i < n_kt; ++i) {
+            const int s = i % ns;
+            if (!umma::mbar_wait(&full[s], (uint32_t)((i / ns) & 1), g.limit_ns)) {
+                atomicOr(&s_fail, 1u);
+                break;
+            }
+            umma::fence_after_sync();
+            const uint64_t off = (uint64_t)(((uint32_t)s * STAGE) >> 4);
+#pragma unroll
+            for (int p = 0; p < 5; ++p) {
+                const uint32_t ra = tap_row(2 * p), rb = p < 4 ? tap_row(2 * p + 1) : ra + 1u;
+#pragma unroll
+                for (int k = 0; k < KT / 16; ++k) {
+                    const uint64_t add = (uint64_t)((ra * 128u + (uint32_t)k * 2048u) >> 4) |
+                                         ((uint64_t)(((rb - ra) * 128u) >> 4) << 16);
+                    umma::mma_bf16(tmem + (uint32_t)(p * BN), dh + add + off, db[k] + off, idesc,
+                                   (i > 0 || k > 0) ? 1u : 0u);
+                }
+            }
+            umma::mma_commit(&empty[s]);
+        }
+        umma::mma_commit(done);
+    }
+    bool ok = umma::mbar_wait(done, 0u, g.limit_ns);
+    umma::fence_after_sync();
+    ok = __syncthreads_and(ok && s_fail == 0u);
+    if (ok) {
+        const int r = warp * 32 + (tid & 31);
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int p = 0; p < 5; ++p) {
+            const int tap = 2 * p + (r >= 64 ? 1 : 0);
+            const int row = tap * g.C + cp * 64 + (r & 63);
+            float* d = g.dw + (size_t)row * g.N;
+#pragma unroll 1
+            for (int c = 0; c < g.N; c += 8) {
+                float v[8];
+                umma::tmem_ld8(lane_addr + (uint32_t)(p * BN + c), v);
+                if (tap < 9) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) atomicAdd(d + c + q, v[q]);
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(g.err, kErrTimeout);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, TCOLS);
+}
+
+// Halo map of the input view: box 64 channels x 72 pixels x 3 rows x 1.
+inline bool encode_halo(CUtensorMap* map, const void* base, int stride, int W, int H, int N)
+{
+    const cuuint64_t dims[4] = {(cuuint64_t)stride, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t strides[3] = {(cuuint64_t)stride * 2u, (cuuint64_t)stride * 2u * W,
+                                   (cuuint64_t)stride * 2u * W * H};
+    const cuuint32_t box[4] = {64u, (cuuint32_t)kHaloRows, 3u, 1u};
+    return utma::encode_tiled(map, 4, base, dims, strides, box, 128);
+}
+
+template <int BN>
+cudaError_t launch_mn_halo(MnHaloArgs<BN>& g, int ctas, cudaStream_t stream)
+{
+    const int parts = g.C / 64;
+    const int want = ctas > parts ? (ctas + parts - 1) / parts : 1;
+    g.kt_per_split = (g.geom.n_kt + want - 1) / want;
+    if (g.kt_per_split < 1) g.kt_per_split = 1;
+    const int splits = (g.geom.n_kt + g.kt_per_split - 1) / g.kt_per_split;
+    const int ns = g.kt_per_split < STAGES ? g.kt_per_split : STAGES;
+    cudaError_t e = cudaFuncSetAttribute(mn_halo_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)mn_halo_smem_bytes<BN>());
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)parts, (unsigned)(splits > 0 ? splits : 1));
+    mn_halo_kernel<BN><<<grid, 128, mn_halo_smem_bytes<BN>(ns), stream>>>(g);
     return cudaGetLastError();
 }
 

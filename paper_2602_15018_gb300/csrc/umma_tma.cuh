@@ -443,7 +443,9 @@ __global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ T
                 tma_load_2d(sB + s * B_BYTES, &g.tb, kt * SBK, 0, &full[s]);
         }
     } else if (tid == 32) {
-        // MMA issuer
+        // MMA issuer: stage-0 descriptors once, a stage adds its offset to the
+        // start-address field
+        const uint64_t da0 = desc_sw<SW>(umma::smem_u32(sA), 0), db0 = desc_sw<SW>(umma::smem_u32(sB), 0);
         for (int kt = 0; kt < n_kt; ++kt) {
             const int s = kt % ns;
             if (!umma::mbar_wait(&full[s], (uint32_t)((kt / ns) & 1), g.limit_ns)) {
@@ -451,10 +453,11 @@ __global__ void __launch_bounds__(128) tma_gemm_kernel(const __grid_constant__ T
                 break;
             }
             umma::fence_after_sync();
-            const uint32_t a0 = umma::smem_u32(sA + s * A_BYTES), b0 = umma::smem_u32(sB + s * B_BYTES);
+            const uint64_t oa = (uint64_t)(((uint32_t)s * A_BYTES) >> 4), ob = (uint64_t)(((uint32_t)s * B_BYTES) >> 4);
 #pragma unroll
             for (int k = 0; k < SBK / 16; ++k)
-                umma::mma_bf16(tmem, desc_sw<SW>(a0, k), desc_sw<SW>(b0, k), idesc, (kt > 0 || k > 0) ? 1u : 0u);
+                umma::mma_bf16(tmem, da0 + oa + (uint64_t)(k * 2), db0 + ob + (uint64_t)(k * 2), idesc,
+                               (kt > 0 || k > 0) ? 1u : 0u);
             umma::mma_commit(&empty[s]);
         }
         umma::mma_commit(done);
