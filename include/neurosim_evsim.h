@@ -462,7 +462,7 @@ int neurosim_event_frames(int32_t *counts_dev, int32_t width, int32_t height, co
  * when their times differ by at most tol_us.  counts = {matched, n_pred,
  * n_ref, sum over (pixel, polarity) of |n_pred - n_ref|}; scores =
  * {precision, recall, F1, count error = counts[3] / n_ref}.  The paper defines
- * no score; this is the one the learned interpolator is judged by. */
+ * no score; this is the one the learned interpolator is scored by. */
 int neurosim_event_f1(const uint64_t *pred, int64_t n_pred, const uint64_t *ref, int64_t n_ref,
                       int64_t tol_us, int64_t *counts, double *scores);
 

@@ -1,6 +1,6 @@
 // Scoring of an event stream against a reference stream (declared in
 // include/neurosim_evsim.h as neurosim_event_f1): host code, not on any hot
-// path.  Used to judge the learned interpolator's events against the plain
+// path.  Used to score the learned interpolator's events against the plain
 // high-rate path.  The paper defines no score; the definition taken is:
 // predicted and reference events match one to one inside the same pixel and
 // polarity, greedily in time order, when their times differ by at most
