@@ -337,3 +337,44 @@ def test_hd_full_size_whole_stream():
     assert np.array_equal(ev, rev)
     assert np.array_equal(st["ref"], ost["ref"]) and np.array_equal(st["lprev"], ost["lprev"])
     assert np.array_equal(st["tlast"].astype(np.int64), np.where(ost["tlast"] < 0, 0xFFFFFFFF, ost["tlast"]))
+
+
+@pytest.mark.parametrize("W,H", [(65535, 64), (65, 32767)])
+def test_maximum_sizes_and_64_bit_keys(W, H):
+    """The largest sensors the library accepts (2^22 pixels, x up to 65534 and
+    y up to 32766 in the record): 22 pixel bits + 10 time bits + polarity take
+    the 64-bit keys of the emission kernel and the interval sort, and the
+    record's coordinates reach their extremes."""
+    T = 6
+    fr = scenes.random_log_frames(W, H, T, seed=W + H, step=0.15)
+    g, o = _sims(W, H, c_pos=0.2, c_neg=0.25, sigma_c=0.03, refractory_us=100, seed=3, input_is_log=True,
+                 max_frames_per_step=T)
+    g.step(torch.from_numpy(fr).cuda(), 0, DT)
+    ev, seg = g.drain()
+    rev, rseg = o.step(fr, 0, DT)
+    assert_same(ev, seg, rev, rseg, f"{W}x{H}")
+    _check_state(g, o)
+    x = (rev >> np.uint64(1)) & np.uint64(0xFFFF)
+    y = (rev >> np.uint64(17)) & np.uint64(0x7FFF)
+    assert int(x.max()) == W - 1 and int(y.max()) == H - 1
+    g.close()
+
+
+def test_long_gap_takes_64_bit_keys():
+    """A step that continues after a 5 s gap: its first interval needs 23 time
+    bits, so a 1000x700 sensor (20 pixel bits) switches to 64-bit keys for
+    that step and back for the next."""
+    W, H, T = 1000, 700, 8
+    fr = scenes.random_log_frames(W, H, 3 * T, seed=11, step=0.12)
+    g, o = _sims(W, H, c_pos=0.2, c_neg=0.2, sigma_c=0.02, refractory_us=50, seed=5, input_is_log=True,
+                 max_frames_per_step=T)
+    starts = [0, 5_000_000 + T * DT, 5_000_000 + 2 * T * DT]
+    for k, t0 in enumerate(starts):
+        chunk = np.ascontiguousarray(fr[k * T:(k + 1) * T])
+        g.step(torch.from_numpy(chunk).cuda(), t0, DT)
+        ev, seg = g.drain()
+        rev, rseg = o.step(chunk, t0, DT)
+        assert_same(ev, seg, rev, rseg, f"step {k}")
+        assert len(rev) > 1000
+    _check_state(g, o)
+    g.close()
