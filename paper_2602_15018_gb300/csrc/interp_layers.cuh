@@ -221,6 +221,9 @@ struct EpiAct {
     int relu;
     static constexpr bool kStaged = true;
     __device__ __forceinline__ bf16* row_ptr(int row) const { return out + (size_t)row * stride + off; }
+    // staged drain: destination of columns c0 .. c0 + 31 of row = base_ptr(row) + col_offset(c0)
+    __device__ __forceinline__ bf16* base_ptr(int row) const { return row_ptr(row); }
+    __device__ __forceinline__ size_t col_offset(int c0) const { return (size_t)c0; }
     // columns c0 .. c0 + 31 of one pixel as four 16-byte chunks
     __device__ __forceinline__ void pack32(int c0, const float (&v)[32], uint4 (&o)[4]) const
     {
@@ -254,6 +257,32 @@ struct EpiConvT {
     int stride, off;
     const float* bias;
     int Cout, Hl, Wl;
+    // staged drain (Cout a multiple of 32): the 32 columns c0 .. c0 + 31 of a
+    // low-resolution pixel are 64 contiguous bytes of one output pixel, so the
+    // warp writes whole sectors instead of 16-byte pieces 256 bytes apart
+    static constexpr bool kStaged = true;
+    __device__ __forceinline__ bf16* base_ptr(int row) const
+    {
+        const int hw = Hl * Wl;
+        const int n = row / hw, rem = row - n * hw, y = rem / Wl, x = rem - (rem / Wl) * Wl;
+        return out + (((size_t)n * 2 * Hl + 2 * y) * (2 * Wl) + 2 * x) * stride + off;
+    }
+    __device__ __forceinline__ size_t col_offset(int c0) const
+    {
+        const int ab = c0 / Cout, o = c0 - ab * Cout;
+        return ((size_t)(ab >> 1) * (2 * Wl) + (ab & 1)) * stride + o;
+    }
+    __device__ __forceinline__ void pack32(int c0, const float (&v)[32], uint4 (&o)[4]) const
+    {
+        const int oc = c0 % Cout;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float t[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) t[i] = v[8 * q + i] + bias[oc + 8 * q + i];
+            o[q] = pack8(t);
+        }
+    }
     __device__ __forceinline__ void store(int row, int c0, const float (&v)[8], int) const
     {
         const int hw = Hl * Wl;

@@ -346,6 +346,13 @@ __device__ __forceinline__ void drain_row_staged(uint32_t lane_addr, int row0, i
                                                  uint4* stage, int lane)
 {
     static_assert(BN % 32 == 0, "columns");
+    // destination rows of this lane's four stores, once per tile
+    decltype(ep.base_ptr(0)) base[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int px = 8 * i + (lane >> 2);
+        base[i] = px < n_valid ? ep.base_ptr(row0 + px) : ep.base_ptr(row0);
+    }
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
@@ -357,11 +364,12 @@ __device__ __forceinline__ void drain_row_staged(uint32_t lane_addr, int row0, i
 #pragma unroll
         for (int q = 0; q < 4; ++q) stage[lane * 4 + (q ^ ((lane >> 1) & 3))] = o[q];
         __syncwarp();
+        const size_t co = ep.col_offset(c0);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int px = 8 * i + (lane >> 2), q = lane & 3;
             const uint4 val = stage[px * 4 + (q ^ ((px >> 1) & 3))];
-            if (px < n_valid) *reinterpret_cast<uint4*>(ep.row_ptr(row0 + px) + c0 + 8 * q) = val;
+            if (px < n_valid) *reinterpret_cast<uint4*>(base[i] + co + 8 * q) = val;
         }
         __syncwarp();
     }
