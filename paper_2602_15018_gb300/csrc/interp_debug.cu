@@ -113,11 +113,8 @@ __global__ void expiring_wait_kernel(int arrive, uint64_t limit_ns, unsigned int
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
-    if (threadIdx.x == 0 && arrive) {
-        uint64_t state;
-        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(umma::smem_u32(&bar)) : "memory");
-        (void)state;
-    }
+    if (threadIdx.x == 0 && arrive)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_u32(&bar)) : "memory");
     __syncwarp();
     const bool ok = umma::mbar_wait(&bar, 0, limit_ns);
     if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) atomicOr(err, nsim::kErrTimeout);

@@ -580,7 +580,7 @@ template <int BN, int SW, int SWA, int CC, class EP>
 __global__ void __launch_bounds__(kHaloThreads) halo_conv_kernel(const __grid_constant__ HaloArgs<EP> g)
 {
     static_assert(SWA == 0 || SWA == 64 || SWA == 128, "halo layouts");
-    static_assert((CC == 8 && SWA == 0) || (CC % 16 == 0 && (SWA == 0 || CC % (SWA / 2) == 0) && CC % bk_of(SW) == 0),
+    static_assert((CC == 8 && SWA == 0) || (CC % 16 == 0 && CC % (SWA ? SWA / 2 : 1) == 0 && CC % bk_of(SW) == 0),
                   "channels");
     constexpr int HC = SWA ? SWA / 2 : 8;           // channels per halo box
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "tcgen05 N for M = 128, two accumulators");
